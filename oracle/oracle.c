@@ -1,0 +1,315 @@
+/*
+ * oracle.c -- plain, slow, single-threaded reference results for the graph
+ * method of "SIMD-X: Programming and Processing of Graph Algorithms on GPUs"
+ * (Liu & Huang).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; it exists so that tests, the smoke check and the timed CPU
+ * baseline can compare the CUDA library against results computed here.  It
+ * shares no code, header or table with the CUDA path.
+ *
+ * Each function is the textbook definition of the result the paper's
+ * iterative method reaches exactly (Sec. 5):
+ *   - BFS levels (Sec. 5, "BFS"): FIFO-queue breadth-first search.
+ *   - SSSP distances (Sec. 2.1, Sec. 3.3): Dijkstra with a binary heap.
+ *     The method (delta-stepping / frontier relaxation) reaches the same
+ *     unique distances in any relaxation order.
+ *   - k-core membership (Sec. 5, "k-Core"): repeatedly delete vertices of
+ *     degree < k; the remaining set is the unique maximal subgraph of
+ *     minimum degree >= k.
+ *   - Core numbers: Batagelj & Zaversnik, "An O(m) algorithm for cores
+ *     decomposition of networks" (2003), as a cross-check of k-core.
+ *   - PageRank (Sec. 5, "PageRank"): Jacobi power iteration in double
+ *     precision, pulling contributions from in-neighbours and summing them.
+ *   - The BSP frontier relaxation of Sec. 2.1 (Fig. 1 narrative): a vertex
+ *     becomes active when its distance changed in the previous iteration.
+ *
+ * Conventions: vertex ids int32, CSR offsets int64, unreached BFS level -1,
+ * unreached distance UINT32_MAX.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OR_EXPORT __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------ BFS */
+/* Sec. 5 "BFS": level by level from src; level(src) = 0. */
+OR_EXPORT int or_bfs(int64_t n, const int64_t *off, const int32_t *idx,
+                     int32_t src, int32_t *level)
+{
+    if (src < 0 || src >= n) return 1;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t v = 0; v < n; ++v) level[v] = -1;
+    int64_t head = 0, tail = 0;
+    level[src] = 0;
+    queue[tail++] = src;
+    while (head < tail) {
+        int32_t v = queue[head++];
+        for (int64_t p = off[v]; p < off[v + 1]; ++p) {
+            int32_t u = idx[p];
+            if (level[u] < 0) {
+                level[u] = level[v] + 1;
+                queue[tail++] = u;
+            }
+        }
+    }
+    free(queue);
+    return 0;
+}
+
+/* ----------------------------------------------------------------- SSSP */
+typedef struct { uint64_t d; int32_t v; } hent;
+
+static void heap_push(hent *h, int64_t *sz, uint64_t d, int32_t v)
+{
+    int64_t i = (*sz)++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h[p].d <= d) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i].d = d;
+    h[i].v = v;
+}
+
+static hent heap_pop(hent *h, int64_t *sz)
+{
+    hent top = h[0], last = h[--(*sz)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *sz) break;
+        if (c + 1 < *sz && h[c + 1].d < h[c].d) ++c;
+        if (h[c].d >= last.d) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*sz > 0) h[i] = last;
+    return top;
+}
+
+/* Dijkstra with lazy deletion.  Distances are accumulated in 64 bits; the
+ * call fails (returns 2) if a reached distance does not fit below
+ * UINT32_MAX, which is the unreached sentinel. */
+OR_EXPORT int or_sssp(int64_t n, const int64_t *off, const int32_t *idx,
+                      const uint32_t *w, int32_t src, uint32_t *dist)
+{
+    if (src < 0 || src >= n) return 1;
+    uint64_t *d = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    uint8_t *done = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t cap = off[n] + 1, sz = 0;
+    hent *h = (hent *)malloc(sizeof(hent) * (size_t)cap);
+    for (int64_t v = 0; v < n; ++v) d[v] = UINT64_MAX;
+    d[src] = 0;
+    heap_push(h, &sz, 0, src);
+    while (sz > 0) {
+        hent t = heap_pop(h, &sz);
+        if (done[t.v]) continue;
+        done[t.v] = 1;
+        for (int64_t p = off[t.v]; p < off[t.v + 1]; ++p) {
+            int32_t u = idx[p];
+            uint64_t nd = t.d + w[p];
+            if (nd < d[u]) {
+                d[u] = nd;
+                heap_push(h, &sz, nd, u);
+            }
+        }
+    }
+    int rc = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (d[v] == UINT64_MAX) dist[v] = UINT32_MAX;
+        else if (d[v] >= UINT32_MAX) { dist[v] = UINT32_MAX; rc = 2; }
+        else dist[v] = (uint32_t)d[v];
+    }
+    free(d);
+    free(done);
+    free(h);
+    return rc;
+}
+
+/* The BSP frontier relaxation narrated in Sec. 2.1: start with src active;
+ * in each iteration every active vertex relaxes its out-edges against the
+ * distances of the previous iteration (Jacobi), and the vertices whose
+ * distance changed form the next active set.  Writes the distance array
+ * after each iteration into hist[it*n ...] (UINT32_MAX = infinite) for up to
+ * max_it iterations and returns the number of iterations run. */
+OR_EXPORT int64_t or_sssp_bsp(int64_t n, const int64_t *off, const int32_t *idx,
+                              const uint32_t *w, int32_t src, int64_t max_it,
+                              uint32_t *hist)
+{
+    uint32_t *cur = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    uint32_t *nxt = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    uint8_t *act = (uint8_t *)calloc((size_t)n, 1);
+    for (int64_t v = 0; v < n; ++v) cur[v] = UINT32_MAX;
+    cur[src] = 0;
+    act[src] = 1;
+    int64_t it = 0;
+    for (; it < max_it; ++it) {
+        memcpy(nxt, cur, sizeof(uint32_t) * (size_t)n);
+        for (int64_t v = 0; v < n; ++v) {
+            if (!act[v]) continue;
+            for (int64_t p = off[v]; p < off[v + 1]; ++p) {
+                uint64_t nd = (uint64_t)cur[v] + w[p];
+                if (nd < nxt[idx[p]]) nxt[idx[p]] = (uint32_t)nd;
+            }
+        }
+        int any = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            act[v] = nxt[v] != cur[v];
+            any |= act[v];
+        }
+        memcpy(hist + it * n, nxt, sizeof(uint32_t) * (size_t)n);
+        memcpy(cur, nxt, sizeof(uint32_t) * (size_t)n);
+        if (!any) { ++it; break; }
+    }
+    free(cur);
+    free(nxt);
+    free(act);
+    return it;
+}
+
+/* --------------------------------------------------------------- k-core */
+/* Sec. 5 "k-Core": delete every vertex whose degree is < k, updating the
+ * degrees of its neighbours, until none is left to delete.  in_core[v] = 1
+ * for survivors; resid[v] = number of surviving neighbours of a survivor,
+ * 0 for deleted vertices. */
+OR_EXPORT int or_kcore(int64_t n, const int64_t *off, const int32_t *idx,
+                       uint32_t k, uint8_t *in_core, uint32_t *resid)
+{
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t head = 0, tail = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        deg[v] = off[v + 1] - off[v];
+        in_core[v] = 1;
+        if (deg[v] < (int64_t)k) {
+            in_core[v] = 0;
+            queue[tail++] = (int32_t)v;
+        }
+    }
+    while (head < tail) {
+        int32_t v = queue[head++];
+        for (int64_t p = off[v]; p < off[v + 1]; ++p) {
+            int32_t u = idx[p];
+            if (!in_core[u]) continue;
+            if (--deg[u] < (int64_t)k) {
+                in_core[u] = 0;
+                queue[tail++] = u;
+            }
+        }
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        uint32_t c = 0;
+        if (in_core[v])
+            for (int64_t p = off[v]; p < off[v + 1]; ++p) c += in_core[idx[p]];
+        if (resid) resid[v] = c;
+    }
+    free(deg);
+    free(queue);
+    return 0;
+}
+
+/* Core number of every vertex (Batagelj & Zaversnik 2003): bucket the
+ * vertices by degree and repeatedly remove a vertex of minimum current
+ * degree; its current degree at removal is its core number. */
+OR_EXPORT int or_coreness(int64_t n, const int64_t *off, const int32_t *idx,
+                          uint32_t *core)
+{
+    if (n == 0) return 0;
+    int64_t md = 0;
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t v = 0; v < n; ++v) {
+        deg[v] = off[v + 1] - off[v];
+        if (deg[v] > md) md = deg[v];
+    }
+    int64_t *bin = (int64_t *)calloc((size_t)md + 2, sizeof(int64_t));
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *vert = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t v = 0; v < n; ++v) bin[deg[v]]++;
+    int64_t start = 0;
+    for (int64_t d = 0; d <= md; ++d) {
+        int64_t num = bin[d];
+        bin[d] = start;
+        start += num;
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        pos[v] = bin[deg[v]];
+        vert[pos[v]] = v;
+        bin[deg[v]]++;
+    }
+    for (int64_t d = md; d >= 1; --d) bin[d] = bin[d - 1];
+    bin[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = vert[i];
+        for (int64_t p = off[v]; p < off[v + 1]; ++p) {
+            int64_t u = idx[p];
+            if (deg[u] > deg[v]) {
+                int64_t du = deg[u], pu = pos[u], pw = bin[du], w = vert[pw];
+                if (u != w) {
+                    pos[u] = pw;
+                    vert[pu] = w;
+                    pos[w] = pu;
+                    vert[pw] = u;
+                }
+                bin[du]++;
+                deg[u]--;
+            }
+        }
+    }
+    for (int64_t v = 0; v < n; ++v) core[v] = (uint32_t)deg[v];
+    free(deg);
+    free(bin);
+    free(pos);
+    free(vert);
+    return 0;
+}
+
+/* ------------------------------------------------------------- PageRank */
+/* Sec. 5 "PageRank": pull the contributions x(u)/outdeg(u) of every
+ * in-neighbour u, sum them, and iterate until the ranks are stable.
+ *   x_0(v)     = 1/n
+ *   x_{t+1}(v) = (1-d)/n + d * ( sum_{u in N_in(v)} x_t(u)/outdeg(u) + D_t/n )
+ * with D_t the rank held by vertices of out-degree 0, spread uniformly.
+ * Stops after the first iteration with ||x_{t+1} - x_t||_1 < tol, or after
+ * max_iter iterations; if fixed_iter >= 0, runs exactly fixed_iter
+ * iterations instead.  in_off/in_idx is the in-neighbour CSR (CSC) and
+ * outdeg the out-degree of each vertex.  Returns the iteration count. */
+OR_EXPORT int64_t or_pagerank(int64_t n, const int64_t *in_off,
+                              const int32_t *in_idx, const int64_t *outdeg,
+                              double d, double tol, int64_t max_iter,
+                              int64_t fixed_iter, double *x_out, double *l1_out)
+{
+    if (n == 0) return 0;
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int64_t v = 0; v < n; ++v) x[v] = 1.0 / (double)n;
+    int64_t t = 0;
+    double l1 = 0.0;
+    int64_t limit = fixed_iter >= 0 ? fixed_iter : max_iter;
+    while (t < limit) {
+        double dangling = 0.0;
+        for (int64_t u = 0; u < n; ++u)
+            if (outdeg[u] == 0) dangling += x[u];
+        l1 = 0.0;
+        for (int64_t v = 0; v < n; ++v) {
+            double s = 0.0;
+            for (int64_t p = in_off[v]; p < in_off[v + 1]; ++p) {
+                int32_t u = in_idx[p];
+                s += x[u] / (double)outdeg[u];
+            }
+            y[v] = (1.0 - d) / (double)n + d * (s + dangling / (double)n);
+            l1 += fabs(y[v] - x[v]);
+        }
+        double *tmp = x; x = y; y = tmp;
+        ++t;
+        if (fixed_iter < 0 && l1 < tol) break;
+    }
+    memcpy(x_out, x, sizeof(double) * (size_t)n);
+    if (l1_out) *l1_out = l1;
+    free(x);
+    free(y);
+    return t;
+}
