@@ -1,0 +1,467 @@
+#!/usr/bin/env python3
+"""Benchmark of the ACC graph hot path on GB300.
+
+Default workload (the configuration the headline metric is quoted on): a
+symmetrised R-MAT graph at scale 20 (1,048,576 vertices, edge factor 16,
+a/b/c/d = 0.57/0.19/0.19/0.05), int32 CSR, uint32 weights in [1,64].  One
+step runs, each as one persistent kernel through the C ABI: SSSP from vertex
+0, k-core with k = 16 and PageRank (d = 0.85, FP32, L1 stop 1e-6).
+Other workloads: --workload rmat24-bfs (BFS from vertex 0 on R-MAT scale 24,
+int64 offsets), rmat16-bfs, rmat24-sssp, grid4096-bfs, grid4096-sssp.
+
+Metric: GTEPS = traversed undirected edges per second (Graph500 counting:
+BFS / SSSP count the edges of the component reached from the source, k-core
+counts every edge once, PageRank counts every edge once per iteration).
+
+Timing: W untimed warm-up steps, then K timed steps; each step is bracketed
+by CUDA events on the launching stream and the L2 is flushed (a 512 MB write)
+between steps, outside the events.  Every kernel launch of a step is also
+bracketed so the dominant kernel's roofline fraction uses its own duration.
+`e2e` repeats the step through the public API with HOST buffers: the graph
+is uploaded from pinned memory (simdx_graph_create) and the results are read
+back, all inside the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    "rmat20": dict(kind="rmat", scale=20, bits=32, algs=["sssp", "kcore", "pagerank"],
+                   desc="R-MAT scale 20 (n=1,048,576, ef 16), int32 CSR, w in [1,64]: "
+                        "SSSP src 0 + k-core k=16 + PageRank d=0.85 tol 1e-6"),
+    "rmat24-bfs": dict(kind="rmat", scale=24, bits=64, algs=["bfs"],
+                       desc="R-MAT scale 24 (n=16,777,216, ef 16), int64 offsets: BFS src 0"),
+    "rmat24-sssp": dict(kind="rmat", scale=24, bits=64, algs=["sssp"],
+                        desc="R-MAT scale 24, int64 offsets, w in [1,64]: SSSP src 0"),
+    "rmat16-bfs": dict(kind="rmat", scale=16, bits=32, algs=["bfs"],
+                       desc="R-MAT scale 16 (n=65,536, ef 16), int32 CSR: BFS src 0"),
+    "grid4096-bfs": dict(kind="grid", rows=4096, bits=64, algs=["bfs"],
+                         desc="4096x4096 4-neighbour grid: BFS from corner 0"),
+    "grid4096-sssp": dict(kind="grid", rows=4096, bits=64, algs=["sssp"], wmax=1000,
+                          desc="4096x4096 4-neighbour grid, w in [1,1000]: SSSP from corner 0"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="simdx", choices=["simdx", "reference"])
+    p.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=5)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def make_graph(wl):
+    import graphgen as gg
+    if wl["kind"] == "rmat":
+        g = gg.rmat(wl["scale"])
+        w = gg.weights(g, gg.weight_seed(wl["scale"]), 1, wl.get("wmax", 64))
+    else:
+        g = gg.grid(wl["rows"], wl["rows"])
+        w = gg.weights(g, 0x6121D ^ 0xFFFF, 1, wl.get("wmax", 1000))
+    return g, w
+
+
+def s_off(bits):
+    return bits // 8
+
+
+# ------------------------------------------------------------ clocks sampling
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={','.join(self.FIELDS)}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1812_04070_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        rec = d[f"{workload}:{kernel}"]
+        if rec.get("source_hash") != kernel_source_hash():
+            return None
+        return float(rec["bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------ work accounting
+def reached_edges(g, reached_mask):
+    deg = g.degrees()
+    e_c = int(deg[reached_mask].sum())
+    return e_c, int(reached_mask.sum())
+
+
+def algorithmic(alg, g, bits, out, iters):
+    """(undirected traversed edges, algorithmic bytes) of one launch."""
+    so = s_off(bits)
+    n, e = g.n, g.e
+    if alg == "bfs":
+        e_c, n_c = reached_edges(g, out >= 0)
+        return e_c // 2, 4 * e_c + (2 * so + 4 + 8) * n_c
+    if alg == "sssp":
+        e_c, n_c = reached_edges(g, out != 0xFFFFFFFF)
+        return e_c // 2, 8 * e_c + (2 * so + 4 + 8) * n_c
+    if alg == "kcore":
+        return e // 2, 4 * e + (2 * so + 1) * n
+    if alg == "pagerank":
+        return (e // 2) * iters, (4 * e + (2 * so + 12) * n) * iters
+    raise ValueError(alg)
+
+
+# ------------------------------------------------------------ the GPU arm
+def run_simdx(args, rank, world, local):
+    import torch
+    from paper_1812_04070_gb300 import Graph, build, simdx_stats
+
+    wl = WORKLOADS[args.workload]
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    build()
+    g, w = make_graph(wl)
+    bits = wl["bits"]
+    off = g.offsets if bits == 64 else g.offsets.astype(np.int32)
+    G = Graph(off, g.indices, weights=w)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    outs = {
+        "bfs": torch.empty(g.n, dtype=torch.int32, device=dev),
+        "sssp": torch.empty(g.n, dtype=torch.int32, device=dev),
+        "kcore": (torch.empty(g.n, dtype=torch.uint8, device=dev), torch.empty(g.n, dtype=torch.int32, device=dev)),
+        "pagerank": torch.empty(g.n, dtype=torch.float32, device=dev),
+    }
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def launch(alg, st=None):
+        if alg == "bfs":
+            G.bfs(0, out=outs["bfs"], stats=st)
+        elif alg == "sssp":
+            G.sssp(0, out=outs["sssp"], stats=st)
+        elif alg == "kcore":
+            G.kcore(16, out=outs["kcore"][0], resid=outs["kcore"][1], stats=st)
+        else:
+            G.pagerank(0.85, 1e-6, 1000, out=outs["pagerank"], stats=st)
+
+    algs = wl["algs"]
+    evs = {a: [] for a in algs}
+    step_ev = []
+
+    def step(record):
+        if record:
+            s0 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+        for a in algs:
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            launch(a)
+            if record:
+                e1.record(stream)
+                evs[a].append((e0, e1))
+        if record:
+            s1 = torch.cuda.Event(enable_timing=True)
+            s1.record(stream)
+            step_ev.append((s0, s1))
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(False)
+    torch.cuda.synchronize()
+    # per-algorithm work (iterations are stable run to run)
+    stats = {}
+    for a in algs:
+        st = simdx_stats()
+        launch(a, st)
+        torch.cuda.synchronize()
+        stats[a] = st
+        assert st.status == 0, f"{a} status {st.status}"
+    work = {}
+    for a in algs:
+        o = outs[a]
+        if a == "kcore":
+            host = None
+        elif a == "sssp":
+            host = o.cpu().numpy().view(np.uint32)
+        else:
+            host = o.cpu().numpy()
+        work[a] = algorithmic(a, g, bits, host, stats[a].iterations)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.2)
+    wall0 = time.time()
+    for _ in range(args.steps):
+        flush.zero_()
+        step(True)
+    torch.cuda.synchronize()
+    wall = time.time() - wall0
+    clocks = clk.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    kern_ms = {a: [x.elapsed_time(y) for x, y in evs[a]] for a in algs}
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    edges_step = sum(work[a][0] for a in algs)
+    value = edges_step * args.steps * world / (total_ms / 1e3) / 1e9
+    # dominant kernel and its roofline
+    mean_k = {a: statistics.mean(kern_ms[a]) for a in algs}
+    dom = max(algs, key=lambda a: mean_k[a])
+    peak, peak_kind = measured_peaks()
+    achieved = work[dom][1] / (mean_k[dom] / 1e3) / 1e9
+    traffic = ncu_traffic(dom + "_kernel", args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": f"{dom}_kernel",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": work[dom][1],
+                "mean_launch_ms": round(mean_k[dom], 4)}
+    per_kernel = {a: {"mean_ms": round(mean_k[a], 4), "median_ms": round(statistics.median(kern_ms[a]), 4),
+                      "iterations": stats[a].iterations, "gteps": round(work[a][0] / (mean_k[a] / 1e3) / 1e9, 3),
+                      "gbs": round(work[a][1] / (mean_k[a] / 1e3) / 1e9, 1),
+                      "frac_of_peak": round(work[a][1] / (mean_k[a] / 1e3) / 1e9 / peak, 4),
+                      "push_iters": stats[a].push_iters, "pull_iters": stats[a].pull_iters,
+                      "ballot_iters": stats[a].ballot_iters, "online_iters": stats[a].online_iters,
+                      "grid_ctas": stats[a].grid_ctas}
+                  for a in algs}
+    # ---- e2e through the C ABI with host buffers
+    e2e = run_e2e(args, g, w, bits, algs, edges_step, world)
+    res = {
+        "metric": "GTEPS", "value": round(value, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic (seeded R-MAT / grid)",
+        "config": {"workload": args.workload, "description": wl["desc"], "n": g.n, "directed_edges": g.e,
+                   "l2": "flushed between steps (512 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline, "kernels": per_kernel, "e2e": e2e, "gpu_launches": len(algs) * args.steps,
+        "clocks": clocks, "wall_s_timed": round(wall, 3),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args.workload, g, w, budget_s=15.0)
+    G.close()
+    return res
+
+
+def run_e2e(args, g, w, bits, algs, edges_step, world):
+    import torch
+    from paper_1812_04070_gb300 import Graph
+
+    off = g.offsets if bits == 64 else g.offsets.astype(np.int32)
+    p_off = torch.from_numpy(off).pin_memory()
+    p_idx = torch.from_numpy(g.indices).pin_memory()
+    p_w = torch.from_numpy(w.view(np.int32)).pin_memory()
+    host_out = {"bfs": torch.empty(g.n, dtype=torch.int32).pin_memory(),
+                "sssp": torch.empty(g.n, dtype=torch.int32).pin_memory(),
+                "kcore": (torch.empty(g.n, dtype=torch.uint8).pin_memory(),
+                          torch.empty(g.n, dtype=torch.int32).pin_memory()),
+                "pagerank": torch.empty(g.n, dtype=torch.float32).pin_memory()}
+    h2d = p_off.numel() * p_off.element_size() + p_idx.numel() * 4 + (p_w.numel() * 4 if "sssp" in algs else 0)
+    d2h = 0
+    for a in algs:
+        d2h += g.n * (4 if a in ("bfs", "sssp", "pagerank") else 5)
+
+    def one():
+        G = Graph(p_off.numpy(), p_idx.numpy(), weights=p_w.numpy().view(np.uint32) if "sssp" in algs else None)
+        for a in algs:
+            if a == "bfs":
+                host_out[a].copy_(G.bfs(0), non_blocking=True)
+            elif a == "sssp":
+                host_out[a].copy_(G.sssp(0), non_blocking=True)
+            elif a == "kcore":
+                ic, rs = G.kcore(16)
+                host_out[a][0].copy_(ic, non_blocking=True)
+                host_out[a][1].copy_(rs, non_blocking=True)
+            else:
+                host_out[a].copy_(G.pagerank(0.85, 1e-6, 1000), non_blocking=True)
+        torch.cuda.synchronize()
+        G.close()
+
+    one()
+    ts = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        one()
+        ts.append(time.perf_counter() - t0)
+    tot = sum(ts)
+    if world > 1:
+        t = torch.tensor([tot], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot = float(t.item())
+    return {"value": round(edges_step * len(ts) * world / tot / 1e9, 3), "unit": "GTEPS",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": round(tot / len(ts) * 1e3, 3),
+            "note": "host pinned CSR -> simdx_graph_create -> algorithms -> results to host, per step"}
+
+
+# ------------------------------------------------------------ CPU oracle legs
+def cpu_baseline(workload, g, w, budget_s=15.0):
+    """The oracle as it stands (single thread), on a bounded sample of the
+    workload; returns GTEPS with the same edge counting."""
+    import oracle
+    wl = WORKLOADS[workload]
+    t_tot, edges = 0.0, 0
+    parts = []
+    for a in wl["algs"]:
+        t0 = time.perf_counter()
+        if a == "bfs":
+            lev = oracle.bfs(g.offsets, g.indices, 0)
+            m = int(g.degrees()[lev >= 0].sum()) // 2
+            parts.append("bfs full")
+        elif a == "sssp":
+            d = oracle.sssp(g.offsets, g.indices, w, 0)
+            m = int(g.degrees()[d != 0xFFFFFFFF].sum()) // 2
+            parts.append("sssp full")
+        elif a == "kcore":
+            oracle.kcore(g.offsets, g.indices, 16)
+            m = g.e // 2
+            parts.append("kcore full")
+        else:
+            iters = 5
+            oracle.pagerank(g.offsets, g.indices, fixed_iter=iters)
+            m = (g.e // 2) * iters
+            parts.append(f"pagerank {iters} iterations")
+        t_tot += time.perf_counter() - t0
+        edges += m
+        if t_tot > budget_s:
+            break
+    return {"value": round(edges / t_tot / 1e9, 4), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{workload}: " + ", ".join(parts) + f" ({t_tot:.1f} s, single thread)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl = WORKLOADS[args.workload]
+    g, w = make_graph(wl)
+    cb = cpu_baseline(args.workload, g, w, budget_s=10.0)  # warm-up of the sample
+    vals = []
+    for _ in range(max(1, args.steps if args.steps <= 3 else 3)):
+        vals.append(cpu_baseline(args.workload, g, w, budget_s=10.0)["value"])
+    v = statistics.median(vals)
+    return {"impl": "reference", "metric": "GTEPS", "value": v, "unit": "GTEPS", "n_gpus": world,
+            "steps": len(vals), "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32+f64", "data": "synthetic (seeded R-MAT / grid)",
+            "config": {"workload": args.workload, "description": wl["desc"]},
+            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_simdx(args, rank, world, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * simdx.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * Active-Compute-Combine (ACC) graph hot path of "SIMD-X: Programming and
+ * Processing of Graph Algorithms on GPUs" (Liu & Huang).
+ *
+ * One call runs one whole graph algorithm as ONE persistent cooperative
+ * kernel (Sec. 5, "Push-Pull based kernel fusion"; Eq. 1): every BSP
+ * iteration filters the active vertices into degree-binned task lists
+ * (Sec. 4, online / ballot filters and the JIT controller), computes on the
+ * edges of each active vertex in push or pull direction, and combines the
+ * updates into vertex state (Sec. 3.2, Active / Compute / Combine), with a
+ * software grid barrier between iterations that cannot deadlock because the
+ * grid is sized to co-residency (Sec. 5, "Compiler-based deadlock free
+ * barrier", Eq. 1) and that times out instead of hanging.
+ *
+ * Conventions shared by every entry point
+ *   - Status codes only (simdx_status); nothing throws across the ABI.
+ *   - Vertex ids are int32 in [0, n).  Graph arrays are CSR (Sec. 6,
+ *     "Storage Format"): offsets[n+1] (int32 or int64, non-decreasing,
+ *     offsets[0] = 0) and indices[e] (int32).
+ *   - Output buffers are DEVICE memory owned by the caller and must hold n
+ *     elements (k*n for batched calls).  The library writes every element.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  `stats`, when non-NULL, is HOST memory written by a
+ *     host function enqueued on the same stream: it is valid once the stream
+ *     has been synchronised.  Errors detected on the device (barrier time
+ *     out) are reported in stats->status and by simdx_graph_last_status().
+ *   - A graph owns one device workspace, so calls on the same graph must not
+ *     overlap in time: issue them on one stream or synchronise in between.
+ *     Different graphs are independent.
+ *   - The library allocates device memory only in simdx_graph_create,
+ *     simdx_graph_set_config (when a larger workspace is needed) and the
+ *     batch / server entry points that say so; the algorithm calls allocate
+ *     nothing.
+ */
+#ifndef SIMDX_H
+#define SIMDX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SIMDX_API __attribute__((visibility("default")))
+#else
+#define SIMDX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIMDX_OK = 0,
+    SIMDX_EINVAL = 1,             /* bad argument (range, NULL, size)           */
+    SIMDX_ENOMEM = 2,             /* device or pinned host allocation failed    */
+    SIMDX_ECUDA = 3,              /* a CUDA runtime call failed                 */
+    SIMDX_EBARRIER_TIMEOUT = 4,   /* a grid-barrier wait ran out (device side)  */
+    SIMDX_EUNSUPPORTED = 5,       /* valid request this build does not support  */
+    SIMDX_EBUSY = 6,              /* resource in use / queue full               */
+    SIMDX_ENOTREADY = 7           /* result not ready yet (server poll)         */
+} simdx_status;
+
+/* Graph in CSR form (Sec. 6 "Storage Format").  `e` = number of directed
+ * edge entries = offsets[n]. */
+typedef struct {
+    int64_t n;
+    int64_t e;
+    int32_t offset_bits;     /* 32 or 64 */
+    const void *offsets;     /* [n+1] int32 or int64 */
+    const int32_t *indices;  /* [e] */
+} simdx_csr;
+
+/* simdx_graph_create flags */
+#define SIMDX_INPUT_HOST 1u  /* arrays are host memory; the library copies them */
+#define SIMDX_BORROW     2u  /* device arrays are used in place, not copied;
+                                the caller keeps them alive until destroy     */
+
+/* Per-call statistics, written to host memory when the stream reaches the
+ * end of the call. */
+typedef struct {
+    int32_t status;          /* simdx_status of the device run              */
+    int32_t iterations;      /* BSP iterations (PageRank: rank updates)     */
+    int32_t push_iters;      /* iterations computed in push direction       */
+    int32_t pull_iters;      /* iterations computed in pull direction       */
+    int32_t ballot_iters;    /* iterations whose lists came from the ballot
+                                filter (online filter overflowed or forced)  */
+    int32_t online_iters;    /* iterations whose lists came from the online
+                                filter                                       */
+    int32_t phases;          /* grid barriers passed                        */
+    int32_t grid_ctas;       /* CTAs of the persistent launch (Eq. 1)       */
+    int64_t edges_visited;   /* edge entries read by compute                */
+    int64_t frontier_sum;    /* sum over iterations of active vertices      */
+    double last_l1;          /* PageRank: L1 change of the last iteration   */
+    int64_t reserved[4];
+} simdx_stats;
+
+/* Tuning knobs (defaults in brackets).  Every knob changes speed only, never
+ * results. */
+typedef struct {
+    int32_t small_max;       /* degree < small_max -> thread list [32]   (Sec. 4 "Classification") */
+    int32_t med_max;         /* degree < med_max   -> warp list   [128]  (Sec. 4) */
+    int32_t huge_min;        /* degree >= huge_min -> split over the grid [16384] */
+    int32_t bin_per_thread;  /* online-filter overflow threshold per thread [64] (Sec. 4
+                                "Overflow thresholds"); 0 forces the ballot filter */
+    int32_t direction;       /* 0 auto, 1 push only, 2 pull only [0] (Sec. 5) */
+    int32_t filter;          /* 0 JIT (online, ballot on overflow), 2 ballot only [0] (Sec. 4) */
+    float alpha;             /* BFS push->pull when frontier edges > unexplored edges / alpha [14] */
+    float beta;              /* BFS pull->push when frontier vertices < n / beta [24] */
+    float kcore_alpha;       /* k-core pull when removed-vertex edges > alive edges / kcore_alpha [8] */
+    uint32_t delta;          /* SSSP delta-stepping bucket width, 0 = unbounded [32] */
+    int32_t ctas_per_sm;     /* 0 = occupancy maximum (Eq. 1); else clamp [0] */
+    int32_t barrier_timeout_ms; /* grid-barrier wait limit [2000] */
+    int32_t debug_skip_cta;  /* test knob: this CTA skips barrier arrival number
+                                debug_skip_phase (-1 = off) [-1] */
+    int32_t debug_skip_phase;
+    int32_t reserved[8];
+} simdx_config;
+
+typedef struct simdx_graph simdx_graph;
+typedef struct simdx_server simdx_server;
+
+/* ------------------------------------------------------------------ misc */
+SIMDX_API const char *simdx_strerror(int status);
+SIMDX_API int simdx_version(void);
+
+/* Text of the last failing CUDA runtime call in this thread ("" if none);
+ * explains SIMDX_ECUDA / SIMDX_ENOMEM. */
+SIMDX_API const char *simdx_last_cuda_error(void);
+
+/* Default knob values. */
+SIMDX_API void simdx_config_default(simdx_config *cfg);
+
+/* Eq. 1 (Sec. 5): #CTA = floor(regs_per_sm / (regs_per_thread *
+ * threads_per_cta)) * n_sm.  Host arithmetic only (no GPU needed); the
+ * launches themselves use the CUDA occupancy calculator, which also counts
+ * shared memory and block limits.  Returns -1 on non-positive input. */
+SIMDX_API int64_t simdx_eq1_ctas(int64_t regs_per_sm, int64_t regs_per_thread,
+                       int64_t threads_per_cta, int64_t n_sm);
+
+/* ----------------------------------------------------------------- graph */
+/* Build a device-resident graph (Sec. 6 "Storage Format": CSR out-edges;
+ * CSC in-edges for directed graphs).
+ *   csr      out-neighbour CSR (required).
+ *   csc      in-neighbour CSR of a directed graph, or NULL for a symmetric
+ *            graph (the CSR is then used for both directions).
+ *   weights  uint32[e] in CSR order, or NULL (SSSP then fails EINVAL).
+ *   flags    SIMDX_INPUT_HOST, SIMDX_BORROW (not both).
+ *   stream   copies are issued on it; the call returns after they finish.
+ * Ownership: the library copies the arrays unless SIMDX_BORROW is given.
+ * Errors: EINVAL (NULL, n < 0, e != offsets[n] when checkable, bad
+ * offset_bits, n >= 2^31), ENOMEM, ECUDA.  *out is NULL on failure. */
+SIMDX_API int simdx_graph_create(const simdx_csr *csr, const simdx_csr *csc,
+                       const uint32_t *weights, uint32_t flags, void *stream,
+                       simdx_graph **out);
+SIMDX_API int simdx_graph_destroy(simdx_graph *g);
+
+/* Size, edge count and the persistent grid (CTAs) used by this graph. */
+SIMDX_API int simdx_graph_info(const simdx_graph *g, int64_t *n, int64_t *e,
+                     int32_t *grid_ctas, int32_t *threads_per_cta);
+
+/* Read / replace the tuning knobs (may reallocate the workspace). */
+SIMDX_API int simdx_graph_get_config(const simdx_graph *g, simdx_config *cfg);
+SIMDX_API int simdx_graph_set_config(simdx_graph *g, const simdx_config *cfg);
+
+/* Status of the last device run on this graph (synchronises `stream`). */
+SIMDX_API int simdx_graph_last_status(simdx_graph *g, void *stream);
+
+/* Per-iteration trace of the last run on this graph (synchronises `stream`).
+ * Each record is 4 int64: {direction(1 push, 2 pull) | filter << 8
+ * (1 online, 2 ballot), active vertices, active edges, bucket or level}.
+ * Writes up to `cap` records to host memory `rec` and returns the number
+ * of iterations of the run in *count. */
+SIMDX_API int simdx_graph_trace(simdx_graph *g, void *stream, int64_t *rec, int64_t cap,
+                      int64_t *count);
+
+/* ------------------------------------------------------------ algorithms */
+/* BFS (Sec. 6 "BFS"; voting combine, Sec. 3.2): levels[v] = hop distance
+ * from src, -1 if unreachable.  Push in the first and last levels, pull in
+ * between (Sec. 5).  levels: device int32[n].  Errors: EINVAL (src out of
+ * range, NULL levels). */
+SIMDX_API int simdx_bfs(simdx_graph *g, int32_t src, int32_t *levels, simdx_stats *stats,
+              void *stream);
+
+/* SSSP (Sec. 2.1, Sec. 3.3; aggregation combine = min): dist[v] = length
+ * of a shortest path from src with the graph's uint32 weights, UINT32_MAX
+ * if unreachable.  Delta-stepping: vertices whose distance changed and is
+ * below the current bucket bound are active (Sec. 3.3).  Path lengths must
+ * stay below UINT32_MAX.  dist: device uint32[n].  Errors: EINVAL (no
+ * weights, src out of range, NULL dist). */
+SIMDX_API int simdx_sssp(simdx_graph *g, int32_t src, uint32_t *dist, simdx_stats *stats,
+               void *stream);
+
+/* k-core (Sec. 6 "k-Core"): repeatedly deletes vertices of degree < k;
+ * in_core[v] = 1 for the vertices of the maximal subgraph whose minimum
+ * degree is >= k, else 0.  residual_deg[v] (optional, may be NULL) = number
+ * of in-core neighbours of an in-core v, 0 for deleted vertices.  Pull
+ * first, push later; a destination is no longer decremented once it is
+ * deleted (Sec. 7.1, k-Core).  Needs a symmetric graph.
+ * Errors: EINVAL (NULL in_core, directed graph). */
+SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
+                uint32_t *residual_deg, simdx_stats *stats, void *stream);
+
+/* PageRank (Sec. 6 "PageRank"; aggregation combine = sum, pull):
+ *   x_0 = 1/n;  x_{t+1}(v) = (1-d)/n + d*(sum_{u in N_in(v)} x_t(u)/outdeg(u)
+ *                                         + D_t/n),
+ * D_t = rank on out-degree-0 vertices.  Stops after the first iteration
+ * whose L1 change is < l1_tol, or after max_iter iterations.  FP32 ranks,
+ * FP32 per-vertex sums in a fixed order, FP64 global sums: results are
+ * identical run to run.  rank: device float[n].
+ * Errors: EINVAL (NULL rank, damping outside [0,1), max_iter < 0). */
+SIMDX_API int simdx_pagerank(simdx_graph *g, float damping, float l1_tol, int32_t max_iter,
+                   float *rank, simdx_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMDX_H */

@@ -9,12 +9,12 @@ Every function is a plain, single-threaded definition written from the paper
 (Liu & Huang, "SIMD-X: Programming and Processing of Graph Algorithms on
 GPUs"), cited per function in ``oracle.c``:
 
-* ``bfs``        -- Sec. 5 "BFS", FIFO-queue levels.
+* ``bfs``        -- Sec. 6 "BFS", FIFO-queue levels.
 * ``sssp``       -- Sec. 2.1 / Sec. 3.3, Dijkstra distances.
 * ``sssp_bsp``   -- Sec. 2.1, the per-iteration BSP relaxation narrative.
-* ``kcore``      -- Sec. 5 "k-Core", queue peeling (membership + residual degree).
+* ``kcore``      -- Sec. 6 "k-Core", queue peeling (membership + residual degree).
 * ``coreness``   -- Batagelj-Zaversnik core numbers (cross-check of ``kcore``).
-* ``pagerank``   -- Sec. 5 "PageRank", FP64 Jacobi pull iteration (readings of
+* ``pagerank``   -- Sec. 6 "PageRank", FP64 Jacobi pull iteration (readings of
                     the unstated teleport, dangling and stop rules: see the
                     function docstring).
 
@@ -135,7 +135,7 @@ def pagerank(in_off, in_idx, outdeg=None, d: float = 0.85, tol: float = 1e-6,
              max_iter: int = 1000, fixed_iter: int = -1):
     """FP64 Jacobi PageRank.
 
-    Readings of what the paper leaves unstated (Sec. 5 "PageRank" gives only
+    Readings of what the paper leaves unstated (Sec. 6 "PageRank" gives only
     "pull, sum, iterate until stable"): teleport (1-d)/n, start x_0 = 1/n,
     rank of out-degree-0 vertices spread uniformly over all vertices, stop
     after the first iteration whose L1 change is below `tol`.  For a

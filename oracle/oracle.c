@@ -9,17 +9,17 @@
  * shares no code, header or table with the CUDA path.
  *
  * Each function is the textbook definition of the result the paper's
- * iterative method reaches exactly (Sec. 5):
- *   - BFS levels (Sec. 5, "BFS"): FIFO-queue breadth-first search.
+ * iterative method reaches exactly (Sec. 6):
+ *   - BFS levels (Sec. 6, "BFS"): FIFO-queue breadth-first search.
  *   - SSSP distances (Sec. 2.1, Sec. 3.3): Dijkstra with a binary heap.
  *     The method (delta-stepping / frontier relaxation) reaches the same
  *     unique distances in any relaxation order.
- *   - k-core membership (Sec. 5, "k-Core"): repeatedly delete vertices of
+ *   - k-core membership (Sec. 6, "k-Core"): repeatedly delete vertices of
  *     degree < k; the remaining set is the unique maximal subgraph of
  *     minimum degree >= k.
  *   - Core numbers: Batagelj & Zaversnik, "An O(m) algorithm for cores
  *     decomposition of networks" (2003), as a cross-check of k-core.
- *   - PageRank (Sec. 5, "PageRank"): Jacobi power iteration in double
+ *   - PageRank (Sec. 6, "PageRank"): Jacobi power iteration in double
  *     precision, pulling contributions from in-neighbours and summing them.
  *   - The BSP frontier relaxation of Sec. 2.1 (Fig. 1 narrative): a vertex
  *     becomes active when its distance changed in the previous iteration.
@@ -35,7 +35,7 @@
 #define OR_EXPORT __attribute__((visibility("default")))
 
 /* ------------------------------------------------------------------ BFS */
-/* Sec. 5 "BFS": level by level from src; level(src) = 0. */
+/* Sec. 6 "BFS": level by level from src; level(src) = 0. */
 OR_EXPORT int or_bfs(int64_t n, const int64_t *off, const int32_t *idx,
                      int32_t src, int32_t *level)
 {
@@ -172,7 +172,7 @@ OR_EXPORT int64_t or_sssp_bsp(int64_t n, const int64_t *off, const int32_t *idx,
 }
 
 /* --------------------------------------------------------------- k-core */
-/* Sec. 5 "k-Core": delete every vertex whose degree is < k, updating the
+/* Sec. 6 "k-Core": delete every vertex whose degree is < k, updating the
  * degrees of its neighbours, until none is left to delete.  in_core[v] = 1
  * for survivors; resid[v] = number of surviving neighbours of a survivor,
  * 0 for deleted vertices. */
@@ -268,7 +268,7 @@ OR_EXPORT int or_coreness(int64_t n, const int64_t *off, const int32_t *idx,
 }
 
 /* ------------------------------------------------------------- PageRank */
-/* Sec. 5 "PageRank": pull the contributions x(u)/outdeg(u) of every
+/* Sec. 6 "PageRank": pull the contributions x(u)/outdeg(u) of every
  * in-neighbour u, sum them, and iterate until the ranks are stable.
  *   x_0(v)     = 1/n
  *   x_{t+1}(v) = (1-d)/n + d * ( sum_{u in N_in(v)} x_t(u)/outdeg(u) + D_t/n )

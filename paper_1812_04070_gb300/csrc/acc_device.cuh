@@ -1,0 +1,654 @@
+// acc_device.cuh -- device building blocks of the ACC hot path (sm_103a).
+//
+// One persistent cooperative kernel per algorithm call runs every BSP
+// iteration (Sec. 5, "Push-Pull based kernel fusion"; here all fusion, see
+// Table 2).  The pieces shared by all algorithms live here:
+//
+//   * grid_sync      -- software global barrier (Sec. 5, "Software global
+//                       barrier").  The grid is sized to co-residency from the
+//                       occupancy calculator (the Eq. 1 analogue) and launched
+//                       cooperatively, so the barrier cannot deadlock; every
+//                       wait is also bounded by a %globaltimer limit, after
+//                       which the run aborts with an error instead of hanging.
+//   * PhaseSlot ring -- per-phase reductions (active counts, list lengths,
+//                       overflow flag) folded into the barrier arrival.
+//   * online filter  -- during compute, updated vertices are recorded in
+//                       per-CTA bins of bounded capacity, one bin per degree
+//                       class (Sec. 4, "Online filter"; threshold 64 per
+//                       thread, "Overflow thresholds").  Bins are concatenated
+//                       into the next task lists before the barrier.
+//   * ballot filter  -- a coalesced scan of vertex metadata with warp ballots
+//                       that emits sorted, duplicate-free task lists
+//                       (Sec. 4, "Ballot filter"); used when a bin overflowed
+//                       (JIT control, Sec. 4).
+//   * class drivers  -- thread / warp / CTA work per small / medium / large
+//                       task (Sec. 4, "Classification"; Sec. 3.3), plus a
+//                       fourth class whose edges are split over the whole
+//                       grid for the very highest degrees.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace simdx {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kClasses = 4;  // 0 thread, 1 warp, 2 CTA, 3 grid
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBallotChunk = kThreads * 32;  // vertices per ballot-filter chunk
+
+// ------------------------------------------------------------ shared state
+struct PhaseSlot {
+  unsigned long long nact;      // vertices recorded for the next iteration
+  unsigned long long mact;      // their degree sum
+  unsigned long long aux0;      // algorithm-specific (u64 sum or min)
+  unsigned long long aux1;
+  unsigned long long aux2;
+  unsigned int list_cnt[kClasses];
+  unsigned int overflow;
+  unsigned int flag;
+};
+
+struct Sync {
+  unsigned long long arrive;    // monotonic barrier arrival counter
+  int abort;                    // a wait ran out somewhere
+  int err;                      // status code of the failure
+  unsigned long long evisit;    // edges read by compute (statistics)
+  PhaseSlot slot[3];
+};
+
+struct DevStats {
+  int status, iterations, push_iters, pull_iters, ballot_iters, online_iters, phases, grid;
+  long long edges_visited, frontier_sum;
+  double last_l1;
+};
+
+struct Knobs {
+  int small_max, med_max, huge_min;
+  int bin_cap;          // per CTA per class (threshold per thread * threads)
+  int direction;        // 0 auto, 1 push, 2 pull
+  int filter;           // 0 JIT, 2 ballot only
+  float alpha, beta, kalpha;
+  unsigned delta;
+  unsigned long long timeout_ns;
+  int skip_cta, skip_phase;
+};
+
+// Workspace shared by all algorithms of one graph.
+struct Work {
+  int32_t* bins;                 // [kClasses][grid][bin_cap]
+  int32_t* list[2][kClasses];    // double-buffered task lists
+  uint32_t* aux3[2];             // per-entry word of the class-3 lists (set to ~0 on append)
+  long long list_cap;
+  int32_t* chunk_cnt;            // [chunks][kClasses] for the deterministic ballot filter
+  uint32_t* bm_nz;               // vertices with an in-edge (pull candidates)
+  uint32_t* bm_vis;              // BFS visited
+  uint32_t* bm_f[2];             // BFS frontier bitmaps
+  void* state;                   // per-algorithm vertex state (12 bytes / vertex)
+  Sync* sync;
+  DevStats* stats;
+  long long* trace;              // [trace_cap][4]
+  int trace_cap;
+};
+
+// --------------------------------------------------------------- PTX bits
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Graph arrays are read-only for the whole kernel: non-coherent loads are safe
+// there (and only there; state written during the kernel uses plain loads).
+template <class T>
+__device__ __forceinline__ T gload(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ------------------------------------------------------------ grid barrier
+// Per-CTA shared bookkeeping of the persistent loop.
+struct CtaShared {
+  unsigned long long phase;  // barriers passed by this CTA
+  int ok;
+  int bincnt[kClasses];      // online-filter bin fill per class
+  int base[kClasses];
+  int wcnt[kClasses][kWarps];
+  unsigned long long red64[kWarps];
+  double redf[kWarps];
+  float redf32[kWarps];
+  int bcast_i[8];
+  unsigned long long bcast_u64[8];
+};
+
+// Every thread of every CTA calls this; returns false when the run aborted.
+// Arrival is one release-add per CTA; the CTA's writes are ordered before it
+// by __syncthreads + the release.  Waiting polls with acquire loads so the
+// data written before other CTAs' arrivals is visible afterwards.
+__device__ __forceinline__ bool grid_sync(Sync* s, unsigned grid, CtaShared& sh, const Knobs& k) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long ph = sh.phase + 1;
+    sh.phase = ph;
+    int ok = 1;
+    bool skip = (k.skip_cta == (int)blockIdx.x) && ((unsigned long long)k.skip_phase == ph);
+    if (!skip) red_release_add_u64(&s->arrive, 1ull);
+    const unsigned long long target = ph * (unsigned long long)grid;
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    while (ld_acquire_u64(&s->arrive) < target) {
+      if (ld_volatile_i32(&s->abort)) { ok = 0; break; }
+      if ((++spins & 63u) == 0) {
+        unsigned long long t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > k.timeout_ns) {
+          atomicExch(&s->abort, 1);
+          atomicCAS(&s->err, 0, 4 /* SIMDX_EBARRIER_TIMEOUT */);
+          ok = 0;
+          break;
+        }
+      }
+      __nanosleep(32);
+    }
+    if (ok && ld_volatile_i32(&s->abort)) ok = 0;
+    sh.ok = ok;
+  }
+  __syncthreads();
+  return sh.ok != 0;
+}
+
+__device__ __forceinline__ int slot_of(unsigned long long phase) { return (int)(phase % 3ull); }
+
+// Called once at the start of each phase by every CTA: CTA 0 clears the slot
+// that the NEXT phase will accumulate into (nobody reads or writes it now).
+__device__ __forceinline__ void clear_next_slot(Sync* s, const CtaShared& sh) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    PhaseSlot& z = s->slot[slot_of(sh.phase + 1)];
+    z.nact = 0; z.mact = 0; z.aux0 = 0; z.aux1 = 0; z.aux2 = 0;
+    for (int c = 0; c < kClasses; ++c) z.list_cnt[c] = 0;
+    z.overflow = 0; z.flag = 0;
+  }
+}
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f32(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_f64(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+// CTA-wide sum; result valid in every thread.  Fixed order (deterministic).
+__device__ __forceinline__ unsigned long long cta_sum_u64(unsigned long long v, CtaShared& sh) {
+  v = warp_sum_u64(v);
+  __syncthreads();
+  if (lane_id() == 0) sh.red64[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) t += sh.red64[w];
+  return t;
+}
+__device__ __forceinline__ float cta_sum_f32(float v, CtaShared& sh) {
+  v = warp_sum_f32(v);
+  __syncthreads();
+  if (lane_id() == 0) sh.redf32[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) t += sh.redf32[w];
+  return t;
+}
+__device__ __forceinline__ double cta_sum_f64(double v, CtaShared& sh) {
+  v = warp_sum_f64(v);
+  __syncthreads();
+  if (lane_id() == 0) sh.redf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) t += sh.redf[w];
+  return t;
+}
+
+// ----------------------------------------------------------- degree class
+__device__ __forceinline__ int degree_class(long long deg, const Knobs& k) {
+  return deg < k.small_max ? 0 : deg < k.med_max ? 1 : deg < k.huge_min ? 2 : 3;
+}
+
+// --------------------------------------------------------- online filter
+// Record vertex u of class cls in this CTA's bin.  Warp-aggregated with
+// __match_any_sync so one shared atomic serves all lanes of a class.  Entries
+// beyond the bin capacity are dropped; the overflow is detected at flush.
+__device__ __forceinline__ void online_record(int u, int cls, CtaShared& sh, const Work& w,
+                                              const Knobs& k, unsigned grid) {
+  unsigned mask = __activemask();
+  unsigned peers = __match_any_sync(mask, cls);
+  int leader = __ffs(peers) - 1;
+  int base = 0;
+  if ((int)lane_id() == leader) base = atomicAdd(&sh.bincnt[cls], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  int pos = base + __popc(peers & lanemask_lt());
+  if (pos < k.bin_cap)
+    w.bins[((size_t)cls * grid + blockIdx.x) * (size_t)k.bin_cap + pos] = u;
+}
+
+__device__ __forceinline__ void online_reset(CtaShared& sh) {
+  if (threadIdx.x < kClasses) sh.bincnt[threadIdx.x] = 0;
+}
+
+// Append this CTA's bins to the next task lists (prefix concatenation of the
+// thread bins, Sec. 3.3): one atomic per non-empty class reserves the CTA's
+// range.  Must be called by all threads of the CTA.
+__device__ __forceinline__ void online_flush(CtaShared& sh, const Work& w, const Knobs& k,
+                                             unsigned grid, int nbuf, PhaseSlot& slot) {
+  __syncthreads();
+  if (threadIdx.x < kClasses) {
+    int c = threadIdx.x;
+    int cnt = sh.bincnt[c];
+    if (cnt > k.bin_cap) {
+      atomicOr(&slot.overflow, 1u);
+      cnt = k.bin_cap;
+    }
+    int b = 0;
+    if (cnt > 0) {
+      b = (int)atomicAdd(&slot.list_cnt[c], (unsigned)cnt);
+      if ((long long)b + cnt > w.list_cap) { atomicOr(&slot.overflow, 1u); cnt = 0; }
+    }
+    sh.base[c] = b;
+    sh.wcnt[c][0] = cnt;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < kClasses; ++c) {
+    int cnt = sh.wcnt[c][0];
+    const int32_t* src = w.bins + ((size_t)c * grid + blockIdx.x) * (size_t)k.bin_cap;
+    int32_t* dst = w.list[nbuf][c] + sh.base[c];
+    for (int i = threadIdx.x; i < cnt; i += kThreads) {
+      dst[i] = src[i];
+      if (c == 3) w.aux3[nbuf][sh.base[c] + i] = 0xffffffffu;
+    }
+  }
+}
+
+// --------------------------------------------------------- ballot filter
+// Scan vertices [0, n) in chunks of kBallotChunk; pred(v) says whether v is
+// active and deg(v) its degree for the class.  Emits, per class, the active
+// vertices of each chunk in increasing order (sorted, unique) into
+// w.list[nbuf][c], reserving each chunk's range with one atomic per class.
+// `visit(v)` is called once for every selected vertex (by the thread that
+// writes it) so callers can fuse per-vertex side effects.
+template <class Pred, class Deg, class Visit>
+__device__ void ballot_filter(int n, Pred pred, Deg deg, Visit visit, CtaShared& sh, const Work& w,
+                              const Knobs& k, unsigned grid, int nbuf, PhaseSlot& slot) {
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  for (long long chunk = blockIdx.x; chunk * kBallotChunk < n; chunk += grid) {
+    const long long wbase = chunk * kBallotChunk + (long long)warp * 1024;
+    unsigned my[kClasses] = {0u, 0u, 0u, 0u};
+    for (int j = 0; j < 32; ++j) {
+      long long v = wbase + j * 32 + lane;
+      bool act = false;
+      int cls = 0;
+      if (v < n && pred((int)v)) {
+        act = true;
+        cls = degree_class(deg((int)v), k);
+      }
+#pragma unroll
+      for (int c = 0; c < kClasses; ++c) {
+        unsigned m = __ballot_sync(kFull, act && cls == c);
+        if (lane == j) my[c] = m;
+      }
+    }
+    // per-class exclusive prefix across lanes, then across warps
+    int pre[kClasses];
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      int x = __popc(my[c]);
+      int incl = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      pre[c] = incl - x;
+      if (lane == 31) sh.wcnt[c][warp] = incl;
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses) {
+      int c = threadIdx.x, run = 0;
+      for (int q = 0; q < kWarps; ++q) {
+        int t = sh.wcnt[c][q];
+        sh.wcnt[c][q] = run;
+        run += t;
+      }
+      int b = 0;
+      if (run > 0) b = (int)atomicAdd(&slot.list_cnt[c], (unsigned)run);
+      sh.base[c] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      unsigned m = my[c];
+      int pos = sh.base[c] + sh.wcnt[c][warp] + pre[c];
+      int32_t* dst = w.list[nbuf][c];
+      while (m) {
+        int b = __ffs(m) - 1;
+        m &= m - 1;
+        int v = (int)(wbase + lane * 32 + b);
+        if (c == 3) w.aux3[nbuf][pos] = 0xffffffffu;
+        dst[pos++] = v;
+        visit(v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Ballot filter whose active set is already a bitmap (one bit per vertex):
+// a lane owns one word, so no ballots are needed; output as above.
+template <class Deg, class Visit>
+__device__ void bitmap_filter(int n, const uint32_t* bm, Deg deg, Visit visit, CtaShared& sh,
+                              const Work& w, const Knobs& k, unsigned grid, int nbuf,
+                              PhaseSlot& slot) {
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const long long nwords = ((long long)n + 31) >> 5;
+  for (long long chunk = blockIdx.x; chunk * kBallotChunk < n; chunk += grid) {
+    const long long word = chunk * kThreads + (long long)warp * 32 + lane;  // 32 words per warp
+    unsigned all = word < nwords ? bm[word] : 0u;
+    unsigned my[kClasses] = {0u, 0u, 0u, 0u};
+    for (unsigned m = all; m;) {
+      int b = __ffs(m) - 1;
+      m &= m - 1;
+      int v = (int)(word * 32 + b);
+      my[degree_class(deg(v), k)] |= 1u << b;
+    }
+    int pre[kClasses];
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      int x = __popc(my[c]);
+      int incl = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      pre[c] = incl - x;
+      if (lane == 31) sh.wcnt[c][warp] = incl;
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses) {
+      int c = threadIdx.x, run = 0;
+      for (int q = 0; q < kWarps; ++q) {
+        int t = sh.wcnt[c][q];
+        sh.wcnt[c][q] = run;
+        run += t;
+      }
+      int b = 0;
+      if (run > 0) b = (int)atomicAdd(&slot.list_cnt[c], (unsigned)run);
+      sh.base[c] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      unsigned m = my[c];
+      int pos = sh.base[c] + sh.wcnt[c][warp] + pre[c];
+      int32_t* dst = w.list[nbuf][c];
+      while (m) {
+        int b = __ffs(m) - 1;
+        m &= m - 1;
+        int v = (int)(word * 32 + b);
+        if (c == 3) w.aux3[nbuf][pos] = 0xffffffffu;
+        dst[pos++] = v;
+        visit(v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------- push class driver
+// Visit every edge of every task in the four class lists.  F provides
+//   typename F::Src;                                 per-source state
+//   bool src(int v, Src& s, int cls, unsigned item); read state; false = skip
+//   void edge(const Src& s, int v, int u, long long p);
+// For cls 1 / 2 every lane / thread of the group calls src() and it must
+// return the same answer in all of them (F broadcasts).  Thread / warp / CTA
+// tasks follow Sec. 3.3; class 3 splits each vertex's edges evenly over all
+// CTAs (a GB300 addition for the highest degrees).
+template <class OffT, class F>
+__device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
+                             const int32_t* const* lists, const unsigned* cnt, unsigned grid,
+                             long long& evisit) {
+  const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  // class 3: grid-split
+  for (unsigned i = 0; i < cnt[3]; ++i) {
+    int v = lists[3][i];
+    long long beg = gload(off + v), end = gload(off + v + 1);
+    long long per = (end - beg + grid - 1) / grid;
+    long long s0 = beg + per * blockIdx.x, s1 = s0 + per < end ? s0 + per : end;
+    if (s1 <= s0) continue;
+    typename F::Src s;
+    if (!f.src(v, s, 3, i)) continue;
+    for (long long p = s0 + tid; p < s1; p += kThreads) f.edge(s, v, gload(idx + p), p);
+    if (tid == 0) evisit += s1 - s0;
+  }
+  // class 2: one CTA per task
+  for (unsigned i = blockIdx.x; i < cnt[2]; i += grid) {
+    int v = lists[2][i];
+    typename F::Src s;
+    if (!f.src(v, s, 2, i)) continue;
+    long long beg = gload(off + v), end = gload(off + v + 1);
+    for (long long p = beg + tid; p < end; p += kThreads) f.edge(s, v, gload(idx + p), p);
+    if (tid == 0) evisit += end - beg;
+  }
+  // class 1: one warp per task
+  const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
+  for (unsigned i = gw; i < cnt[1]; i += nw) {
+    int v = lists[1][i];
+    typename F::Src s;
+    if (!f.src(v, s, 1, i)) continue;
+    long long beg = gload(off + v), end = gload(off + v + 1);
+    for (long long p = beg + lane; p < end; p += 32) f.edge(s, v, gload(idx + p), p);
+    if (lane == 0) evisit += end - beg;
+  }
+  // class 0: one thread per task
+  const unsigned gt = blockIdx.x * kThreads + tid, nt = grid * kThreads;
+  for (unsigned i = gt; i < cnt[0]; i += nt) {
+    int v = lists[0][i];
+    typename F::Src s;
+    if (!f.src(v, s, 0, i)) continue;
+    long long beg = gload(off + v), end = gload(off + v + 1);
+#pragma unroll 4
+    for (long long p = beg; p < end; ++p) f.edge(s, v, gload(idx + p), p);
+    evisit += end - beg;
+  }
+}
+
+// ----------------------------------------------------- pull class driver
+// For every task u in the class lists, combine (sum) a per-edge value over
+// u's in-edges and hand the total to F:
+//   typename F::Acc;  Acc zero();  void edge(Acc&, int u, int v, long long p);
+//   void finish(int u, Acc total);   (called by exactly one thread per task)
+// Thread tasks sum serially in edge order; warp tasks sum lane-strided and
+// reduce with a fixed shuffle tree; CTA tasks (classes 2 and 3) reduce with
+// a fixed block tree.  The order of every sum is therefore fixed.
+template <class Acc>
+__device__ __forceinline__ Acc warp_sum(Acc v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <class OffT, class F>
+__device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const int32_t* const* lists,
+                             const unsigned* cnt, unsigned grid, typename F::Acc* red,
+                             long long& evisit) {
+  using Acc = typename F::Acc;
+  const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  for (int c = 3; c >= 2; --c) {
+    for (unsigned i = blockIdx.x; i < cnt[c]; i += grid) {
+      int u = lists[c][i];
+      long long beg = gload(off + u), end = gload(off + u + 1);
+      Acc a = f.zero();
+      for (long long p = beg + tid; p < end; p += kThreads) f.edge(a, u, gload(idx + p), p);
+      a = warp_sum(a);
+      __syncthreads();
+      if (lane == 0) red[warp] = a;
+      __syncthreads();
+      if (tid == 0) {
+        Acc t = f.zero();
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) t += red[q];
+        f.finish(u, t);
+        evisit += end - beg;
+      }
+    }
+  }
+  const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
+  for (unsigned i = gw; i < cnt[1]; i += nw) {
+    int u = lists[1][i];
+    long long beg = gload(off + u), end = gload(off + u + 1);
+    Acc a = f.zero();
+    for (long long p = beg + lane; p < end; p += 32) f.edge(a, u, gload(idx + p), p);
+    a = warp_sum(a);
+    if (lane == 0) {
+      f.finish(u, a);
+      evisit += end - beg;
+    }
+  }
+  const unsigned gt = blockIdx.x * kThreads + tid, nt = grid * kThreads;
+  for (unsigned i = gt; i < cnt[0]; i += nt) {
+    int u = lists[0][i];
+    long long beg = gload(off + u), end = gload(off + u + 1);
+    Acc a = f.zero();
+#pragma unroll 4
+    for (long long p = beg; p < end; ++p) f.edge(a, u, gload(idx + p), p);
+    f.finish(u, a);
+    evisit += end - beg;
+  }
+}
+
+// ------------------------------------- deterministic (two-pass) ballot filter
+// Same output as ballot_filter but globally sorted and identical run to run:
+// pass 1 counts each chunk's active vertices per class; after a grid barrier
+// pass 2 writes each chunk at the prefix of the counts of earlier chunks (the
+// prefix-scan concatenation of Sec. 3.3, no atomics).  The caller runs
+// count_pass, grid_sync, write_pass.
+template <class Pred, class Deg>
+__device__ void det_filter_count(int n, Pred pred, Deg deg, CtaShared& sh, const Work& w,
+                                 const Knobs& k, unsigned grid) {
+  for (long long chunk = blockIdx.x; chunk * kBallotChunk < n; chunk += grid) {
+    int my[kClasses] = {0, 0, 0, 0};
+    for (int j = threadIdx.x; j < kBallotChunk; j += kThreads) {
+      long long v = chunk * kBallotChunk + j;
+      if (v < n && pred((int)v)) my[degree_class(deg((int)v), k)]++;
+    }
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      int t = (int)cta_sum_u64((unsigned long long)my[c], sh);
+      if (threadIdx.x == 0) w.chunk_cnt[chunk * kClasses + c] = t;
+    }
+  }
+}
+
+template <class Pred, class Deg>
+__device__ void det_filter_write(int n, Pred pred, Deg deg, CtaShared& sh, const Work& w,
+                                 const Knobs& k, unsigned grid, int nbuf, unsigned* totals) {
+  const long long nchunks = ((long long)n + kBallotChunk - 1) / kBallotChunk;
+  // totals over all chunks (every CTA computes them; fixed order)
+#pragma unroll
+  for (int c = 0; c < kClasses; ++c) {
+    unsigned long long t = 0;
+    for (long long q = threadIdx.x; q < nchunks; q += kThreads) t += (unsigned)w.chunk_cnt[q * kClasses + c];
+    totals[c] = (unsigned)cta_sum_u64(t, sh);
+  }
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += grid) {
+    if (threadIdx.x < kClasses) sh.bcast_i[threadIdx.x] = 0;
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      unsigned long long t = 0;
+      for (long long q = threadIdx.x; q < chunk; q += kThreads) t += (unsigned)w.chunk_cnt[q * kClasses + c];
+      t = cta_sum_u64(t, sh);
+      if (threadIdx.x == 0) sh.base[c] = (int)t;
+    }
+    const long long wbase = chunk * kBallotChunk + (long long)warp * 1024;
+    unsigned my[kClasses] = {0u, 0u, 0u, 0u};
+    for (int j = 0; j < 32; ++j) {
+      long long v = wbase + j * 32 + lane;
+      bool act = false;
+      int cls = 0;
+      if (v < n && pred((int)v)) {
+        act = true;
+        cls = degree_class(deg((int)v), k);
+      }
+#pragma unroll
+      for (int c = 0; c < kClasses; ++c) {
+        unsigned m = __ballot_sync(kFull, act && cls == c);
+        if (lane == j) my[c] = m;
+      }
+    }
+    int pre[kClasses];
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      int x = __popc(my[c]);
+      int incl = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      pre[c] = incl - x;
+      if (lane == 31) sh.wcnt[c][warp] = incl;
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses) {
+      int c = threadIdx.x, run = 0;
+      for (int q = 0; q < kWarps; ++q) {
+        int t = sh.wcnt[c][q];
+        sh.wcnt[c][q] = run;
+        run += t;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+      unsigned m = my[c];
+      int pos = sh.base[c] + sh.wcnt[c][warp] + pre[c];
+      int32_t* dst = w.list[nbuf][c];
+      while (m) {
+        int b = __ffs(m) - 1;
+        m &= m - 1;
+        dst[pos++] = (int)(wbase + lane * 32 + b);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Write one trace record (CTA 0 thread 0 only).
+__device__ __forceinline__ void trace_put(const Work& w, int it, long long a, long long b,
+                                          long long c, long long d) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && it < w.trace_cap) {
+    long long* r = w.trace + 4ll * it;
+    r[0] = a; r[1] = b; r[2] = c; r[3] = d;
+  }
+}
+
+}  // namespace simdx

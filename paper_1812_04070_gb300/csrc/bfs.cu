@@ -1,0 +1,413 @@
+// bfs.cu -- BFS as one persistent ACC kernel (Sec. 6 "BFS"; voting combine,
+// Sec. 3.2).
+//
+// Active(v)   : level(v) == current level.
+// Compute     : push -- every frontier vertex offers level+1 to its
+//               out-neighbours; pull -- every unvisited vertex looks for one
+//               in-neighbour on the frontier and stops at the first hit
+//               (collaborative early termination, Sec. 3.3 "Comparison").
+// Combine     : vote.  All updates to a vertex carry the same value, so plain
+//               stores suffice (no atomics); the owner writes in pull.
+// Direction   : push in the first and last levels, pull in between (Sec. 5).
+//               The switch uses frontier edge / vertex counts folded into the
+//               grid barrier: pull when frontier edges exceed unexplored
+//               edges / alpha, back to push when the frontier holds fewer
+//               than n / beta vertices and shrinks.
+// Task lists  : online filter into degree-class bins during push and pull;
+//               on overflow (or when forced) the ballot filter rebuilds
+//               sorted, unique lists from the level array or the frontier
+//               bitmap (Sec. 4, JIT control).
+#include "simdx_internal.h"
+
+namespace simdx {
+
+enum { kPush = 1, kPull = 2 };
+enum { kOnline = 1, kBallot = 2 };
+
+template <class OffT>
+struct BfsArgs {
+  int n, src;
+  const OffT* off;
+  const int32_t* idx;
+  const OffT* ioff;
+  const int32_t* iidx;
+  int32_t* level;
+  long long m_total;
+  Work w;
+  Knobs k;
+};
+
+// The frontier bitmap is rewritten by other CTAs during the kernel, so it is
+// read with plain (coherent) loads, never through the non-coherent path.
+__device__ __forceinline__ bool bm_test(const uint32_t* bm, int v) {
+  return (bm[v >> 5] >> (v & 31)) & 1u;
+}
+
+// r-th (0-based) set bit of x.
+__device__ __forceinline__ int nth_set_bit(unsigned x, int r) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s; s >>= 1) {
+    unsigned lo = x & ((1u << s) - 1u);
+    int c = __popc(lo);
+    if (r >= c) {
+      r -= c;
+      x >>= s;
+      pos += s;
+    } else {
+      x = lo;
+    }
+  }
+  return pos;
+}
+
+template <class OffT>
+struct BfsPush {
+  struct Src {};
+  int32_t* level;
+  const OffT* off;
+  int next;
+  CtaShared& sh;
+  const Work& w;
+  const Knobs& k;
+  unsigned grid;
+  unsigned long long nrec = 0, mrec = 0;
+  __device__ BfsPush(int32_t* l, const OffT* o, int nx, CtaShared& s, const Work& ww, const Knobs& kk,
+                     unsigned g)
+      : level(l), off(o), next(nx), sh(s), w(ww), k(kk), grid(g) {}
+  __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
+  __device__ __forceinline__ void edge(const Src&, int, int u, long long) {
+    if (level[u] == -1) {
+      level[u] = next;  // vote: every writer stores the same value
+      long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
+      ++nrec;
+      mrec += (unsigned long long)d;
+      online_record(u, degree_class(d, k), sh, w, k, grid);
+    }
+  }
+};
+
+struct PullShared {
+  unsigned newbits[kWarps][32];
+  int defer_v[kWarps][32];
+  int defer_j[kWarps][32];
+};
+
+// One pull iteration over all unvisited vertices with an in-edge.  Each warp
+// takes 32 bitmap words, compacts their candidates and gives one candidate
+// to each lane; candidates with in-degree >= small_max are scanned by the
+// whole warp, 32 edges at a time, stopping at the first frontier hit.
+template <class OffT>
+__device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
+                         uint32_t* fbm_next, CtaShared& sh, PullShared& ps, unsigned grid,
+                         unsigned long long& nrec, unsigned long long& mrec, long long& evisit) {
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  const long long nwords = ((long long)a.n + 31) >> 5;
+  const int next = cur + 1;
+  for (long long g = (long long)blockIdx.x * kWarps + warp; g * 32 < nwords; g += (long long)grid * kWarps) {
+    const long long wid = g * 32 + lane;
+    unsigned vis = wid < nwords ? a.w.bm_vis[wid] : ~0u;
+    unsigned cand = wid < nwords ? (~vis & a.w.bm_nz[wid]) : 0u;
+    int c = __popc(cand);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    ps.newbits[warp][lane] = 0u;
+    __syncwarp();
+    for (int r = 0; r < total; r += 32) {
+      const int kk = r + lane;
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        int t = __shfl_sync(kFull, incl, j + step - 1);
+        if (t <= kk) j += step;
+      }
+      const int excl_j = __shfl_sync(kFull, incl - c, j);
+      const unsigned cand_j = __shfl_sync(kFull, cand, j);
+      bool deferred = false;
+      int u = -1, bit = 0;
+      if (kk < total) {
+        bit = nth_set_bit(cand_j, kk - excl_j);
+        u = (int)((g * 32 + j) * 32 + bit);
+        const long long beg = gload(a.ioff + u), end = gload(a.ioff + u + 1);
+        if (end - beg >= a.k.small_max) {
+          deferred = true;
+        } else {
+          bool found = false;
+          long long p = beg;
+          for (; p + 4 <= end && !found; p += 4) {
+            int v0 = gload(a.iidx + p), v1 = gload(a.iidx + p + 1), v2 = gload(a.iidx + p + 2),
+                v3 = gload(a.iidx + p + 3);
+            found = bm_test(fbm, v0) | bm_test(fbm, v1) | bm_test(fbm, v2) | bm_test(fbm, v3);
+          }
+          for (; p < end && !found; ++p) found = bm_test(fbm, gload(a.iidx + p));
+          evisit += (p < end ? p : end) - beg;
+          if (found) {
+            a.level[u] = next;
+            atomicOr(&ps.newbits[warp][j], 1u << bit);
+            long long od = (long long)gload(a.off + u + 1) - (long long)gload(a.off + u);
+            ++nrec;
+            mrec += (unsigned long long)od;
+            online_record(u, degree_class(od, a.k), sh, a.w, a.k, grid);
+          }
+        }
+      }
+      // warp-cooperative scan of the deferred (higher in-degree) candidates
+      const unsigned dm = __ballot_sync(kFull, deferred);
+      if (deferred) {
+        int slot = __popc(dm & lanemask_lt());
+        ps.defer_v[warp][slot] = u;
+        ps.defer_j[warp][slot] = (j << 5) | bit;
+      }
+      __syncwarp();
+      const int nd = __popc(dm);
+      for (int q = 0; q < nd; ++q) {
+        const int v = ps.defer_v[warp][q];
+        const long long beg = gload(a.ioff + v), end = gload(a.ioff + v + 1);
+        bool found = false;
+        long long seen = 0;
+        for (long long base = beg; base < end; base += 32) {
+          long long p = base + lane;
+          bool hit = p < end && bm_test(fbm, gload(a.iidx + p));
+          seen += 32;
+          if (__any_sync(kFull, hit)) {
+            found = true;
+            break;
+          }
+        }
+        if (lane == 0) evisit += seen < end - beg ? seen : end - beg;
+        if (found && lane == 0) {
+          a.level[v] = next;
+          const int jb = ps.defer_j[warp][q];
+          atomicOr(&ps.newbits[warp][jb >> 5], 1u << (jb & 31));
+          long long od = (long long)gload(a.off + v + 1) - (long long)gload(a.off + v);
+          ++nrec;
+          mrec += (unsigned long long)od;
+          online_record(v, degree_class(od, a.k), sh, a.w, a.k, grid);
+        }
+        __syncwarp();
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    if (wid < nwords) {
+      unsigned nb = ps.newbits[warp][lane];
+      fbm_next[wid] = nb;
+      if (nb) a.w.bm_vis[wid] = vis | nb;  // owner of the word
+    }
+    __syncwarp();
+  }
+}
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
+  __shared__ CtaShared sh;
+  __shared__ PullShared ps;
+  const unsigned grid = gridDim.x;
+  Sync* s = a.w.sync;
+  const Knobs& k = a.k;
+  const int n = a.n;
+  const long long nwords = ((long long)n + 31) >> 5;
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long gthreads = (long long)grid * kThreads;
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+
+  // ---- phase 0: reset levels and bitmaps; seed the first task list
+  for (long long v = gtid; v < n; v += gthreads) a.level[v] = (v == a.src) ? 0 : -1;
+  for (long long wd = gtid; wd < nwords; wd += gthreads) {
+    unsigned m = (wd == (a.src >> 5)) ? (1u << (a.src & 31)) : 0u;
+    a.w.bm_vis[wd] = m;
+    a.w.bm_f[0][wd] = m;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    long long d = (long long)a.off[a.src + 1] - (long long)a.off[a.src];
+    int c = degree_class(d, k);
+    a.w.list[0][c][0] = a.src;
+    s->slot[0].list_cnt[c] = 1;
+    s->slot[0].nact = 1;
+    s->slot[0].mact = (unsigned long long)d;
+  }
+  clear_next_slot(s, sh);
+  if (!grid_sync(s, grid, sh, k)) return;
+
+  // uniform loop state (identical in every CTA)
+  int L = 0;                 // level of the current frontier
+  int lbuf = 0, fb = 0;      // current list buffer / frontier bitmap
+  bool lists_ok = true;      // current task lists are valid
+  bool bm_ok = true;         // fbm[fb] and bm_vis are valid for level L
+  int prev_dir = kPush;
+  unsigned cnt[kClasses];
+  {
+    const PhaseSlot& p = s->slot[0];
+    for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+  }
+  unsigned long long n_f = 1, prev_n_f = 0, m_f = 0;
+  long long m_u = a.m_total;
+  {
+    long long d = (long long)a.off[a.src + 1] - (long long)a.off[a.src];
+    m_f = (unsigned long long)d;
+    m_u -= d;
+  }
+  int it = 0, push_it = 0, pull_it = 0, ballot_it = 0, online_it = 0;
+  long long evisit = 0, fsum = 0;
+
+  while (true) {
+    // -------- direction for this iteration
+    int dir;
+    if (k.direction == 1) dir = kPush;
+    else if (k.direction == 2) dir = kPull;
+    else if (prev_dir == kPush) dir = ((double)m_f > (double)m_u / k.alpha) ? kPull : kPush;
+    else dir = ((double)n_f < (double)n / k.beta && n_f <= prev_n_f) ? kPush : kPull;
+    int filt = kOnline;
+
+    // -------- make the frontier representation match the direction
+    if (dir == kPull && !bm_ok) {
+      // ballot scan of the level array: visited and frontier bitmaps
+      clear_next_slot(s, sh);
+      const int lane = lane_id();
+      const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+      for (long long wd = gw; wd < nwords; wd += (long long)grid * kWarps) {
+        long long v = wd * 32 + lane;
+        int lv = v < n ? a.level[v] : -1;
+        unsigned vis = __ballot_sync(kFull, lv != -1);
+        unsigned fr = __ballot_sync(kFull, lv == L);
+        if (lane == 0) {
+          a.w.bm_vis[wd] = vis;
+          a.w.bm_f[fb][wd] = fr;
+        }
+      }
+      if (!grid_sync(s, grid, sh, k)) return;
+      bm_ok = true;
+      filt = kBallot;
+    }
+    if (dir == kPush && (!lists_ok || k.filter == 2)) {
+      clear_next_slot(s, sh);
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      const OffT* off = a.off;
+      auto deg = [off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+      auto none = [](int) {};
+      if (bm_ok) {
+        bitmap_filter(n, a.w.bm_f[fb], deg, none, sh, a.w, k, grid, lbuf, slot);
+      } else {
+        const int32_t* lev = a.level;
+        const int LL = L;
+        auto pred = [lev, LL](int v) { return lev[v] == LL; };
+        ballot_filter(n, pred, deg, none, sh, a.w, k, grid, lbuf, slot);
+      }
+      if (!grid_sync(s, grid, sh, k)) return;
+      const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+      for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+      lists_ok = true;
+      filt = kBallot;
+    }
+
+    // -------- compute (push or pull) with the online filter recording
+    clear_next_slot(s, sh);
+    online_reset(sh);
+    __syncthreads();
+    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+    unsigned long long nrec = 0, mrec = 0;
+    if (dir == kPush) {
+      BfsPush<OffT> f(a.level, a.off, L + 1, sh, a.w, k, grid);
+      const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                        a.w.list[lbuf][3]};
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, evisit);
+      nrec = f.nrec;
+      mrec = f.mrec;
+      ++push_it;
+    } else {
+      bfs_pull<OffT>(a, L, a.w.bm_f[fb], a.w.bm_f[fb ^ 1], sh, ps, grid, nrec, mrec, evisit);
+      ++pull_it;
+    }
+    if (filt == kBallot || dir == kPull) ++ballot_it; else ++online_it;
+    online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
+    unsigned long long tn = cta_sum_u64(nrec, sh);
+    unsigned long long tm = cta_sum_u64(mrec, sh);
+    if (threadIdx.x == 0 && tn) {
+      atomicAdd(&slot.nact, tn);
+      atomicAdd(&slot.mact, tm);
+    }
+    if (!grid_sync(s, grid, sh, k)) return;
+
+    // -------- read the reductions of the compute phase
+    const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+    const unsigned long long nn = p.nact, mm = p.mact;
+    const bool ovf = p.overflow != 0;
+    trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, L);
+    fsum += (long long)n_f;
+    ++it;
+    if (nn == 0) break;
+    for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+    lists_ok = !ovf;
+    bm_ok = (dir == kPull);
+    if (dir == kPull) fb ^= 1;
+    lbuf ^= 1;
+    prev_dir = dir;
+    prev_n_f = n_f;
+    n_f = nn;
+    m_f = mm;
+    m_u -= (long long)mm;
+    ++L;
+  }
+  // statistics
+  unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+  if (!grid_sync(s, grid, sh, k)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats& st = *a.w.stats;
+    st.status = 0;
+    st.iterations = it;
+    st.push_iters = push_it;
+    st.pull_iters = pull_it;
+    st.ballot_iters = ballot_it;
+    st.online_iters = online_it;
+    st.phases = (int)sh.phase;
+    st.grid = (int)grid;
+    st.edges_visited = (long long)s->evisit;
+    st.frontier_sum = fsum;
+    st.last_l1 = 0.0;
+  }
+}
+
+const void* bfs_kernel_ptr(int off_bits) {
+  return off_bits == 32 ? (const void*)bfs_kernel<int32_t> : (const void*)bfs_kernel<long long>;
+}
+
+template <class OffT>
+static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* stats, cudaStream_t st) {
+  BfsArgs<OffT> a{};
+  a.n = (int)g->n;
+  a.src = src;
+  a.off = (const OffT*)g->off;
+  a.idx = g->idx;
+  a.ioff = (const OffT*)g->in_off;
+  a.iidx = g->in_idx;
+  a.level = levels;
+  a.m_total = g->e;
+  a.w = make_work(g);
+  a.k = make_knobs(g);
+  const void* kern = (const void*)bfs_kernel<OffT>;
+  int grid = grid_for(g, kern);
+  int rc = prepare_launch(g, st);
+  if (rc) return rc;
+  void* args[] = {&a};
+  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st);
+}
+
+}  // namespace simdx
+
+using namespace simdx;
+
+extern "C" int simdx_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* stats, void* stream) {
+  if (!g || !levels || src < 0 || src >= g->n) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return g->off_bits == 32 ? run_bfs<int32_t>(g, src, levels, stats, st)
+                           : run_bfs<long long>(g, src, levels, stats, st);
+}

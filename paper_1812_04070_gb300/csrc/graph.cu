@@ -1,0 +1,440 @@
+// graph.cu -- graph residency (Sec. 6, "Storage Format"), workspace, knobs,
+// launch helpers and the small host-only entry points of the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+
+#include "simdx_internal.h"
+
+namespace simdx {
+
+// Kernel handles of the algorithm translation units (for occupancy sizing).
+const void* bfs_kernel_ptr(int off_bits);
+const void* sssp_kernel_ptr(int off_bits);
+const void* kcore_kernel_ptr(int off_bits);
+const void* pagerank_kernel_ptr(int off_bits);
+
+static thread_local char g_last_cuda[256] = "";
+
+int cuda_status(cudaError_t e, const char* what) {
+  snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return SIMDX_ENOMEM;
+  return SIMDX_ECUDA;
+}
+
+Knobs make_knobs(const simdx_graph* g) {
+  const simdx_config& c = g->cfg;
+  Knobs k{};
+  k.small_max = c.small_max;
+  k.med_max = c.med_max;
+  k.huge_min = c.huge_min;
+  k.bin_cap = g->bin_cap;
+  k.direction = c.direction;
+  k.filter = c.filter;
+  k.alpha = c.alpha;
+  k.beta = c.beta;
+  k.kalpha = c.kcore_alpha;
+  k.delta = c.delta;
+  k.timeout_ns = (unsigned long long)(c.barrier_timeout_ms > 0 ? c.barrier_timeout_ms : 2000) * 1000000ull;
+  k.skip_cta = c.debug_skip_cta;
+  k.skip_phase = c.debug_skip_phase;
+  return k;
+}
+
+Work make_work(const simdx_graph* g) {
+  Work w{};
+  w.bins = g->bins;
+  w.list_cap = g->list_cap;
+  for (int b = 0; b < 2; ++b) {
+    for (int c = 0; c < kClasses; ++c)
+      w.list[b][c] = g->lists + ((size_t)b * kClasses + c) * (size_t)g->list_cap;
+    w.aux3[b] = g->aux3 + (size_t)b * (size_t)g->list_cap;
+  }
+  w.chunk_cnt = g->chunk_cnt;
+  long long words = (g->n + 31) / 32 + 1;
+  w.bm_nz = g->bitmaps;
+  w.bm_vis = g->bitmaps + words;
+  w.bm_f[0] = g->bitmaps + 2 * words;
+  w.bm_f[1] = g->bitmaps + 3 * words;
+  w.state = g->state;
+  w.sync = g->sync;
+  w.stats = g->dstats;
+  w.trace = g->trace;
+  w.trace_cap = g->trace_cap;
+  return w;
+}
+
+static std::mutex g_occ_mu;
+static std::unordered_map<const void*, int> g_occ;
+
+static int occupancy(const void* kernel) {
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  auto it = g_occ.find(kernel);
+  if (it != g_occ.end()) return it->second;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, kThreads, 0) != cudaSuccess) blocks = 0;
+  g_occ[kernel] = blocks;
+  return blocks;
+}
+
+int grid_for(const simdx_graph* g, const void* kernel) {
+  int per_sm = occupancy(kernel);
+  if (g->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, g->cfg.ctas_per_sm);
+  int grid = per_sm * g->num_sms;
+  return std::min(grid, g->grid_max);
+}
+
+int prepare_launch(simdx_graph* g, cudaStream_t st) {
+  SIMDX_CUDA(cudaMemsetAsync(g->sync, 0, sizeof(Sync), st));
+  SIMDX_CUDA(cudaMemsetAsync(g->dstats, 0, sizeof(DevStats), st));
+  return SIMDX_OK;
+}
+
+int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st) {
+  if (grid <= 0) return SIMDX_EUNSUPPORTED;
+  SIMDX_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kThreads), args, 0, st));
+  return SIMDX_OK;
+}
+
+struct PendingStats {
+  simdx_graph* g;
+  simdx_stats* user;
+};
+
+static void CUDART_CB stats_cb(void* p) {
+  PendingStats* ps = static_cast<PendingStats*>(p);
+  const DevStats& d = ps->g->h_stats->ds;
+  simdx_stats* u = ps->user;
+  std::memset(u, 0, sizeof(*u));
+  u->status = ps->g->h_stats->status();
+  u->iterations = d.iterations;
+  u->push_iters = d.push_iters;
+  u->pull_iters = d.pull_iters;
+  u->ballot_iters = d.ballot_iters;
+  u->online_iters = d.online_iters;
+  u->phases = d.phases;
+  u->grid_ctas = d.grid;
+  u->edges_visited = d.edges_visited;
+  u->frontier_sum = d.frontier_sum;
+  u->last_l1 = d.last_l1;
+  delete ps;
+}
+
+int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st) {
+  SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->ds, g->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+  SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->err, &g->sync->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (user) {
+    PendingStats* ps = new (std::nothrow) PendingStats{g, user};
+    if (!ps) return SIMDX_ENOMEM;
+    cudaError_t e = cudaLaunchHostFunc(st, stats_cb, ps);
+    if (e != cudaSuccess) {
+      delete ps;
+      return cuda_status(e, "cudaLaunchHostFunc");
+    }
+  }
+  return SIMDX_OK;
+}
+
+// ------------------------------------------------------------ validation
+// Checks a CSR on the device: offsets[0] = 0, non-decreasing, offsets[n] = e,
+// indices in [0, n).  Also builds the "has an in-edge" bitmap.
+template <class OffT>
+__global__ void validate_kernel(long long n, long long e, const OffT* off, const int32_t* idx,
+                                int* bad) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = tid; v < n; v += stride)
+    if (off[v + 1] < off[v]) atomicOr(bad, 1);
+  if (tid == 0 && (off[0] != 0 || (long long)off[n] != e)) atomicOr(bad, 2);
+  for (long long p = tid; p < e; p += stride) {
+    int32_t u = idx[p];
+    if (u < 0 || (long long)u >= n) atomicOr(bad, 4);
+  }
+}
+
+template <class OffT>
+__global__ void nonzero_bitmap_kernel(long long n, const OffT* off, uint32_t* bm) {
+  long long words = (n + 31) / 32;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long wd = tid; wd < words; wd += stride) {
+    uint32_t m = 0;
+    for (int b = 0; b < 32; ++b) {
+      long long v = wd * 32 + b;
+      if (v < n && off[v + 1] > off[v]) m |= 1u << b;
+    }
+    bm[wd] = m;
+  }
+}
+
+}  // namespace simdx
+
+using namespace simdx;
+
+extern "C" {
+
+const char* simdx_strerror(int s) {
+  switch (s) {
+    case SIMDX_OK: return "ok";
+    case SIMDX_EINVAL: return "invalid argument";
+    case SIMDX_ENOMEM: return "out of memory";
+    case SIMDX_ECUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+    case SIMDX_EBARRIER_TIMEOUT: return "grid barrier wait timed out";
+    case SIMDX_EUNSUPPORTED: return "unsupported";
+    case SIMDX_EBUSY: return "busy";
+    case SIMDX_ENOTREADY: return "not ready";
+    default: return "unknown status";
+  }
+}
+
+int simdx_version(void) { return 10000; }
+
+void simdx_config_default(simdx_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->small_max = 32;
+  c->med_max = 128;
+  c->huge_min = 16384;
+  c->bin_per_thread = 64;
+  c->direction = 0;
+  c->filter = 0;
+  c->alpha = 14.f;
+  c->beta = 24.f;
+  c->kcore_alpha = 8.f;
+  c->delta = 32;
+  c->ctas_per_sm = 0;
+  c->barrier_timeout_ms = 2000;
+  c->debug_skip_cta = -1;
+  c->debug_skip_phase = -1;
+}
+
+int64_t simdx_eq1_ctas(int64_t regs_per_sm, int64_t regs_per_thread, int64_t threads_per_cta,
+                       int64_t n_sm) {
+  if (regs_per_sm <= 0 || regs_per_thread <= 0 || threads_per_cta <= 0 || n_sm <= 0) return -1;
+  return (regs_per_sm / (regs_per_thread * threads_per_cta)) * n_sm;
+}
+
+static void free_workspace(simdx_graph* g) {
+  cudaFree(g->bins);
+  cudaFree(g->lists);
+  cudaFree(g->aux3);
+  g->bins = nullptr;
+  g->lists = nullptr;
+  g->aux3 = nullptr;
+}
+
+static int alloc_workspace(simdx_graph* g) {
+  free_workspace(g);
+  int per_sm = 0;
+  const void* ks[4] = {bfs_kernel_ptr(g->off_bits), sssp_kernel_ptr(g->off_bits),
+                       kcore_kernel_ptr(g->off_bits), pagerank_kernel_ptr(g->off_bits)};
+  for (const void* k : ks) per_sm = std::max(per_sm, occupancy(k));
+  if (per_sm <= 0) return SIMDX_ECUDA;
+  if (g->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, g->cfg.ctas_per_sm);
+  g->grid_max = per_sm * g->num_sms;
+  int bpt = std::max(0, g->cfg.bin_per_thread);
+  g->bin_cap = bpt * kThreads;
+  long long online_total = (long long)g->grid_max * g->bin_cap;
+  g->list_cap = std::max<long long>(g->n, online_total) + 64;
+  size_t bins_bytes = sizeof(int32_t) * (size_t)kClasses * g->grid_max * std::max(1, g->bin_cap);
+  size_t list_bytes = sizeof(int32_t) * (size_t)2 * kClasses * g->list_cap;
+  SIMDX_CUDA(cudaMalloc(&g->bins, bins_bytes));
+  SIMDX_CUDA(cudaMalloc(&g->lists, list_bytes));
+  SIMDX_CUDA(cudaMalloc(&g->aux3, sizeof(uint32_t) * 2 * (size_t)g->list_cap));
+  return SIMDX_OK;
+}
+
+int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_t* weights,
+                       uint32_t flags, void* stream, simdx_graph** out) {
+  if (!out) return SIMDX_EINVAL;
+  *out = nullptr;
+  if (!csr || csr->n < 0 || csr->n >= (1ll << 31) - 1 || csr->e < 0 ||
+      (csr->offset_bits != 32 && csr->offset_bits != 64) || !csr->offsets ||
+      (csr->e > 0 && !csr->indices))
+    return SIMDX_EINVAL;
+  if ((flags & SIMDX_INPUT_HOST) && (flags & SIMDX_BORROW)) return SIMDX_EINVAL;
+  if (csr->offset_bits == 32 && csr->e >= (1ll << 31)) return SIMDX_EINVAL;
+  if (csc && (csc->n != csr->n || csc->e != csr->e || csc->offset_bits != csr->offset_bits ||
+              !csc->offsets || (csc->e > 0 && !csc->indices)))
+    return SIMDX_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  simdx_graph* g = new (std::nothrow) simdx_graph();
+  if (!g) return SIMDX_ENOMEM;
+  simdx_config_default(&g->cfg);
+  g->n = csr->n;
+  g->e = csr->e;
+  g->off_bits = csr->offset_bits;
+  g->symmetric = (csc == nullptr);
+  g->borrowed = (flags & SIMDX_BORROW) != 0;
+  const bool host = (flags & SIMDX_INPUT_HOST) != 0;
+  size_t osz = (size_t)(g->off_bits / 8) * (size_t)(g->n + 1);
+  size_t isz = sizeof(int32_t) * (size_t)std::max<int64_t>(g->e, 1);
+  int rc = SIMDX_OK;
+  auto fail = [&](int r) {
+    simdx_graph_destroy(g);
+    return r;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&g->device)) != cudaSuccess) return fail(cuda_status(e, "cudaGetDevice"));
+  if ((e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device)) != cudaSuccess)
+    return fail(cuda_status(e, "cudaDeviceGetAttribute"));
+  auto place = [&](const void* src, size_t bytes, void** dst) -> int {
+    if (g->borrowed) {
+      *dst = const_cast<void*>(src);
+      return SIMDX_OK;
+    }
+    cudaError_t ee = cudaMalloc(dst, bytes);
+    if (ee != cudaSuccess) return cuda_status(ee, "cudaMalloc(graph)");
+    if (src && bytes) {
+      ee = cudaMemcpyAsync(*dst, src, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+      if (ee != cudaSuccess) return cuda_status(ee, "cudaMemcpyAsync(graph)");
+    }
+    return SIMDX_OK;
+  };
+  if ((rc = place(csr->offsets, osz, &g->off)) != SIMDX_OK) return fail(rc);
+  if ((rc = place(csr->indices, g->e ? isz : 0, (void**)&g->idx)) != SIMDX_OK) return fail(rc);
+  if (csc) {
+    if ((rc = place(csc->offsets, osz, &g->in_off)) != SIMDX_OK) return fail(rc);
+    if ((rc = place(csc->indices, g->e ? isz : 0, (void**)&g->in_idx)) != SIMDX_OK) return fail(rc);
+  } else {
+    g->in_off = g->off;
+    g->in_idx = g->idx;
+  }
+  if (weights) {
+    if ((rc = place(weights, sizeof(uint32_t) * (size_t)std::max<int64_t>(g->e, 1), (void**)&g->w)) != SIMDX_OK)
+      return fail(rc);
+  }
+  // validate on the device (also catches bad host input after the copy)
+  int* d_bad = nullptr;
+  if ((e = cudaMalloc(&d_bad, sizeof(int))) != cudaSuccess) return fail(cuda_status(e, "cudaMalloc"));
+  cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  int vblocks = std::max(1, std::min(4 * g->num_sms, (int)((g->e + g->n) / 256 + 1)));
+  const simdx_csr* parts[2] = {csr, csc};
+  for (int pi = 0; pi < 2; ++pi) {
+    if (!parts[pi]) continue;
+    void* o = pi == 0 ? g->off : g->in_off;
+    int32_t* ix = pi == 0 ? g->idx : g->in_idx;
+    if (g->off_bits == 32)
+      validate_kernel<int32_t><<<vblocks, 256, 0, st>>>(g->n, g->e, (const int32_t*)o, ix, d_bad);
+    else
+      validate_kernel<long long><<<vblocks, 256, 0, st>>>(g->n, g->e, (const long long*)o, ix, d_bad);
+  }
+  int h_bad = 0;
+  e = cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_bad);
+  if (e != cudaSuccess) return fail(cuda_status(e, "graph validation"));
+  if (h_bad) return fail(SIMDX_EINVAL);
+  // workspace
+  long long words = (g->n + 31) / 32 + 1;
+  if ((e = cudaMalloc(&g->bitmaps, sizeof(uint32_t) * 4 * (size_t)words)) != cudaSuccess)
+    return fail(cuda_status(e, "cudaMalloc(bitmaps)"));
+  cudaMemsetAsync(g->bitmaps, 0, sizeof(uint32_t) * 4 * (size_t)words, st);
+  if ((e = cudaMalloc(&g->state, 12 * (size_t)std::max<int64_t>(g->n, 1) + 64)) != cudaSuccess)
+    return fail(cuda_status(e, "cudaMalloc(state)"));
+  if ((e = cudaMalloc(&g->sync, sizeof(Sync))) != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(sync)"));
+  {
+    long long chunks = (g->n + kBallotChunk - 1) / kBallotChunk + 1;
+    if ((e = cudaMalloc(&g->chunk_cnt, sizeof(int32_t) * kClasses * (size_t)chunks)) != cudaSuccess)
+      return fail(cuda_status(e, "cudaMalloc(chunk_cnt)"));
+  }
+  if ((e = cudaMalloc(&g->dstats, sizeof(DevStats))) != cudaSuccess)
+    return fail(cuda_status(e, "cudaMalloc(stats)"));
+  cudaMemsetAsync(g->dstats, 0, sizeof(DevStats), st);
+  g->trace_cap = 1 << 16;
+  if ((e = cudaMalloc(&g->trace, sizeof(long long) * 4 * (size_t)g->trace_cap)) != cudaSuccess)
+    return fail(cuda_status(e, "cudaMalloc(trace)"));
+  if ((e = cudaHostAlloc(&g->h_stats, sizeof(HostStage), cudaHostAllocDefault)) != cudaSuccess)
+    return fail(cuda_status(e, "cudaHostAlloc"));
+  std::memset(g->h_stats, 0, sizeof(HostStage));
+  cudaMemsetAsync(g->sync, 0, sizeof(Sync), st);
+  if ((rc = alloc_workspace(g)) != SIMDX_OK) return fail(rc);
+  int nb = std::max(1, std::min(4 * g->num_sms, (int)(words / 256 + 1)));
+  if (g->off_bits == 32)
+    nonzero_bitmap_kernel<int32_t><<<nb, 256, 0, st>>>(g->n, (const int32_t*)g->in_off, g->bitmaps);
+  else
+    nonzero_bitmap_kernel<long long><<<nb, 256, 0, st>>>(g->n, (const long long*)g->in_off, g->bitmaps);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_status(e, "graph create"));
+  *out = g;
+  return SIMDX_OK;
+}
+
+int simdx_graph_destroy(simdx_graph* g) {
+  if (!g) return SIMDX_EINVAL;
+  cudaDeviceSynchronize();
+  if (!g->borrowed) {
+    cudaFree(g->off);
+    cudaFree(g->idx);
+    if (!g->symmetric) {
+      cudaFree(g->in_off);
+      cudaFree(g->in_idx);
+    }
+    cudaFree(g->w);
+  }
+  free_workspace(g);
+  cudaFree(g->bitmaps);
+  cudaFree(g->state);
+  cudaFree(g->sync);
+  cudaFree(g->chunk_cnt);
+  cudaFree(g->dstats);
+  cudaFree(g->trace);
+  if (g->h_stats) cudaFreeHost(g->h_stats);
+  delete g;
+  return SIMDX_OK;
+}
+
+int simdx_graph_info(const simdx_graph* g, int64_t* n, int64_t* e, int32_t* grid_ctas,
+                     int32_t* threads_per_cta) {
+  if (!g) return SIMDX_EINVAL;
+  if (n) *n = g->n;
+  if (e) *e = g->e;
+  if (grid_ctas) *grid_ctas = g->grid_max;
+  if (threads_per_cta) *threads_per_cta = kThreads;
+  return SIMDX_OK;
+}
+
+int simdx_graph_get_config(const simdx_graph* g, simdx_config* cfg) {
+  if (!g || !cfg) return SIMDX_EINVAL;
+  *cfg = g->cfg;
+  return SIMDX_OK;
+}
+
+int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
+  if (!g || !cfg) return SIMDX_EINVAL;
+  if (cfg->small_max < 1 || cfg->med_max < cfg->small_max || cfg->huge_min < cfg->med_max ||
+      cfg->bin_per_thread < 0 || cfg->bin_per_thread > 4096 || cfg->direction < 0 ||
+      cfg->direction > 2 || (cfg->filter != 0 && cfg->filter != 2) || !(cfg->alpha > 0.f) ||
+      !(cfg->beta > 0.f) || !(cfg->kcore_alpha > 0.f) || cfg->ctas_per_sm < 0)
+    return SIMDX_EINVAL;
+  bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm;
+  cudaDeviceSynchronize();
+  g->cfg = *cfg;
+  if (realloc_ws) return alloc_workspace(g);
+  return SIMDX_OK;
+}
+
+int simdx_graph_last_status(simdx_graph* g, void* stream) {
+  if (!g) return SIMDX_EINVAL;
+  SIMDX_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  return g->h_stats->status();
+}
+
+int simdx_graph_trace(simdx_graph* g, void* stream, int64_t* rec, int64_t cap, int64_t* count) {
+  if (!g || (cap > 0 && !rec)) return SIMDX_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SIMDX_CUDA(cudaStreamSynchronize(st));
+  int64_t it = g->h_stats->ds.iterations;
+  if (count) *count = it;
+  int64_t m = std::min<int64_t>(std::min<int64_t>(it, cap), g->trace_cap);
+  if (m > 0) SIMDX_CUDA(cudaMemcpy(rec, g->trace, sizeof(long long) * 4 * (size_t)m, cudaMemcpyDeviceToHost));
+  return SIMDX_OK;
+}
+
+const char* simdx_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

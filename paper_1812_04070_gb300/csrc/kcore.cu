@@ -1,0 +1,290 @@
+// kcore.cu -- k-core as one persistent ACC kernel (Sec. 6 "k-Core";
+// aggregation combine, Sec. 3.2).
+//
+// Iteration 0 deletes every vertex of degree < k (a ballot-filter scan of the
+// offsets: the degree is offsets[v+1] - offsets[v], no edges are read).
+// Iteration i then propagates the deletions of iteration i-1 (the frontier
+// R_{i-1}, removed_at == i-1):
+//   push : every frontier vertex decrements the degree of each still-alive
+//          neighbour; the decrement that takes a degree from k to k-1 deletes
+//          that neighbour (removed_at = i) and records it -- exactly one
+//          thread sees that transition, so lists carry no duplicates.  A
+//          deleted destination is no longer decremented (Sec. 7.1, k-Core).
+//   pull : every alive vertex recounts its neighbours alive at the start of
+//          the iteration (removed_at >= i) and is deleted if the count is < k;
+//          the owner writes, no atomics.
+// Pull runs while the deleted vertices carry many edges (the start), push
+// once they become few (Sec. 5: "k-Core conducts pull at the beginning while
+// push in the end"); the switch compares the frontier's edges with the alive
+// vertices' edges.
+#include <climits>
+
+#include "simdx_internal.h"
+
+namespace simdx {
+
+template <class OffT>
+struct KcoreArgs {
+  int n;
+  unsigned kk;
+  const OffT* off;
+  const int32_t* idx;
+  uint8_t* in_core;
+  uint32_t* resid;
+  Work w;
+  Knobs k;
+};
+
+template <class OffT>
+struct KcorePush {
+  struct Src {};
+  int32_t* removed_at;
+  uint32_t* cnt;
+  const OffT* off;
+  unsigned kk;
+  int it;
+  CtaShared& sh;
+  const Work& w;
+  const Knobs& k;
+  unsigned grid;
+  unsigned long long nrec = 0, mrec = 0;
+  __device__ KcorePush(int32_t* r, uint32_t* c, const OffT* o, unsigned kv, int i, CtaShared& s,
+                       const Work& ww, const Knobs& kn, unsigned g)
+      : removed_at(r), cnt(c), off(o), kk(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
+  __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
+  __device__ __forceinline__ void edge(const Src&, int, int u, long long) {
+    if (removed_at[u] != INT_MAX || cnt[u] < kk) return;  // stop once below k
+    const unsigned old = atomicSub(&cnt[u], 1u);
+    if (old == kk) {
+      removed_at[u] = it;
+      long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
+      ++nrec;
+      mrec += (unsigned long long)d;
+      online_record(u, degree_class(d, k), sh, w, k, grid);
+    }
+  }
+};
+
+template <class OffT>
+struct KcorePull {
+  using Acc = unsigned;
+  const int32_t* removed_at;
+  int32_t* removed_w;
+  uint32_t* cnt;
+  const OffT* off;
+  unsigned kk;
+  int it;
+  CtaShared& sh;
+  const Work& w;
+  const Knobs& k;
+  unsigned grid;
+  unsigned long long nrec = 0, mrec = 0;
+  __device__ KcorePull(int32_t* r, uint32_t* c, const OffT* o, unsigned kv, int i, CtaShared& s,
+                       const Work& ww, const Knobs& kn, unsigned g)
+      : removed_at(r), removed_w(r), cnt(c), off(o), kk(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
+  __device__ __forceinline__ Acc zero() const { return 0u; }
+  __device__ __forceinline__ void edge(Acc& a, int, int v, long long) { a += removed_at[v] >= it ? 1u : 0u; }
+  __device__ __forceinline__ void finish(int u, Acc c) {
+    cnt[u] = c;
+    if (c < kk) {
+      removed_w[u] = it;
+      long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
+      ++nrec;
+      mrec += (unsigned long long)d;
+      online_record(u, degree_class(d, k), sh, w, k, grid);
+    }
+  }
+};
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
+  __shared__ CtaShared sh;
+  __shared__ unsigned red_u32[kWarps];
+  const unsigned grid = gridDim.x;
+  Sync* s = a.w.sync;
+  const Knobs& k = a.k;
+  const int n = a.n;
+  const unsigned kk = a.kk;
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long gthreads = (long long)grid * kThreads;
+  int32_t* removed_at = reinterpret_cast<int32_t*>(a.w.state);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(removed_at + n);
+  const OffT* off = a.off;
+  auto deg = [off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+
+  // ---- phase 0: degrees, first deletions (ballot filter over the offsets)
+  int lbuf = 0;
+  {
+    clear_next_slot(s, sh);
+    PhaseSlot& slot = s->slot[0];
+    unsigned long long m_rm = 0, m_alive = 0, n_rm = 0;
+    auto pred = [&](int v) {
+      const long long d = deg(v);
+      cnt[v] = (uint32_t)d;
+      const bool rm = d < (long long)kk;
+      removed_at[v] = rm ? 0 : INT_MAX;
+      if (rm) { m_rm += d; ++n_rm; } else m_alive += d;
+      return rm;
+    };
+    auto none = [](int) {};
+    ballot_filter(n, pred, deg, none, sh, a.w, k, grid, lbuf, slot);
+    unsigned long long t0 = cta_sum_u64(n_rm, sh), t1 = cta_sum_u64(m_rm, sh), t2 = cta_sum_u64(m_alive, sh);
+    if (threadIdx.x == 0) {
+      atomicAdd(&slot.nact, t0);
+      atomicAdd(&slot.mact, t1);
+      atomicAdd(&slot.aux0, t2);
+    }
+  }
+  if (!grid_sync(s, grid, sh, k)) return;
+  unsigned cnt_l[kClasses];
+  unsigned long long n_f, m_f, m_alive;
+  {
+    const PhaseSlot& p = s->slot[0];
+    for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
+    n_f = p.nact;
+    m_f = p.mact;
+    m_alive = p.aux0;
+  }
+  bool lists_ok = true;
+  int it = 1, push_it = 0, pull_it = 0, ballot_it = 0, online_it = 0;
+  long long evisit = 0, fsum = (long long)n_f;
+  trace_put(a.w, 0, 2 | (2 << 8), (long long)n_f, (long long)m_f, 0);
+
+  while (n_f > 0) {
+    int dir;
+    if (k.direction == 1) dir = 1;
+    else if (k.direction == 2) dir = 2;
+    else dir = ((double)m_f > (double)m_alive / k.kalpha) ? 2 : 1;
+    int filt = 1;
+    if (dir == 1 && (!lists_ok || k.filter == 2)) {
+      // rebuild the frontier lists from the metadata
+      clear_next_slot(s, sh);
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      const int prev = it - 1;
+      auto pred = [=](int v) { return removed_at[v] == prev; };
+      auto none = [](int) {};
+      ballot_filter(n, pred, deg, none, sh, a.w, k, grid, lbuf, slot);
+      if (!grid_sync(s, grid, sh, k)) return;
+      const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+      for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
+      filt = 2;
+    }
+    if (dir == 2) {
+      // task lists of the alive vertices (ballot filter)
+      clear_next_slot(s, sh);
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      auto pred = [=](int v) { return removed_at[v] == INT_MAX; };
+      auto none = [](int) {};
+      ballot_filter(n, pred, deg, none, sh, a.w, k, grid, lbuf, slot);
+      if (!grid_sync(s, grid, sh, k)) return;
+      const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+      for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
+      filt = 2;
+    }
+    clear_next_slot(s, sh);
+    online_reset(sh);
+    __syncthreads();
+    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+    const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                      a.w.list[lbuf][3]};
+    unsigned long long nrec = 0, mrec = 0;
+    if (dir == 1) {
+      KcorePush<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, evisit);
+      nrec = f.nrec;
+      mrec = f.mrec;
+      ++push_it;
+    } else {
+      KcorePull<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
+      pull_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, red_u32, evisit);
+      nrec = f.nrec;
+      mrec = f.mrec;
+      ++pull_it;
+    }
+    if (filt == 2) ++ballot_it; else ++online_it;
+    online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
+    unsigned long long tn = cta_sum_u64(nrec, sh), tm = cta_sum_u64(mrec, sh);
+    if (threadIdx.x == 0 && tn) {
+      atomicAdd(&slot.nact, tn);
+      atomicAdd(&slot.mact, tm);
+    }
+    if (!grid_sync(s, grid, sh, k)) return;
+    const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+    trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, it);
+    for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
+    lists_ok = p.overflow == 0;
+    m_alive -= p.mact;
+    n_f = p.nact;
+    m_f = p.mact;
+    fsum += (long long)n_f;
+    lbuf ^= 1;
+    ++it;
+  }
+  // ---- outputs
+  for (long long v = gtid; v < n; v += gthreads) {
+    const bool in = removed_at[v] == INT_MAX;
+    a.in_core[v] = in ? 1 : 0;
+    if (a.resid) a.resid[v] = in ? cnt[v] : 0u;
+  }
+  unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+  if (!grid_sync(s, grid, sh, k)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats& st = *a.w.stats;
+    st.status = 0;
+    st.iterations = it;
+    st.push_iters = push_it;
+    st.pull_iters = pull_it;
+    st.ballot_iters = ballot_it + 1;
+    st.online_iters = online_it;
+    st.phases = (int)sh.phase;
+    st.grid = (int)grid;
+    st.edges_visited = (long long)s->evisit;
+    st.frontier_sum = fsum;
+    st.last_l1 = 0.0;
+  }
+}
+
+const void* kcore_kernel_ptr(int off_bits) {
+  return off_bits == 32 ? (const void*)kcore_kernel<int32_t> : (const void*)kcore_kernel<long long>;
+}
+
+template <class OffT>
+static int run_kcore(simdx_graph* g, uint32_t kk, uint8_t* in_core, uint32_t* resid, simdx_stats* stats,
+                     cudaStream_t st) {
+  KcoreArgs<OffT> a{};
+  a.n = (int)g->n;
+  a.kk = kk;
+  a.off = (const OffT*)g->off;
+  a.idx = g->idx;
+  a.in_core = in_core;
+  a.resid = resid;
+  a.w = make_work(g);
+  a.k = make_knobs(g);
+  const void* kern = (const void*)kcore_kernel<OffT>;
+  int grid = grid_for(g, kern);
+  int rc = prepare_launch(g, st);
+  if (rc) return rc;
+  void* args[] = {&a};
+  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st);
+}
+
+}  // namespace simdx
+
+using namespace simdx;
+
+extern "C" int simdx_kcore(simdx_graph* g, uint32_t k, uint8_t* in_core, uint32_t* residual_deg,
+                           simdx_stats* stats, void* stream) {
+  if (!g || !in_core || !g->symmetric) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g->n == 0) {
+    int rc = prepare_launch(g, st);
+    return rc ? rc : finish_launch(g, stats, st);
+  }
+  return g->off_bits == 32 ? run_kcore<int32_t>(g, k, in_core, residual_deg, stats, st)
+                           : run_kcore<long long>(g, k, in_core, residual_deg, stats, st);
+}

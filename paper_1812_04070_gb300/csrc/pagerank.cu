@@ -1,0 +1,206 @@
+// pagerank.cu -- PageRank as one persistent ACC kernel (Sec. 6 "PageRank";
+// aggregation combine = sum, pull, all vertices active).
+//
+//   x_0 = 1/n
+//   x_{t+1}(v) = (1-d)/n + d * ( sum_{u in N_in(v)} c_t(u) + D_t / n )
+//   c_t(u) = x_t(u) / outdeg(u)      (0 for outdeg 0)
+//   D_t    = sum of x_t over vertices with outdeg 0
+// stopping after the first iteration with ||x_{t+1} - x_t||_1 < tol.
+//
+// All vertices are active in every iteration, so the ballot filter runs once
+// (Sec. 4: PageRank needs the ballot filter exactly at the first iteration)
+// and its sorted task lists are reused.  Each vertex sums its in-neighbours'
+// contributions in FP32 in a fixed order (thread: edge order; warp / CTA:
+// lane-strided partial sums and a fixed tree).  The two global sums (L1 change
+// and dangling rank) are accumulated per CTA in FP64 and combined across CTAs
+// as 2^-60 fixed-point integers, whose sum does not depend on arrival order:
+// together with the deterministic lists this makes every run bit-identical.
+// One grid barrier per iteration: the sums of iteration t are read right
+// after its barrier, before iteration t+1 starts.
+#include "simdx_internal.h"
+
+namespace simdx {
+
+constexpr double kFix = 1152921504606846976.0;  // 2^60
+
+template <class OffT>
+struct PrArgs {
+  int n;
+  float d, tol;
+  int max_iter;
+  const OffT* off;   // out-edges (out-degree)
+  const OffT* ioff;  // in-edges
+  const int32_t* iidx;
+  float* rank;
+  Work w;
+  Knobs k;
+};
+
+template <class OffT>
+struct PrPull {
+  using Acc = float;
+  const float* cin;
+  float* cout;
+  const float* xold;
+  float* xnew;
+  const OffT* off;
+  float base, d, dn;
+  double l1 = 0.0, dang = 0.0;
+  __device__ __forceinline__ Acc zero() const { return 0.f; }
+  __device__ __forceinline__ void edge(Acc& a, int, int v, long long) { a += cin[v]; }
+  __device__ __forceinline__ void finish(int u, Acc sum) {
+    const float xn = base + d * (sum + dn);
+    xnew[u] = xn;
+    const long long od = (long long)gload(off + u + 1) - (long long)gload(off + u);
+    cout[u] = od > 0 ? xn / (float)od : 0.f;
+    if (od == 0) dang += (double)xn;
+    l1 += fabs((double)xn - (double)xold[u]);
+  }
+};
+
+__device__ __forceinline__ unsigned long long to_fix(double x) { return __double2ull_rn(x * kFix); }
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
+  __shared__ CtaShared sh;
+  __shared__ float red_f[kWarps];
+  const unsigned grid = gridDim.x;
+  Sync* s = a.w.sync;
+  const Knobs& k = a.k;
+  const int n = a.n;
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long gthreads = (long long)grid * kThreads;
+  float* xalt = reinterpret_cast<float*>(a.w.state);
+  float* cbuf[2] = {xalt + n, xalt + 2 * (size_t)n};
+  float* xbuf[2] = {a.rank, xalt};
+  const OffT* off = a.off;
+  const OffT* ioff = a.ioff;
+  auto indeg = [ioff](int v) { return (long long)gload(ioff + v + 1) - (long long)gload(ioff + v); };
+  auto all = [](int) { return true; };
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+
+  // ---- phase 0: x_0, c_0, D_0 and the per-chunk class counts
+  {
+    clear_next_slot(s, sh);
+    PhaseSlot& slot = s->slot[0];
+    const float x0 = 1.0f / (float)n;
+    double dang = 0.0;
+    for (long long v = gtid; v < n; v += gthreads) {
+      const long long od = (long long)gload(off + v + 1) - (long long)gload(off + v);
+      xbuf[0][v] = x0;
+      cbuf[0][v] = od > 0 ? x0 / (float)od : 0.f;
+      if (od == 0) dang += (double)x0;
+    }
+    dang = cta_sum_f64(dang, sh);
+    if (threadIdx.x == 0) atomicAdd(&slot.aux0, to_fix(dang));
+    det_filter_count(n, all, indeg, sh, a.w, k, grid);
+  }
+  if (!grid_sync(s, grid, sh, k)) return;
+  unsigned long long Dfix = s->slot[0].aux0;
+  // ---- phase 1: sorted task lists of all vertices by in-degree
+  unsigned cnt[kClasses];
+  clear_next_slot(s, sh);
+  det_filter_write(n, all, indeg, sh, a.w, k, grid, 0, cnt);
+  if (!grid_sync(s, grid, sh, k)) return;
+
+  const int32_t* lists[kClasses] = {a.w.list[0][0], a.w.list[0][1], a.w.list[0][2], a.w.list[0][3]};
+  const float base = (1.0f - a.d) / (float)n;
+  int t = 0;
+  double l1_last = 0.0;
+  long long evisit = 0;
+  while (true) {
+    if (t >= a.max_iter) break;
+    // ---- compute x_{t+1}
+    clear_next_slot(s, sh);
+    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+    PrPull<OffT> f;
+    f.cin = cbuf[t & 1];
+    f.cout = cbuf[(t + 1) & 1];
+    f.xold = xbuf[t & 1];
+    f.xnew = xbuf[(t + 1) & 1];
+    f.off = off;
+    f.base = base;
+    f.d = a.d;
+    f.dn = (float)(((double)Dfix / kFix) / (double)n);
+    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_f, evisit);
+    const double l1 = cta_sum_f64(f.l1, sh);
+    const double dg = cta_sum_f64(f.dang, sh);
+    if (threadIdx.x == 0) {
+      atomicAdd(&slot.aux0, to_fix(dg));
+      atomicAdd(&slot.aux1, to_fix(l1));
+    }
+    if (!grid_sync(s, grid, sh, k)) return;
+    const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+    Dfix = p.aux0;
+    l1_last = (double)p.aux1 / kFix;
+    trace_put(a.w, t, 2 | (2 << 8), n, 0, (long long)p.aux1);
+    ++t;
+    if (l1_last < (double)a.tol) break;
+  }
+  // ---- result: x_t lives in xbuf[t & 1]
+  if (t & 1)
+    for (long long v = gtid; v < n; v += gthreads) a.rank[v] = xalt[v];
+  unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+  if (!grid_sync(s, grid, sh, k)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats& st = *a.w.stats;
+    st.status = 0;
+    st.iterations = t;
+    st.push_iters = 0;
+    st.pull_iters = t;
+    st.ballot_iters = 1;
+    st.online_iters = 0;
+    st.phases = (int)sh.phase;
+    st.grid = (int)grid;
+    st.edges_visited = (long long)s->evisit;
+    st.frontier_sum = (long long)t * n;
+    st.last_l1 = l1_last;
+  }
+}
+
+const void* pagerank_kernel_ptr(int off_bits) {
+  return off_bits == 32 ? (const void*)pagerank_kernel<int32_t> : (const void*)pagerank_kernel<long long>;
+}
+
+template <class OffT>
+static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank, simdx_stats* stats,
+                  cudaStream_t st) {
+  PrArgs<OffT> a{};
+  a.n = (int)g->n;
+  a.d = d;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.off = (const OffT*)g->off;
+  a.ioff = (const OffT*)g->in_off;
+  a.iidx = g->in_idx;
+  a.rank = rank;
+  a.w = make_work(g);
+  a.k = make_knobs(g);
+  const void* kern = (const void*)pagerank_kernel<OffT>;
+  int grid = grid_for(g, kern);
+  int rc = prepare_launch(g, st);
+  if (rc) return rc;
+  void* args[] = {&a};
+  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st);
+}
+
+}  // namespace simdx
+
+using namespace simdx;
+
+extern "C" int simdx_pagerank(simdx_graph* g, float damping, float l1_tol, int32_t max_iter, float* rank,
+                              simdx_stats* stats, void* stream) {
+  if (!g || !rank || !(damping >= 0.f && damping < 1.f) || max_iter < 0 || !(l1_tol >= 0.f))
+    return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g->n == 0) {
+    int rc = prepare_launch(g, st);
+    return rc ? rc : finish_launch(g, stats, st);
+  }
+  return g->off_bits == 32 ? run_pr<int32_t>(g, damping, l1_tol, max_iter, rank, stats, st)
+                           : run_pr<long long>(g, damping, l1_tol, max_iter, rank, stats, st);
+}

@@ -1,0 +1,92 @@
+// simdx_internal.h -- host-side graph object, workspace and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/simdx.h"
+#include "acc_device.cuh"
+
+namespace simdx {
+// Pinned host copy of a run's statistics plus the barrier error word (an
+// aborted run never writes its statistics, so the error travels separately).
+struct HostStage {
+  DevStats ds;
+  int err;
+  int pad;
+  int status() const { return err ? err : ds.status; }
+};
+}  // namespace simdx
+
+struct simdx_graph {
+  int64_t n = 0, e = 0;
+  int off_bits = 64;
+  bool symmetric = true;
+  bool borrowed = false;
+  int device = 0;
+  int num_sms = 0;
+  // graph arrays (device)
+  void* off = nullptr;       // CSR offsets (int32 or int64)
+  int32_t* idx = nullptr;
+  void* in_off = nullptr;    // CSC offsets (== off when symmetric)
+  int32_t* in_idx = nullptr;
+  uint32_t* w = nullptr;
+  // knobs
+  simdx_config cfg{};
+  // workspace
+  int grid_max = 0;          // CTAs the workspace is sized for
+  int bin_cap = 0;           // entries per CTA per class
+  int32_t* bins = nullptr;
+  int32_t* lists = nullptr;  // [2][kClasses][list_cap]
+  uint32_t* aux3 = nullptr;  // [2][list_cap]
+  long long list_cap = 0;
+  int32_t* chunk_cnt = nullptr;
+  uint32_t* bitmaps = nullptr;  // [4][words]
+  void* state = nullptr;        // 12 bytes per vertex
+  simdx::Sync* sync = nullptr;
+  simdx::DevStats* dstats = nullptr;
+  long long* trace = nullptr;
+  int trace_cap = 0;
+  // host side
+  simdx::HostStage* h_stats = nullptr;  // pinned staging of the last run's statistics
+  struct Pending {
+    simdx_graph* g;
+    simdx_stats* user;
+  } pending[64];
+  unsigned pending_head = 0;
+  std::mutex mu;
+};
+
+namespace simdx {
+
+// Convert the public knobs into the device copy.
+Knobs make_knobs(const simdx_graph* g);
+
+// Workspace views for a launch of `grid` CTAs.
+Work make_work(const simdx_graph* g);
+
+// Occupancy-based grid (the Eq. 1 analogue): resident CTAs per SM times the
+// SM count, optionally clamped by cfg.ctas_per_sm.
+int grid_for(const simdx_graph* g, const void* kernel);
+
+// Reset the barrier/slot block and statistics before a launch.
+int prepare_launch(simdx_graph* g, cudaStream_t st);
+
+// Launch `kernel` cooperatively with `grid` CTAs of kThreads threads.
+int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st);
+
+// Enqueue the copy of device statistics into `user` (may be NULL).
+int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st);
+
+int cuda_status(cudaError_t e, const char* what);
+
+}  // namespace simdx
+
+#define SIMDX_CUDA(call)                                             \
+  do {                                                               \
+    cudaError_t _e = (call);                                         \
+    if (_e != cudaSuccess) return simdx::cuda_status(_e, #call);     \
+  } while (0)

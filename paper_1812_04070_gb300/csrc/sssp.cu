@@ -1,0 +1,330 @@
+// sssp.cu -- SSSP as one persistent ACC kernel (Sec. 2.1; Sec. 3.3 uses
+// SSSP as its running example; aggregation combine = min, Sec. 3.2).
+//
+// Active(v)  : v's distance changed since its out-edges were last relaxed
+//              (Sec. 3.2, "Active": metadata differs from the prior
+//              iteration).  pdist[v] holds the distance v's edges were last
+//              relaxed with, so "active" is dist[v] < pdist[v].
+// Delta-step : only active vertices below the bucket bound T are processed
+//              (Sec. 3.3, delta-step); when none is left, T advances by delta
+//              (or jumps to the bucket of the smallest pending distance).
+// Compute    : push: offer dist[v] + w(v,u) to every out-neighbour u.
+// Combine    : min.  In push the min lands with one atomicMin per improving
+//              edge (the one atomic of the path; Sec. 3.2 gives no
+//              atomic-free scheme for scattered aggregation).  Improved
+//              vertices below T go to the online-filter bins; every improved
+//              vertex gets its pending flag set (a plain byte store).
+// Task lists : online filter; on overflow the ballot filter rebuilds sorted
+//              lists from {pending and dist < pdist and dist < T}.
+// Grid class : a very-high-degree task is relaxed by all CTAs; they agree on
+//              one source distance through a per-entry "first reader wins"
+//              word, so pdist records a distance every slice really used.
+#include "simdx_internal.h"
+
+namespace simdx {
+
+template <class OffT>
+struct SsspArgs {
+  int n, src;
+  const OffT* off;
+  const int32_t* idx;
+  const uint32_t* wt;
+  uint32_t* dist;
+  Work w;
+  Knobs k;
+};
+
+template <class OffT>
+struct SsspPush {
+  struct Src {
+    uint32_t d;
+  };
+  uint32_t* dist;
+  uint32_t* pdist;
+  uint8_t* pend;
+  const OffT* off;
+  const uint32_t* wt;
+  uint32_t* aux3;
+  unsigned long long T;
+  CtaShared& sh;
+  const Work& w;
+  const Knobs& k;
+  unsigned grid;
+  unsigned long long nrec = 0, mrec = 0;
+  __device__ SsspPush(SsspArgs<OffT>& a, uint32_t* pd, uint8_t* pe, uint32_t* ax, unsigned long long t,
+                      CtaShared& s, unsigned g)
+      : dist(a.dist), pdist(pd), pend(pe), off(a.off), wt(a.wt), aux3(ax), T(t), sh(s), w(a.w), k(a.k),
+        grid(g) {}
+
+  // Decide once per task whether v still needs relaxing and with what d.
+  __device__ __forceinline__ bool claim(int v, uint32_t& d) {
+    d = dist[v];
+    if (d >= pdist[v]) return false;  // already relaxed with this or a better distance
+    pdist[v] = d;
+    return true;
+  }
+  __device__ __forceinline__ bool src(int v, Src& s, int cls, unsigned item) {
+    if (cls == 0) return claim(v, s.d);
+    if (cls == 1) {
+      uint32_t d = 0;
+      int go = 0;
+      if (lane_id() == 0) go = claim(v, d);
+      go = __shfl_sync(kFull, go, 0);
+      s.d = __shfl_sync(kFull, d, 0);
+      return go != 0;
+    }
+    if (cls == 2) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t d = 0;
+        sh.bcast_i[0] = claim(v, d);
+        sh.bcast_i[1] = (int)d;
+      }
+      __syncthreads();
+      s.d = (uint32_t)sh.bcast_i[1];
+      return sh.bcast_i[0] != 0;
+    }
+    // cls 3: all CTAs relax slices of v; the first CTA to look fixes d.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t mine = dist[v];
+      uint32_t old = atomicCAS(&aux3[item], 0xffffffffu, mine);
+      uint32_t d = (old == 0xffffffffu) ? mine : old;
+      if (d < pdist[v]) pdist[v] = d;  // benign: every CTA stores the agreed d
+      sh.bcast_i[1] = (int)d;
+    }
+    __syncthreads();
+    s.d = (uint32_t)sh.bcast_i[1];
+    return true;
+  }
+  __device__ __forceinline__ void edge(const Src& s, int, int u, long long p) {
+    const unsigned long long nd64 = (unsigned long long)s.d + gload(wt + p);
+    if (nd64 < dist[u]) {
+      const uint32_t nd = (uint32_t)nd64;
+      const uint32_t old = atomicMin(&dist[u], nd);
+      if (nd < old) {
+        pend[u] = 1;
+        if ((unsigned long long)nd < T) {
+          long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
+          ++nrec;
+          mrec += (unsigned long long)d;
+          online_record(u, degree_class(d, k), sh, w, k, grid);
+        }
+      }
+    }
+  }
+};
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
+  __shared__ CtaShared sh;
+  const unsigned grid = gridDim.x;
+  Sync* s = a.w.sync;
+  const Knobs& k = a.k;
+  const int n = a.n;
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long gthreads = (long long)grid * kThreads;
+  uint32_t* pdist = reinterpret_cast<uint32_t*>(a.w.state);
+  uint8_t* pend = reinterpret_cast<uint8_t*>(pdist + n);
+  const unsigned long long delta = k.delta ? k.delta : 0ull;
+  const unsigned long long kInfT = ~0ull;
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+
+  // ---- phase 0: reset state, seed the source
+  for (long long v = gtid; v < n; v += gthreads) {
+    a.dist[v] = (v == a.src) ? 0u : 0xffffffffu;
+    pdist[v] = 0xffffffffu;
+    pend[v] = (v == a.src) ? 1 : 0;  // the source is the first pending vertex
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    long long d = (long long)a.off[a.src + 1] - (long long)a.off[a.src];
+    int c = degree_class(d, k);
+    a.w.list[0][c][0] = a.src;
+    if (c == 3) a.w.aux3[0][0] = 0xffffffffu;
+    s->slot[0].list_cnt[c] = 1;
+  }
+  clear_next_slot(s, sh);
+  if (!grid_sync(s, grid, sh, k)) return;
+
+  unsigned long long T = delta ? delta : kInfT;  // bucket bound: process dist < T
+  int lbuf = 0;
+  unsigned cnt[kClasses];
+  bool lists_ok = true;
+  {
+    const PhaseSlot& p = s->slot[0];
+    for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+  }
+  int it = 0, ballot_it = 0, online_it = 0;
+  long long evisit = 0, fsum = 0;
+  int filt = 1;
+
+  while (true) {
+    unsigned total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    filt = 1;
+    if (!lists_ok || k.filter == 2) {
+      // ballot filter: near active vertices from the metadata
+      clear_next_slot(s, sh);
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      const unsigned long long TT = T;
+      uint32_t* dist = a.dist;
+      auto pred = [=](int v) {
+        if (!pend[v]) return false;
+        const uint32_t d = dist[v];
+        return d < pdist[v] && (unsigned long long)d < TT;
+      };
+      auto deg = [off = a.off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+      auto visit = [=](int v) { pend[v] = 0; };
+      ballot_filter(n, pred, deg, visit, sh, a.w, k, grid, lbuf, slot);
+      if (!grid_sync(s, grid, sh, k)) return;
+      const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+      for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+      total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+      lists_ok = true;
+      filt = 2;
+    }
+    if (total == 0) {
+      // bucket advance: one scan gives the min pending distance, the pending
+      // count and (guessing the next bucket) its task lists
+      bool done = false;
+      unsigned long long Tn = (T == kInfT) ? kInfT : T + delta;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        clear_next_slot(s, sh);
+        PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+        unsigned long long mymin = ~0ull, mycnt = 0;
+        const unsigned long long TT = Tn;
+        uint32_t* dist = a.dist;
+        auto pred = [&](int v) {
+          if (!pend[v]) return false;
+          const uint32_t d = dist[v];
+          if (d >= pdist[v]) {
+            pend[v] = 0;  // stale flag
+            return false;
+          }
+          ++mycnt;
+          if (d < mymin) mymin = d;
+          return (unsigned long long)d < TT;
+        };
+        auto deg = [off = a.off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+        auto visit = [=](int v) { pend[v] = 0; };
+        ballot_filter(n, pred, deg, visit, sh, a.w, k, grid, lbuf, slot);
+        unsigned long long c_cnt = cta_sum_u64(mycnt, sh);
+        // CTA min
+        {
+          unsigned long long m = mymin;
+          for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long y = __shfl_xor_sync(kFull, m, o);
+            m = y < m ? y : m;
+          }
+          __syncthreads();
+          if (lane_id() == 0) sh.red64[threadIdx.x >> 5] = m;
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            unsigned long long t = ~0ull;
+            for (int q = 0; q < kWarps; ++q) t = sh.red64[q] < t ? sh.red64[q] : t;
+            if (c_cnt) {
+              atomicAdd(&slot.aux1, c_cnt);
+              atomicMax(&slot.aux2, ~t);  // slots start at 0: keep the min inverted
+            }
+          }
+        }
+        if (!grid_sync(s, grid, sh, k)) return;
+        const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+        for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+        total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+        const unsigned long long pending = p.aux1;
+        if (pending == 0) {
+          done = true;
+          break;
+        }
+        T = Tn;
+        if (total > 0 || delta == 0) break;
+        // the guessed bucket was empty: jump to the bucket of the min distance
+        const unsigned long long mn = ~p.aux2;
+        Tn = (mn / delta + 1) * delta;
+      }
+      if (done) break;
+      filt = 2;
+      if (total == 0) continue;  // (cannot happen: the jump bucket holds the min)
+    }
+
+    // -------- compute: push relaxations from the current task lists
+    clear_next_slot(s, sh);
+    online_reset(sh);
+    __syncthreads();
+    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+    SsspPush<OffT> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
+    const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                      a.w.list[lbuf][3]};
+    push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, evisit);
+    online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
+    unsigned long long tn = cta_sum_u64(f.nrec, sh);
+    unsigned long long tm = cta_sum_u64(f.mrec, sh);
+    if (threadIdx.x == 0 && tn) {
+      atomicAdd(&slot.nact, tn);
+      atomicAdd(&slot.mact, tm);
+    }
+    if (filt == 2) ++ballot_it; else ++online_it;
+    if (!grid_sync(s, grid, sh, k)) return;
+    const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+    trace_put(a.w, it, 1 | (filt << 8), (long long)total, 0, (long long)(T == kInfT ? -1 : (long long)T));
+    fsum += total;
+    ++it;
+    for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+    lists_ok = p.overflow == 0;
+    lbuf ^= 1;
+  }
+  unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+  if (!grid_sync(s, grid, sh, k)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats& st = *a.w.stats;
+    st.status = 0;
+    st.iterations = it;
+    st.push_iters = it;
+    st.pull_iters = 0;
+    st.ballot_iters = ballot_it;
+    st.online_iters = online_it;
+    st.phases = (int)sh.phase;
+    st.grid = (int)grid;
+    st.edges_visited = (long long)s->evisit;
+    st.frontier_sum = fsum;
+    st.last_l1 = 0.0;
+  }
+}
+
+const void* sssp_kernel_ptr(int off_bits) {
+  return off_bits == 32 ? (const void*)sssp_kernel<int32_t> : (const void*)sssp_kernel<long long>;
+}
+
+template <class OffT>
+static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* stats, cudaStream_t st) {
+  SsspArgs<OffT> a{};
+  a.n = (int)g->n;
+  a.src = src;
+  a.off = (const OffT*)g->off;
+  a.idx = g->idx;
+  a.wt = g->w;
+  a.dist = dist;
+  a.w = make_work(g);
+  a.k = make_knobs(g);
+  const void* kern = (const void*)sssp_kernel<OffT>;
+  int grid = grid_for(g, kern);
+  int rc = prepare_launch(g, st);
+  if (rc) return rc;
+  void* args[] = {&a};
+  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st);
+}
+
+}  // namespace simdx
+
+using namespace simdx;
+
+extern "C" int simdx_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* stats, void* stream) {
+  if (!g || !dist || !g->w || src < 0 || src >= g->n) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return g->off_bits == 32 ? run_sssp<int32_t>(g, src, dist, stats, st)
+                           : run_sssp<long long>(g, src, dist, stats, st);
+}

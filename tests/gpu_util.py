@@ -1,0 +1,70 @@
+"""Helpers shared by the GPU parity tests (not collected as tests)."""
+from __future__ import annotations
+
+import numpy as np
+
+import graphgen as gg
+import oracle
+
+UNREACHED = np.uint32(0xFFFFFFFF)
+
+# Knob settings that force every path of the method (results must not change).
+FORCED = {
+    "default": {},
+    "push": dict(direction=1),
+    "pull": dict(direction=2),
+    "ballot": dict(filter=2),
+    "overflow": dict(bin_per_thread=0),
+    "tiny_bins": dict(bin_per_thread=1),
+    "all_classes": dict(small_max=2, med_max=4, huge_min=8),
+    "all_classes_pull": dict(small_max=2, med_max=4, huge_min=8, direction=2),
+    "all_classes_ballot": dict(small_max=2, med_max=4, huge_min=8, filter=2),
+    "one_cta_per_sm": dict(ctas_per_sm=1),
+}
+
+
+def small_graphs():
+    out = [gg.path(1), gg.path(2), gg.path(7), gg.star(9), gg.complete(6), gg.star(3000),
+           gg.path(3000), gg.complete(70), gg.grid(33, 17), gg.from_edges(10, [0, 1, 5, 6], [1, 2, 6, 7])]
+    for seed in range(4):
+        n = 50 + 300 * seed
+        out.append(gg.random_graph(n, int(1.3 * n), seed=100 + seed))
+        out.append(gg.random_graph(n, 6 * n, seed=200 + seed))
+    out += [gg.rmat(10), gg.rmat(12)]
+    return out
+
+
+def sources(g, k=3):
+    deg = g.degrees()
+    s = [0, g.n - 1]
+    if g.n > 2:
+        s.append(int(np.argmax(deg)))
+    if g.n > 4:
+        nz = np.nonzero(deg)[0]
+        if nz.size:
+            s.append(int(nz[len(nz) // 2]))
+    return sorted(set(x for x in s if 0 <= x < g.n))[:k + 1]
+
+
+def make(g, w=None, bits=64, **cfg):
+    from paper_1812_04070_gb300 import Graph
+    off = g.offsets if bits == 64 else g.offsets.astype(np.int32)
+    G = Graph(off, g.indices, weights=w)
+    if cfg:
+        G.set_config(**cfg)
+    return G
+
+
+def check_pagerank(G, g, d=0.85, tol=1e-6, max_iter=1000):
+    from paper_1812_04070_gb300 import simdx_stats
+    import torch
+    st = simdx_stats()
+    x = G.pagerank(d, tol, max_iter, stats=st)
+    torch.cuda.synchronize()
+    x = x.cpu().numpy().astype(np.float64)
+    t = st.iterations
+    ex, _, _ = oracle.pagerank(g.offsets, g.indices, d=d, fixed_iter=t)
+    denom = np.abs(ex).sum()
+    rel = np.abs(x - ex).sum() / denom if denom > 0 else 0.0
+    _, t_stop, _ = oracle.pagerank(g.offsets, g.indices, d=d, tol=tol, max_iter=max_iter)
+    return rel, t, t_stop, st

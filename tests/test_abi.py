@@ -1,0 +1,57 @@
+"""The C-ABI library loads and exports every symbol include/simdx.h declares;
+host-only entry points work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(simdx_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1812_04070_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_declarations():
+    from paper_1812_04070_gb300 import simdx
+    names = declared_functions()
+    assert set(names) <= set(simdx.SIGNATURES), set(names) - set(simdx.SIGNATURES)
+
+
+def test_eq1_worked_example(lib):
+    # Sec. 5, Eq. 1 worked example: 65,536 registers per SMX, 110 registers
+    # per thread, 128 threads per CTA, 15 SMX -> floor(4.65) * 15 = 60 CTAs.
+    from paper_1812_04070_gb300 import simdx
+    assert simdx.simdx_eq1_ctas(65536, 110, 128, 15) == 60
+    assert simdx.simdx_eq1_ctas(65536, 48, 128, 15) == 150
+    assert simdx.simdx_eq1_ctas(0, 1, 1, 1) == -1
+
+
+def test_host_only_calls(lib):
+    from paper_1812_04070_gb300 import simdx
+    assert simdx.simdx_strerror(simdx.EBARRIER_TIMEOUT) == "grid barrier wait timed out"
+    c = simdx.simdx_config_default()
+    assert (c.small_max, c.med_max, c.bin_per_thread) == (32, 128, 64)  # Sec. 4 defaults
+    assert simdx.simdx_version() >= 10000

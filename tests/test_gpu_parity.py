@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+BFS levels, SSSP distances and k-core membership / residual degrees are
+compared bit for bit; PageRank must be within 1e-6 relative L1 of the FP64
+oracle run for the same number of iterations, and stop within one
+iteration of the oracle's own stopping point.  Every forced path (push
+only, pull only, ballot filter only, online-filter overflow, every degree
+class, one CTA per SM) must give the same results.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from gpu_util import FORCED, check_pagerank, make, small_graphs, sources
+
+pytestmark = pytest.mark.gpu
+
+GRAPHS = small_graphs()
+GRAPH_IDS = [f"{i}:{g.name}" for i, g in enumerate(GRAPHS)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    import torch
+    from paper_1812_04070_gb300 import build
+    build()
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("mode", list(FORCED))
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_bfs(gi, mode):
+    g = GRAPHS[gi]
+    G = make(g, bits=32 if gi % 2 else 64, **FORCED[mode])
+    for s in sources(g):
+        lev = G.bfs(s).cpu().numpy()
+        assert np.array_equal(lev, oracle.bfs(g.offsets, g.indices, s)), (g.name, mode, s)
+    assert G.last_status() == 0
+    G.close()
+
+
+@pytest.mark.parametrize("mode", list(FORCED))
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_sssp(gi, mode):
+    g = GRAPHS[gi]
+    w = gg.weights(g, 77 + gi, 1, 64)
+    G = make(g, w, bits=64 if gi % 2 else 32, **FORCED[mode])
+    for s in sources(g):
+        d = G.sssp(s).cpu().numpy().view(np.uint32)
+        assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, s)), (g.name, mode, s)
+    G.close()
+
+
+@pytest.mark.parametrize("delta", [0, 1, 7, 64, 100000])
+def test_sssp_delta(delta):
+    g = gg.rmat(12)
+    w = gg.weights(g, 5, 1, 1000)
+    G = make(g, w, delta=delta)
+    for s in sources(g):
+        d = G.sssp(s).cpu().numpy().view(np.uint32)
+        assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, s))
+    G.close()
+
+
+@pytest.mark.parametrize("mode", ["default", "push", "pull", "ballot", "overflow", "all_classes",
+                                  "all_classes_pull", "one_cta_per_sm"])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_kcore(gi, mode):
+    g = GRAPHS[gi]
+    G = make(g, **FORCED[mode])
+    for k in (0, 1, 2, 3, 5, 16):
+        inc, res = G.kcore(k)
+        einc, eres = oracle.kcore(g.offsets, g.indices, k)
+        assert np.array_equal(inc.cpu().numpy(), einc), (g.name, mode, k)
+        assert np.array_equal(res.cpu().numpy().view(np.uint32), eres), (g.name, mode, k)
+    G.close()
+
+
+@pytest.mark.parametrize("mode", ["default", "all_classes", "one_cta_per_sm"])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_pagerank(gi, mode):
+    g = GRAPHS[gi]
+    G = make(g, **FORCED[mode])
+    rel, t, t_stop, st = check_pagerank(G, g)
+    assert rel <= 1e-6, (g.name, mode, rel)
+    assert abs(t - t_stop) <= 1, (t, t_stop)
+    G.close()
+
+
+def test_pagerank_deterministic_and_max_iter():
+    import torch
+    g = gg.rmat(13)
+    G = make(g)
+    a = G.pagerank().clone()
+    b = G.pagerank().clone()
+    assert torch.equal(a, b)
+    x0 = G.pagerank(max_iter=0).cpu().numpy()
+    assert np.all(x0 == np.float32(1.0 / g.n))
+    rel, t, _, _ = check_pagerank(G, g, max_iter=3)
+    assert t == 3 and rel <= 1e-6
+    G.close()
+
+
+def test_errors_and_validation():
+    from paper_1812_04070_gb300 import Graph, SimdxError
+    g = gg.path(5)
+    G = make(g)
+    with pytest.raises(SimdxError):
+        G.bfs(5)
+    with pytest.raises(SimdxError):
+        G.sssp(0)  # no weights
+    with pytest.raises(SimdxError):
+        G.set_config(med_max=1)
+    G.close()
+    bad = g.indices.copy()
+    bad[0] = 7  # out of range
+    with pytest.raises(SimdxError):
+        Graph(g.offsets, bad)
+    badoff = g.offsets.copy()
+    badoff[2] = badoff[3] + 1  # not monotone
+    with pytest.raises(SimdxError):
+        Graph(badoff, g.indices)
+
+
+def test_device_input_and_borrow():
+    import torch
+    from paper_1812_04070_gb300 import Graph
+    g = gg.rmat(11)
+    off = torch.from_numpy(g.offsets).cuda()
+    idx = torch.from_numpy(g.indices).cuda()
+    for borrow in (False, True):
+        G = Graph(off, idx, borrow=borrow)
+        assert np.array_equal(G.bfs(3).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 3))
+        G.close()
+
+
+def test_barrier_timeout_reports_error():
+    """A CTA that never arrives makes the others' bounded waits run out; the
+    run ends with SIMDX_EBARRIER_TIMEOUT and the context stays usable."""
+    from paper_1812_04070_gb300 import simdx, simdx_stats
+    import torch
+    g = gg.rmat(10)
+    G = make(g, debug_skip_cta=3, debug_skip_phase=2, barrier_timeout_ms=300)
+    st = simdx_stats()
+    G.bfs(0, stats=st)
+    torch.cuda.synchronize()
+    assert st.status == simdx.EBARRIER_TIMEOUT
+    assert G.last_status() == simdx.EBARRIER_TIMEOUT
+    G.set_config(debug_skip_cta=-1, debug_skip_phase=-1)
+    assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
+    assert G.last_status() == 0
+    G.close()
+
+
+def test_stats_and_trace():
+    from paper_1812_04070_gb300 import simdx_stats
+    import torch
+    g = gg.rmat(14)
+    G = make(g)
+    st = simdx_stats()
+    lev = G.bfs(0, stats=st).cpu().numpy()
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.iterations == lev.max() + 1
+    assert st.push_iters + st.pull_iters == st.iterations
+    assert st.pull_iters >= 1  # R-MAT from the hub switches to pull (Sec. 5)
+    tr = G.trace()
+    assert tr.shape[0] == st.iterations
+    assert list(tr[:, 3]) == list(range(st.iterations))
+    G.close()
