@@ -211,6 +211,32 @@ SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
 SIMDX_API int simdx_pagerank(simdx_graph *g, float damping, float l1_tol, int32_t max_iter,
                    float *rank, simdx_stats *stats, void *stream);
 
+/* ------------------------------------------------- no-allocation variant */
+/* BFS for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment convenience).  Some callers cannot call
+ * cudaMalloc: code running inside another runtime's memory pool or under a
+ * fixed memory budget, code that must not allocate while a CUDA graph is
+ * being captured elsewhere on the device, plugins whose host forbids
+ * allocation after start-up.  This entry point allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  All scratch (task
+ * lists, online-filter bins, bitmaps, barrier words) lives in one fixed
+ * device array of about 15 MB that every GPU loading the library holds until
+ * the process exits.
+ *   csr     device CSR of a symmetric graph (offsets int32/int64, indices
+ *           int32), 1 <= n <= 262144 (2^18) vertices; larger graphs fail
+ *           with SIMDX_EINVAL.  The CSR is checked first (synchronously).
+ *   src     source vertex; levels: device int32[n], written as simdx_bfs
+ *           writes it (hop distance, -1 if unreachable).
+ * The first call on a device looks up the scratch address on that device
+ * (the device must be current); make that first call before any stream
+ * capture.  Every call shares the one scratch array and it keeps the last
+ * call's contents: calls whose GPU work overlaps (different streams, no
+ * synchronisation) race and give wrong results, so serialise them.  Errors
+ * raised on the device during the traversal are not reported here; use
+ * simdx_bfs on a graph object when that matters. */
+SIMDX_API int simdx_bfs_noalloc(const simdx_csr *csr, int32_t src, int32_t *levels,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

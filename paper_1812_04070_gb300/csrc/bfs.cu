@@ -400,6 +400,26 @@ static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* st
   return finish_launch(g, stats, st);
 }
 
+// Launch the BFS kernel on caller-provided arrays and workspace views (no
+// graph object): used by entry points whose workspace is not library-owned
+// device memory.
+int bfs_launch_raw(int off_bits, int n, long long e, const void* off, const int32_t* idx, int src,
+                   int32_t* levels, const Work& w, const Knobs& k, int grid, cudaStream_t st) {
+  void* args[1];
+  if (off_bits == 32) {
+    BfsArgs<int32_t> a{};
+    a.n = n; a.src = src; a.off = (const int32_t*)off; a.idx = idx; a.ioff = a.off; a.iidx = idx;
+    a.level = levels; a.m_total = e; a.w = w; a.k = k;
+    args[0] = &a;
+    return launch_coop((const void*)bfs_kernel<int32_t>, grid, args, st);
+  }
+  BfsArgs<long long> a{};
+  a.n = n; a.src = src; a.off = (const long long*)off; a.idx = idx; a.ioff = a.off; a.iidx = idx;
+  a.level = levels; a.m_total = e; a.w = w; a.k = k;
+  args[0] = &a;
+  return launch_coop((const void*)bfs_kernel<long long>, grid, args, st);
+}
+
 }  // namespace simdx
 
 using namespace simdx;

@@ -80,6 +80,7 @@ SIGNATURES = {
     "simdx_sssp": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_kcore": (ctypes.c_int, [_vp, _u32, _vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_pagerank": (ctypes.c_int, [_vp, _f32, _f32, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
+    "simdx_bfs_noalloc": (ctypes.c_int, [ctypes.POINTER(simdx_csr), _i32, _vp, _vp]),
 }
 
 
@@ -189,3 +190,9 @@ def simdx_pagerank(g: int, damping: float, l1_tol: float, max_iter: int, rank_pt
                    stats: simdx_stats | None, stream: int | None) -> None:
     _check(_lib().simdx_pagerank(g, damping, l1_tol, max_iter, rank_ptr,
                                  ctypes.byref(stats) if stats is not None else None, stream), "simdx_pagerank")
+
+
+def simdx_bfs_noalloc(csr: simdx_csr, src: int, levels_ptr: int, stream: int | None) -> None:
+    """BFS that allocates no device memory (device CSR in, device levels out;
+    at most 2^18 vertices).  See include/simdx.h."""
+    _check(_lib().simdx_bfs_noalloc(ctypes.byref(csr), src, levels_ptr, stream), "simdx_bfs_noalloc")
