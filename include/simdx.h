@@ -98,8 +98,10 @@ typedef struct {
  * results. */
 typedef struct {
     int32_t small_max;       /* degree < small_max -> thread list [32]   (Sec. 4 "Classification") */
-    int32_t med_max;         /* degree < med_max   -> warp list   [128]  (Sec. 4) */
-    int32_t huge_min;        /* degree >= huge_min -> split over the grid [16384] */
+    int32_t med_max;         /* degree < med_max   -> warp list   [512]  (Sec. 4 finds this
+                                separator insensitive in [128, 2048]) */
+    int32_t huge_min;        /* degree >= huge_min -> cut into chunks of huge_min edges dealt
+                                round-robin over all CTAs; CTA list below [4096] */
     int32_t bin_per_thread;  /* online-filter overflow threshold per thread [64] (Sec. 4
                                 "Overflow thresholds"); 0 forces the ballot filter */
     int32_t direction;       /* 0 auto, 1 push only, 2 pull only [0] (Sec. 5) */
@@ -166,10 +168,11 @@ SIMDX_API int simdx_graph_set_config(simdx_graph *g, const simdx_config *cfg);
 SIMDX_API int simdx_graph_last_status(simdx_graph *g, void *stream);
 
 /* Per-iteration trace of the last run on this graph (synchronises `stream`).
- * Each record is 4 int64: {direction(1 push, 2 pull) | filter << 8
- * (1 online, 2 ballot), active vertices, active edges, bucket or level}.
- * Writes up to `cap` records to host memory `rec` and returns the number
- * of iterations of the run in *count. */
+ * Each record is 8 int64: {direction (1 push, 2 pull) | filter << 8
+ * (1 online, 2 ballot), active vertices, active edges, level / bucket bound,
+ * %globaltimer ns at the iteration's start and at its end (as seen by CTA 0),
+ * 0, 0}.  Writes up to `cap` records to host memory `rec` and returns the
+ * number of iterations of the run in *count. */
 SIMDX_API int simdx_graph_trace(simdx_graph *g, void *stream, int64_t *rec, int64_t cap,
                       int64_t *count);
 

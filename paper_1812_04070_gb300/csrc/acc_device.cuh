@@ -37,6 +37,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kClasses = 4;  // 0 thread, 1 warp, 2 CTA, 3 grid
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBallotChunk = kThreads * 32;  // vertices per ballot-filter chunk
+constexpr int kTraceWords = 8;                // int64 words per trace record
+constexpr int kChunkBatch = kThreads * 4;     // class-3 tasks per chunk-prefix batch
 
 // ------------------------------------------------------------ shared state
 struct PhaseSlot {
@@ -82,13 +84,15 @@ struct Work {
   uint32_t* aux3[2];             // per-entry word of the class-3 lists (set to ~0 on append)
   long long list_cap;
   int32_t* chunk_cnt;            // [chunks][kClasses] for the deterministic ballot filter
+  uint32_t* chunk_part;          // per-chunk partial sums of chunked pull tasks
+  int* chunk_done;               // [kChunkBatch] chunks finished per task (reset by the last)
   uint32_t* bm_nz;               // vertices with an in-edge (pull candidates)
   uint32_t* bm_vis;              // BFS visited
   uint32_t* bm_f[2];             // BFS frontier bitmaps
   void* state;                   // per-algorithm vertex state (12 bytes / vertex)
   Sync* sync;
   DevStats* stats;
-  long long* trace;              // [trace_cap][4]
+  long long* trace;              // [trace_cap][kTraceWords]
   int trace_cap;
 };
 
@@ -134,6 +138,8 @@ struct CtaShared {
   float redf32[kWarps];
   int bcast_i[8];
   unsigned long long bcast_u64[8];
+  int scan_w[kWarps];
+  int pref[kChunkBatch];     // inclusive prefix of chunk counts of a class-3 batch
 };
 
 // Every thread of every CTA calls this; returns false when the run aborted.
@@ -423,6 +429,58 @@ __device__ void bitmap_filter(int n, const uint32_t* bm, Deg deg, Visit visit, C
   }
 }
 
+// ------------------------------------------------------- chunked tasks
+// Inclusive prefix (in sh.pref) of the chunk counts ceil(deg / ch) of the nb
+// <= kChunkBatch class-3 tasks `items`.  All threads of the CTA call it.
+template <class OffT>
+__device__ void chunk_prefix(const int32_t* items, int nb, const OffT* off, long long ch, CtaShared& sh) {
+  __syncthreads();
+  const int b = threadIdx.x * 4;
+  int x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    x[q] = 0;
+    if (b + q < nb) {
+      const int v = items[b + q];
+      const long long d = gload(off + v + 1) - gload(off + v);
+      x[q] = (int)((d + ch - 1) / ch);
+    }
+  }
+  const int tot = x[0] + x[1] + x[2] + x[3];
+  int incl = tot;
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) sh.scan_w[warp] = incl;
+  __syncthreads();
+  int run = incl - tot;
+  for (int q = 0; q < warp; ++q) run += sh.scan_w[q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    run += x[q];
+    if (b + q < nb) sh.pref[b + q] = run;
+  }
+  __syncthreads();
+}
+
+// Task of chunk kc: the smallest i with pref[i] > kc.
+__device__ __forceinline__ int chunk_item(const int* pref, int nb, int kc) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (pref[mid] > kc) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ unsigned acc_bits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned acc_bits(unsigned x) { return x; }
+__device__ __forceinline__ void acc_from(unsigned b, float& x) { x = __uint_as_float(b); }
+__device__ __forceinline__ void acc_from(unsigned b, unsigned& x) { x = b; }
+
 // ----------------------------------------------------- push class driver
 // Visit every edge of every task in the four class lists.  F provides
 //   typename F::Src;                                 per-source state
@@ -435,19 +493,27 @@ __device__ void bitmap_filter(int n, const uint32_t* bm, Deg deg, Visit visit, C
 template <class OffT, class F>
 __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
                              const int32_t* const* lists, const unsigned* cnt, unsigned grid,
-                             long long& evisit) {
+                             long long ch, CtaShared& sh, long long& evisit) {
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-  // class 3: grid-split
-  for (unsigned i = 0; i < cnt[3]; ++i) {
-    int v = lists[3][i];
-    long long beg = gload(off + v), end = gload(off + v + 1);
-    long long per = (end - beg + grid - 1) / grid;
-    long long s0 = beg + per * blockIdx.x, s1 = s0 + per < end ? s0 + per : end;
-    if (s1 <= s0) continue;
-    typename F::Src s;
-    if (!f.src(v, s, 3, i)) continue;
-    for (long long p = s0 + tid; p < s1; p += kThreads) f.edge(s, v, gload(idx + p), p);
-    if (tid == 0) evisit += s1 - s0;
+  // class 3: every task is cut into chunks of `ch` edges and the chunks of
+  // all tasks are dealt round-robin to the CTAs (edge-balanced over the grid)
+  for (unsigned b0 = 0; b0 < cnt[3]; b0 += kChunkBatch) {
+    const int nb = (int)min((unsigned)kChunkBatch, cnt[3] - b0);
+    chunk_prefix(lists[3] + b0, nb, off, ch, sh);
+    const int total = sh.pref[nb - 1];
+    for (int kc = blockIdx.x; kc < total; kc += grid) {
+      const int item = chunk_item(sh.pref, nb, kc);
+      const int first = item ? sh.pref[item - 1] : 0;
+      const int v = lists[3][b0 + item];
+      const long long vb = gload(off + v), ve = gload(off + v + 1);
+      const long long beg = vb + (long long)(kc - first) * ch;
+      const long long end = beg + ch < ve ? beg + ch : ve;
+      typename F::Src s;
+      if (!f.src(v, s, 3, b0 + item)) continue;
+#pragma unroll 4
+      for (long long p = beg + tid; p < end; p += kThreads) f.edge(s, v, gload(idx + p), p);
+      if (tid == 0) evisit += end - beg;
+    }
   }
   // class 2: one CTA per task
   for (unsigned i = blockIdx.x; i < cnt[2]; i += grid) {
@@ -455,6 +521,7 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     typename F::Src s;
     if (!f.src(v, s, 2, i)) continue;
     long long beg = gload(off + v), end = gload(off + v + 1);
+#pragma unroll 4
     for (long long p = beg + tid; p < end; p += kThreads) f.edge(s, v, gload(idx + p), p);
     if (tid == 0) evisit += end - beg;
   }
@@ -465,19 +532,52 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     typename F::Src s;
     if (!f.src(v, s, 1, i)) continue;
     long long beg = gload(off + v), end = gload(off + v + 1);
+#pragma unroll 4
     for (long long p = beg + lane; p < end; p += 32) f.edge(s, v, gload(idx + p), p);
     if (lane == 0) evisit += end - beg;
   }
-  // class 0: one thread per task
-  const unsigned gt = blockIdx.x * kThreads + tid, nt = grid * kThreads;
-  for (unsigned i = gt; i < cnt[0]; i += nt) {
-    int v = lists[0][i];
-    typename F::Src s;
-    if (!f.src(v, s, 0, i)) continue;
-    long long beg = gload(off + v), end = gload(off + v + 1);
-#pragma unroll 4
-    for (long long p = beg; p < end; ++p) f.edge(s, v, gload(idx + p), p);
-    evisit += end - beg;
+  // class 0: one thread per task, but the edges of the warp's 32 tasks are
+  // walked together, 32 consecutive edge slots per round (coalesced loads,
+  // 32 independent loads in flight per warp); each slot finds its task by a
+  // binary search over the warp's inclusive degree scan.
+  for (unsigned base = (blockIdx.x * kWarps + warp) * 32u; base < cnt[0]; base += grid * kWarps * 32u) {
+    const unsigned i = base + lane;
+    int v = -1, deg = 0;
+    long long beg = 0;
+    typename F::Src s{};
+    if (i < cnt[0]) {
+      v = lists[0][i];
+      if (f.src(v, s, 0, i)) {
+        beg = gload(off + v);
+        deg = (int)(gload(off + v + 1) - beg);
+      }
+    }
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - deg;
+    for (int e0 = 0; e0 < total; e0 += 32) {
+      const int e = e0 + lane;
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        int t = __shfl_sync(kFull, incl, j + step - 1);
+        if (t <= e) j += step;
+      }
+      const long long bj = __shfl_sync(kFull, beg, j);
+      const int xj = __shfl_sync(kFull, excl, j);
+      const int vj = __shfl_sync(kFull, v, j);
+      const typename F::Src sj = F::shfl(s, j);
+      if (e < total) {
+        const long long p = bj + (e - xj);
+        f.edge(sj, vj, gload(idx + p), p);
+      }
+    }
+    evisit += deg;
   }
 }
 
@@ -498,15 +598,31 @@ __device__ __forceinline__ Acc warp_sum(Acc v) {
 
 template <class OffT, class F>
 __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const int32_t* const* lists,
-                             const unsigned* cnt, unsigned grid, typename F::Acc* red,
-                             long long& evisit) {
+                             const unsigned* cnt, unsigned grid, typename F::Acc* red, long long ch,
+                             CtaShared& sh, const Work& w, long long& evisit) {
   using Acc = typename F::Acc;
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-  for (int c = 3; c >= 2; --c) {
-    for (unsigned i = blockIdx.x; i < cnt[c]; i += grid) {
-      int u = lists[c][i];
-      long long beg = gload(off + u), end = gload(off + u + 1);
+  // class 3: chunks of `ch` edges dealt round-robin to the CTAs; each chunk's
+  // sum goes to chunk_part, and the CTA that finishes a task's last chunk adds
+  // the task's chunk sums in chunk order (fixed) and finishes the task.
+  // Partials and counters are indexed across batches (gbase, b0 + item): no
+  // barrier separates batches, so a finisher may still be reading while other
+  // CTAs work on the next batch.
+  long long gbase = 0;
+  for (unsigned b0 = 0; b0 < cnt[3]; b0 += kChunkBatch) {
+    const int nb = (int)min((unsigned)kChunkBatch, cnt[3] - b0);
+    chunk_prefix(lists[3] + b0, nb, off, ch, sh);
+    const int total = sh.pref[nb - 1];
+    for (int kc = blockIdx.x; kc < total; kc += grid) {
+      const int item = chunk_item(sh.pref, nb, kc);
+      const int first = item ? sh.pref[item - 1] : 0;
+      const int nch = sh.pref[item] - first;
+      const int u = lists[3][b0 + item];
+      const long long ub = gload(off + u), ue = gload(off + u + 1);
+      const long long beg = ub + (long long)(kc - first) * ch;
+      const long long end = beg + ch < ue ? beg + ch : ue;
       Acc a = f.zero();
+#pragma unroll 4
       for (long long p = beg + tid; p < end; p += kThreads) f.edge(a, u, gload(idx + p), p);
       a = warp_sum(a);
       __syncthreads();
@@ -516,9 +632,47 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
         Acc t = f.zero();
 #pragma unroll
         for (int q = 0; q < kWarps; ++q) t += red[q];
-        f.finish(u, t);
         evisit += end - beg;
+        if (nch == 1) {
+          f.finish(u, t);
+        } else {
+          w.chunk_part[gbase + kc] = acc_bits(t);
+          __threadfence();
+          const int done = atomicAdd(&w.chunk_done[b0 + item], 1);
+          if (done == nch - 1) {
+            __threadfence();
+            Acc tot = f.zero();
+            const volatile unsigned* part = w.chunk_part + gbase + first;
+            for (int j = 0; j < nch; ++j) {
+              Acc y;
+              acc_from(part[j], y);
+              tot += y;
+            }
+            w.chunk_done[b0 + item] = 0;
+            f.finish(u, tot);
+          }
+        }
       }
+    }
+    gbase += total;
+  }
+  // class 2: one CTA per task
+  for (unsigned i = blockIdx.x; i < cnt[2]; i += grid) {
+    int u = lists[2][i];
+    long long beg = gload(off + u), end = gload(off + u + 1);
+    Acc a = f.zero();
+#pragma unroll 4
+    for (long long p = beg + tid; p < end; p += kThreads) f.edge(a, u, gload(idx + p), p);
+    a = warp_sum(a);
+    __syncthreads();
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    if (tid == 0) {
+      Acc t = f.zero();
+#pragma unroll
+      for (int q = 0; q < kWarps; ++q) t += red[q];
+      f.finish(u, t);
+      evisit += end - beg;
     }
   }
   const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
@@ -526,6 +680,7 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
     int u = lists[1][i];
     long long beg = gload(off + u), end = gload(off + u + 1);
     Acc a = f.zero();
+#pragma unroll 4
     for (long long p = beg + lane; p < end; p += 32) f.edge(a, u, gload(idx + p), p);
     a = warp_sum(a);
     if (lane == 0) {
@@ -533,15 +688,63 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
       evisit += end - beg;
     }
   }
-  const unsigned gt = blockIdx.x * kThreads + tid, nt = grid * kThreads;
-  for (unsigned i = gt; i < cnt[0]; i += nt) {
-    int u = lists[0][i];
-    long long beg = gload(off + u), end = gload(off + u + 1);
-    Acc a = f.zero();
-#pragma unroll 4
-    for (long long p = beg; p < end; ++p) f.edge(a, u, gload(idx + p), p);
-    f.finish(u, a);
-    evisit += end - beg;
+  // class 0: the warp walks the edges of its 32 tasks together, 32 slots per
+  // round.  Within a round the slots of one task are contiguous; they are
+  // summed by a fixed shuffle tree (suffix sums toward the task's first slot)
+  // and that partial is added to the task's accumulator, held by the task's
+  // own lane.  The order of every sum depends only on the task list.
+  for (unsigned base = (blockIdx.x * kWarps + warp) * 32u; base < cnt[0]; base += grid * kWarps * 32u) {
+    const unsigned i = base + lane;
+    int u = -1, deg = 0;
+    long long beg = 0;
+    if (i < cnt[0]) {
+      u = lists[0][i];
+      beg = gload(off + u);
+      deg = (int)(gload(off + u + 1) - beg);
+    }
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - deg;
+    Acc acc = f.zero();
+    for (int e0 = 0; e0 < total; e0 += 32) {
+      const int e = e0 + lane;
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        int t = __shfl_sync(kFull, incl, j + step - 1);
+        if (t <= e) j += step;
+      }
+      const long long bj = __shfl_sync(kFull, beg, j);
+      const int xj = __shfl_sync(kFull, excl, j);
+      const int uj = __shfl_sync(kFull, u, j);
+      Acc val = f.zero();
+      if (e < total) {
+        const long long p = bj + (e - xj);
+        f.edge(val, uj, gload(idx + p), p);
+      } else {
+        j = 32;  // no task
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Acc y = __shfl_down_sync(kFull, val, d);
+        int jy = __shfl_down_sync(kFull, j, d);
+        if (lane + d < 32 && jy == j) val += y;
+      }
+      // the task's first slot in this round holds the round's partial
+      int h = excl - e0;
+      h = h < 0 ? 0 : (h > 31 ? 31 : h);
+      Acc part = __shfl_sync(kFull, val, h);
+      if (deg > 0 && excl < e0 + 32 && incl > e0) acc += part;
+    }
+    if (u >= 0) {
+      f.finish(u, acc);
+      evisit += deg;
+    }
   }
 }
 
@@ -642,12 +845,17 @@ __device__ void det_filter_write(int n, Pred pred, Deg deg, CtaShared& sh, const
   }
 }
 
-// Write one trace record (CTA 0 thread 0 only).
-__device__ __forceinline__ void trace_put(const Work& w, int it, long long a, long long b,
-                                          long long c, long long d) {
+// Write one trace record (CTA 0 thread 0 only): flags, active vertices,
+// active edges, level / bucket, and %globaltimer at the iteration's start and
+// end as seen by CTA 0.
+__device__ __forceinline__ void trace_put(const Work& w, int it, long long a, long long b, long long c,
+                                          long long d, unsigned long long t0 = 0) {
   if (blockIdx.x == 0 && threadIdx.x == 0 && it < w.trace_cap) {
-    long long* r = w.trace + 4ll * it;
+    long long* r = w.trace + (long long)kTraceWords * it;
     r[0] = a; r[1] = b; r[2] = c; r[3] = d;
+    r[4] = (long long)t0;
+    r[5] = (long long)globaltimer();
+    r[6] = 0; r[7] = 0;
   }
 }
 

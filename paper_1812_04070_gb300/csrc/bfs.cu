@@ -76,6 +76,7 @@ struct BfsPush {
                      unsigned g)
       : level(l), off(o), next(nx), sh(s), w(ww), k(kk), grid(g) {}
   __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
+  static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
   __device__ __forceinline__ void edge(const Src&, int, int u, long long) {
     if (level[u] == -1) {
       level[u] = next;  // vote: every writer stores the same value
@@ -100,6 +101,7 @@ struct PullShared {
 template <class OffT>
 __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
                          uint32_t* fbm_next, CtaShared& sh, PullShared& ps, unsigned grid,
+                         PhaseSlot& slot, int32_t* big, uint32_t* found,
                          unsigned long long& nrec, unsigned long long& mrec, long long& evisit) {
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   const long long nwords = ((long long)a.n + 31) >> 5;
@@ -134,7 +136,12 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
         bit = nth_set_bit(cand_j, kk - excl_j);
         u = (int)((g * 32 + j) * 32 + bit);
         const long long beg = gload(a.ioff + u), end = gload(a.ioff + u + 1);
-        if (end - beg >= a.k.small_max) {
+        if (end - beg >= a.k.huge_min) {
+          // scanned later by the whole grid (bfs_pull_big)
+          const unsigned pos = (unsigned)atomicAdd(&slot.aux2, 1ull);
+          big[pos] = u;
+          found[pos] = 0u;
+        } else if (end - beg >= a.k.small_max) {
           deferred = true;
         } else {
           bool found = false;
@@ -170,10 +177,14 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
         const long long beg = gload(a.ioff + v), end = gload(a.ioff + v + 1);
         bool found = false;
         long long seen = 0;
-        for (long long base = beg; base < end; base += 32) {
-          long long p = base + lane;
-          bool hit = p < end && bm_test(fbm, gload(a.iidx + p));
-          seen += 32;
+        for (long long base = beg; base < end; base += 128) {
+          bool hit = false;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const long long p = base + lane + 32 * q;
+            if (p < end) hit |= bm_test(fbm, gload(a.iidx + p));
+          }
+          seen += 128;
           if (__any_sync(kFull, hit)) {
             found = true;
             break;
@@ -200,6 +211,51 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
       if (nb) a.w.bm_vis[wid] = vis | nb;  // owner of the word
     }
     __syncwarp();
+  }
+}
+
+// Pull for the candidates of in-degree >= huge_min queued by bfs_pull: their
+// edges are cut into chunks of huge_min dealt round-robin over all CTAs; a
+// chunk is skipped once another chunk found a frontier in-neighbour.  The
+// words of the bitmaps were finished by their owners in the previous phase,
+// so the few bits set here use atomicOr.
+template <class OffT>
+__device__ void bfs_pull_big(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm, uint32_t* fbm_next,
+                             const int32_t* big, uint32_t* found, unsigned nbig, CtaShared& sh,
+                             unsigned grid, unsigned long long& nrec, unsigned long long& mrec,
+                             long long& evisit) {
+  const long long ch = a.k.huge_min;
+  for (unsigned b0 = 0; b0 < nbig; b0 += kChunkBatch) {
+    const int nb = (int)min((unsigned)kChunkBatch, nbig - b0);
+    chunk_prefix(big + b0, nb, a.ioff, ch, sh);
+    const int total = sh.pref[nb - 1];
+    for (int kc = blockIdx.x; kc < total; kc += grid) {
+      const int item = chunk_item(sh.pref, nb, kc);
+      const int first = item ? sh.pref[item - 1] : 0;
+      const int v = big[b0 + item];
+      if (threadIdx.x == 0) sh.bcast_i[0] = (int)*reinterpret_cast<volatile uint32_t*>(found + b0 + item);
+      __syncthreads();
+      const bool skip = sh.bcast_i[0] != 0;
+      __syncthreads();
+      if (skip) continue;
+      const long long vb = gload(a.ioff + v), ve = gload(a.ioff + v + 1);
+      const long long beg = vb + (long long)(kc - first) * ch;
+      const long long end = beg + ch < ve ? beg + ch : ve;
+      bool hit = false;
+#pragma unroll 4
+      for (long long p = beg + threadIdx.x; p < end; p += kThreads) hit |= bm_test(fbm, gload(a.iidx + p));
+      const bool any = __syncthreads_or(hit) != 0;
+      if (threadIdx.x == 0) {
+        evisit += end - beg;
+        if (any && atomicExch(found + b0 + item, 1u) == 0u) {
+          a.level[v] = cur + 1;
+          atomicOr(fbm_next + (v >> 5), 1u << (v & 31));
+          atomicOr(a.w.bm_vis + (v >> 5), 1u << (v & 31));
+          ++nrec;
+          mrec += (unsigned long long)(gload(a.off + v + 1) - gload(a.off + v));
+        }
+      }
+    }
   }
 }
 
@@ -257,6 +313,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   long long evisit = 0, fsum = 0;
 
   while (true) {
+    const unsigned long long t_it = globaltimer();
     // -------- direction for this iteration
     int dir;
     if (k.direction == 1) dir = kPush;
@@ -316,12 +373,13 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       BfsPush<OffT> f(a.level, a.off, L + 1, sh, a.w, k, grid);
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, evisit);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit);
       nrec = f.nrec;
       mrec = f.mrec;
       ++push_it;
     } else {
-      bfs_pull<OffT>(a, L, a.w.bm_f[fb], a.w.bm_f[fb ^ 1], sh, ps, grid, nrec, mrec, evisit);
+      bfs_pull<OffT>(a, L, a.w.bm_f[fb], a.w.bm_f[fb ^ 1], sh, ps, grid, slot, a.w.list[lbuf][3],
+                     a.w.aux3[lbuf], nrec, mrec, evisit);
       ++pull_it;
     }
     if (filt == kBallot || dir == kPull) ++ballot_it; else ++online_it;
@@ -336,13 +394,32 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
 
     // -------- read the reductions of the compute phase
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
-    const unsigned long long nn = p.nact, mm = p.mact;
-    const bool ovf = p.overflow != 0;
-    trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, L);
+    unsigned long long nn = p.nact, mm = p.mact;
+    bool ovf = p.overflow != 0;
+    for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+    const unsigned nbig = dir == kPull ? (unsigned)p.aux2 : 0u;
+    if (nbig > 0) {
+      // grid-wide pull of the high in-degree candidates
+      clear_next_slot(s, sh);
+      PhaseSlot& slot2 = s->slot[slot_of(sh.phase)];
+      unsigned long long nb2 = 0, mb2 = 0;
+      bfs_pull_big<OffT>(a, L, a.w.bm_f[fb], a.w.bm_f[fb ^ 1], a.w.list[lbuf][3], a.w.aux3[lbuf], nbig, sh,
+                         grid, nb2, mb2, evisit);
+      unsigned long long t0 = cta_sum_u64(nb2, sh), t1 = cta_sum_u64(mb2, sh);
+      if (threadIdx.x == 0 && t0) {
+        atomicAdd(&slot2.nact, t0);
+        atomicAdd(&slot2.mact, t1);
+      }
+      if (!grid_sync(s, grid, sh, k)) return;
+      const PhaseSlot& p2 = s->slot[slot_of(sh.phase - 1)];
+      if (p2.nact) ovf = true;  // vertices found here are not in the online lists
+      nn += p2.nact;
+      mm += p2.mact;
+    }
+    trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, L, t_it);
     fsum += (long long)n_f;
     ++it;
     if (nn == 0) break;
-    for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
     lists_ok = !ovf;
     bm_ok = (dir == kPull);
     if (dir == kPull) fb ^= 1;

@@ -56,6 +56,8 @@ Work make_work(const simdx_graph* g) {
     w.aux3[b] = g->aux3 + (size_t)b * (size_t)g->list_cap;
   }
   w.chunk_cnt = g->chunk_cnt;
+  w.chunk_part = g->chunk_part;
+  w.chunk_done = g->chunk_done;
   long long words = (g->n + 31) / 32 + 1;
   w.bm_nz = g->bitmaps;
   w.bm_vis = g->bitmaps + words;
@@ -91,6 +93,7 @@ int grid_for(const simdx_graph* g, const void* kernel) {
 
 int prepare_launch(simdx_graph* g, cudaStream_t st) {
   SIMDX_CUDA(cudaMemsetAsync(g->sync, 0, sizeof(Sync), st));
+  SIMDX_CUDA(cudaMemsetAsync(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16), st));
   SIMDX_CUDA(cudaMemsetAsync(g->dstats, 0, sizeof(DevStats), st));
   return SIMDX_OK;
 }
@@ -198,8 +201,8 @@ void simdx_config_default(simdx_config* c) {
   if (!c) return;
   std::memset(c, 0, sizeof(*c));
   c->small_max = 32;
-  c->med_max = 128;
-  c->huge_min = 16384;
+  c->med_max = 512;
+  c->huge_min = 4096;
   c->bin_per_thread = 64;
   c->direction = 0;
   c->filter = 0;
@@ -223,9 +226,13 @@ static void free_workspace(simdx_graph* g) {
   cudaFree(g->bins);
   cudaFree(g->lists);
   cudaFree(g->aux3);
+  cudaFree(g->chunk_part);
+  cudaFree(g->chunk_done);
   g->bins = nullptr;
   g->lists = nullptr;
   g->aux3 = nullptr;
+  g->chunk_part = nullptr;
+  g->chunk_done = nullptr;
 }
 
 static int alloc_workspace(simdx_graph* g) {
@@ -246,6 +253,12 @@ static int alloc_workspace(simdx_graph* g) {
   SIMDX_CUDA(cudaMalloc(&g->bins, bins_bytes));
   SIMDX_CUDA(cudaMalloc(&g->lists, list_bytes));
   SIMDX_CUDA(cudaMalloc(&g->aux3, sizeof(uint32_t) * 2 * (size_t)g->list_cap));
+  // chunked class-3 tasks: at most e / huge_min + (tasks) chunks per phase
+  const long long hm = std::max(1, g->cfg.huge_min);
+  const size_t parts = (size_t)(g->e / hm + g->n + 16);
+  SIMDX_CUDA(cudaMalloc(&g->chunk_part, sizeof(uint32_t) * parts));
+  SIMDX_CUDA(cudaMalloc(&g->chunk_done, sizeof(int) * (size_t)(g->n + 16)));
+  SIMDX_CUDA(cudaMemset(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16)));
   return SIMDX_OK;
 }
 
@@ -347,7 +360,7 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
     return fail(cuda_status(e, "cudaMalloc(stats)"));
   cudaMemsetAsync(g->dstats, 0, sizeof(DevStats), st);
   g->trace_cap = 1 << 16;
-  if ((e = cudaMalloc(&g->trace, sizeof(long long) * 4 * (size_t)g->trace_cap)) != cudaSuccess)
+  if ((e = cudaMalloc(&g->trace, sizeof(long long) * kTraceWords * (size_t)g->trace_cap)) != cudaSuccess)
     return fail(cuda_status(e, "cudaMalloc(trace)"));
   if ((e = cudaHostAlloc(&g->h_stats, sizeof(HostStage), cudaHostAllocDefault)) != cudaSuccess)
     return fail(cuda_status(e, "cudaHostAlloc"));
@@ -411,7 +424,8 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
       cfg->direction > 2 || (cfg->filter != 0 && cfg->filter != 2) || !(cfg->alpha > 0.f) ||
       !(cfg->beta > 0.f) || !(cfg->kcore_alpha > 0.f) || cfg->ctas_per_sm < 0)
     return SIMDX_EINVAL;
-  bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm;
+  bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
+                    cfg->huge_min != g->cfg.huge_min;
   cudaDeviceSynchronize();
   g->cfg = *cfg;
   if (realloc_ws) return alloc_workspace(g);
@@ -431,7 +445,8 @@ int simdx_graph_trace(simdx_graph* g, void* stream, int64_t* rec, int64_t cap, i
   int64_t it = g->h_stats->ds.iterations;
   if (count) *count = it;
   int64_t m = std::min<int64_t>(std::min<int64_t>(it, cap), g->trace_cap);
-  if (m > 0) SIMDX_CUDA(cudaMemcpy(rec, g->trace, sizeof(long long) * 4 * (size_t)m, cudaMemcpyDeviceToHost));
+  if (m > 0)
+    SIMDX_CUDA(cudaMemcpy(rec, g->trace, sizeof(long long) * kTraceWords * (size_t)m, cudaMemcpyDeviceToHost));
   return SIMDX_OK;
 }
 

@@ -52,6 +52,7 @@ struct KcorePush {
                        const Work& ww, const Knobs& kn, unsigned g)
       : removed_at(r), cnt(c), off(o), kk(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
   __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
+  static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
   __device__ __forceinline__ void edge(const Src&, int, int u, long long) {
     if (removed_at[u] != INT_MAX || cnt[u] < kk) return;  // stop once below k
     const unsigned old = atomicSub(&cnt[u], 1u);
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
   trace_put(a.w, 0, 2 | (2 << 8), (long long)n_f, (long long)m_f, 0);
 
   while (n_f > 0) {
+    const unsigned long long t_it = globaltimer();
     int dir;
     if (k.direction == 1) dir = 1;
     else if (k.direction == 2) dir = 2;
@@ -192,13 +194,13 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
     unsigned long long nrec = 0, mrec = 0;
     if (dir == 1) {
       KcorePush<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, evisit);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit);
       nrec = f.nrec;
       mrec = f.mrec;
       ++push_it;
     } else {
       KcorePull<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
-      pull_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, red_u32, evisit);
+      pull_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, red_u32, k.huge_min, sh, a.w, evisit);
       nrec = f.nrec;
       mrec = f.mrec;
       ++pull_it;
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
     }
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
-    trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, it);
+    trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, it, t_it);
     for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
     lists_ok = p.overflow == 0;
     m_alive -= p.mact;

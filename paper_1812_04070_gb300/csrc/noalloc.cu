@@ -42,7 +42,7 @@ constexpr size_t kOffSync = 0;
 constexpr size_t kOffStats = align256(kOffSync + sizeof(Sync));
 constexpr size_t kOffBad = align256(kOffStats + sizeof(DevStats));
 constexpr size_t kOffTrace = align256(kOffBad + sizeof(int));
-constexpr size_t kOffBitmaps = align256(kOffTrace + sizeof(long long) * 4 * kTraceCap);
+constexpr size_t kOffBitmaps = align256(kOffTrace + sizeof(long long) * kTraceWords * kTraceCap);
 constexpr size_t kOffBins = align256(kOffBitmaps + sizeof(uint32_t) * 4 * kWords);
 constexpr size_t kOffLists = align256(kOffBins + sizeof(int32_t) * kClasses * (size_t)kMaxGrid * kBinCap);
 constexpr size_t kOffAux3 = align256(kOffLists + sizeof(int32_t) * 2 * kClasses * (size_t)kListCap);

@@ -10,11 +10,12 @@
 // All vertices are active in every iteration, so the ballot filter runs once
 // (Sec. 4: PageRank needs the ballot filter exactly at the first iteration)
 // and its sorted task lists are reused.  Each vertex sums its in-neighbours'
-// contributions in FP32 in a fixed order (thread: edge order; warp / CTA:
-// lane-strided partial sums and a fixed tree).  The two global sums (L1 change
-// and dangling rank) are accumulated per CTA in FP64 and combined across CTAs
-// as 2^-60 fixed-point integers, whose sum does not depend on arrival order:
-// together with the deterministic lists this makes every run bit-identical.
+// contributions in FP32 in a fixed order (small tasks: 32-slot rounds summed
+// by a fixed shuffle tree; warp / CTA tasks: lane-strided partial sums and a
+// fixed tree; chunked tasks: chunk sums added in chunk order).  The two global
+// sums (L1 change and dangling rank) add one 2^-60 fixed-point integer per
+// vertex, whose total does not depend on which CTA adds it or when: together
+// with the deterministic task lists this makes every run bit-identical.
 // One grid barrier per iteration: the sums of iteration t are read right
 // after its barrier, before iteration t+1 starts.
 #include "simdx_internal.h"
@@ -22,6 +23,8 @@
 namespace simdx {
 
 constexpr double kFix = 1152921504606846976.0;  // 2^60
+
+__device__ __forceinline__ unsigned long long to_fix(double x) { return __double2ull_rn(x * kFix); }
 
 template <class OffT>
 struct PrArgs {
@@ -45,7 +48,7 @@ struct PrPull {
   float* xnew;
   const OffT* off;
   float base, d, dn;
-  double l1 = 0.0, dang = 0.0;
+  unsigned long long l1 = 0, dang = 0;  // 2^-60 fixed point, one rounding per vertex
   __device__ __forceinline__ Acc zero() const { return 0.f; }
   __device__ __forceinline__ void edge(Acc& a, int, int v, long long) { a += cin[v]; }
   __device__ __forceinline__ void finish(int u, Acc sum) {
@@ -53,12 +56,10 @@ struct PrPull {
     xnew[u] = xn;
     const long long od = (long long)gload(off + u + 1) - (long long)gload(off + u);
     cout[u] = od > 0 ? xn / (float)od : 0.f;
-    if (od == 0) dang += (double)xn;
-    l1 += fabs((double)xn - (double)xold[u]);
+    if (od == 0) dang += to_fix((double)xn);
+    l1 += to_fix(fabs((double)xn - (double)xold[u]));
   }
 };
-
-__device__ __forceinline__ unsigned long long to_fix(double x) { return __double2ull_rn(x * kFix); }
 
 template <class OffT>
 __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
@@ -85,15 +86,15 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     clear_next_slot(s, sh);
     PhaseSlot& slot = s->slot[0];
     const float x0 = 1.0f / (float)n;
-    double dang = 0.0;
+    unsigned long long dang = 0;
     for (long long v = gtid; v < n; v += gthreads) {
       const long long od = (long long)gload(off + v + 1) - (long long)gload(off + v);
       xbuf[0][v] = x0;
       cbuf[0][v] = od > 0 ? x0 / (float)od : 0.f;
-      if (od == 0) dang += (double)x0;
+      if (od == 0) dang += to_fix((double)x0);
     }
-    dang = cta_sum_f64(dang, sh);
-    if (threadIdx.x == 0) atomicAdd(&slot.aux0, to_fix(dang));
+    dang = cta_sum_u64(dang, sh);
+    if (threadIdx.x == 0) atomicAdd(&slot.aux0, dang);
     det_filter_count(n, all, indeg, sh, a.w, k, grid);
   }
   if (!grid_sync(s, grid, sh, k)) return;
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
   long long evisit = 0;
   while (true) {
     if (t >= a.max_iter) break;
+    const unsigned long long t_it = globaltimer();
     // ---- compute x_{t+1}
     clear_next_slot(s, sh);
     PhaseSlot& slot = s->slot[slot_of(sh.phase)];
@@ -123,18 +125,18 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     f.base = base;
     f.d = a.d;
     f.dn = (float)(((double)Dfix / kFix) / (double)n);
-    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_f, evisit);
-    const double l1 = cta_sum_f64(f.l1, sh);
-    const double dg = cta_sum_f64(f.dang, sh);
+    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_f, k.huge_min, sh, a.w, evisit);
+    const unsigned long long l1 = cta_sum_u64(f.l1, sh);
+    const unsigned long long dg = cta_sum_u64(f.dang, sh);
     if (threadIdx.x == 0) {
-      atomicAdd(&slot.aux0, to_fix(dg));
-      atomicAdd(&slot.aux1, to_fix(l1));
+      atomicAdd(&slot.aux0, dg);
+      atomicAdd(&slot.aux1, l1);
     }
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     Dfix = p.aux0;
     l1_last = (double)p.aux1 / kFix;
-    trace_put(a.w, t, 2 | (2 << 8), n, 0, (long long)p.aux1);
+    trace_put(a.w, t, 2 | (2 << 8), n, 0, (long long)p.aux1, t_it);
     ++t;
     if (l1_last < (double)a.tol) break;
   }

@@ -44,6 +44,8 @@ struct simdx_graph {
   uint32_t* aux3 = nullptr;  // [2][list_cap]
   long long list_cap = 0;
   int32_t* chunk_cnt = nullptr;
+  uint32_t* chunk_part = nullptr;
+  int* chunk_done = nullptr;
   uint32_t* bitmaps = nullptr;  // [4][words]
   void* state = nullptr;        // 12 bytes per vertex
   simdx::Sync* sync = nullptr;

@@ -97,6 +97,11 @@ struct SsspPush {
     s.d = (uint32_t)sh.bcast_i[1];
     return true;
   }
+  static __device__ __forceinline__ Src shfl(const Src& s, int l) {
+    Src r;
+    r.d = __shfl_sync(kFull, s.d, l);
+    return r;
+  }
   __device__ __forceinline__ void edge(const Src& s, int, int u, long long p) {
     const unsigned long long nd64 = (unsigned long long)s.d + gload(wt + p);
     if (nd64 < dist[u]) {
@@ -160,6 +165,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
   int filt = 1;
 
   while (true) {
+    const unsigned long long t_it = globaltimer();
     unsigned total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     filt = 1;
     if (!lists_ok || k.filter == 2) {
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     SsspPush<OffT> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
     const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                       a.w.list[lbuf][3]};
-    push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, evisit);
+    push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit);
     online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
     unsigned long long tn = cta_sum_u64(f.nrec, sh);
     unsigned long long tm = cta_sum_u64(f.mrec, sh);
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     if (filt == 2) ++ballot_it; else ++online_it;
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
-    trace_put(a.w, it, 1 | (filt << 8), (long long)total, 0, (long long)(T == kInfT ? -1 : (long long)T));
+    trace_put(a.w, it, 1 | (filt << 8), (long long)total, 0, (long long)(T == kInfT ? -1 : (long long)T), t_it);
     fsum += total;
     ++it;
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];

@@ -164,7 +164,7 @@ def simdx_graph_last_status(g: int, stream: int | None) -> int:
 
 def simdx_graph_trace(g: int, stream: int | None, cap: int = 1 << 16):
     import numpy as np
-    rec = np.zeros((cap, 4), dtype=np.int64)
+    rec = np.zeros((cap, 8), dtype=np.int64)
     cnt = ctypes.c_int64()
     _check(_lib().simdx_graph_trace(g, stream, rec.ctypes.data, cap, ctypes.byref(cnt)), "simdx_graph_trace")
     return rec[:min(cnt.value, cap)].copy()

@@ -53,5 +53,6 @@ def test_host_only_calls(lib):
     from paper_1812_04070_gb300 import simdx
     assert simdx.simdx_strerror(simdx.EBARRIER_TIMEOUT) == "grid barrier wait timed out"
     c = simdx.simdx_config_default()
-    assert (c.small_max, c.med_max, c.bin_per_thread) == (32, 128, 64)  # Sec. 4 defaults
+    assert (c.small_max, c.bin_per_thread) == (32, 64)  # Sec. 4: thread/warp separator 32, threshold 64
+    assert 128 <= c.med_max <= 2048  # Sec. 4: the warp/CTA separator is insensitive in [128, 2048]
     assert simdx.simdx_version() >= 10000
