@@ -325,8 +325,8 @@ def run_simdx(args, rank, world, local):
                       "ballot_iters": stats[a].ballot_iters, "online_iters": stats[a].online_iters,
                       "grid_ctas": stats[a].grid_ctas}
                   for a in algs}
-    # ---- e2e through the C ABI with host buffers
-    e2e = run_e2e(args, g, w, bits, algs, edges_step, world)
+    # ---- e2e through the C ABI with host buffers (--e2e-steps 0 skips it, for profiling runs)
+    e2e = run_e2e(args, g, w, bits, algs, edges_step, world) if args.e2e_steps > 0 else None
     res = {
         "metric": "GTEPS", "value": round(value, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,

@@ -171,7 +171,10 @@ SIMDX_API int simdx_graph_last_status(simdx_graph *g, void *stream);
  * Each record is 8 int64: {direction (1 push, 2 pull) | filter << 8
  * (1 online, 2 ballot), active vertices, active edges, level / bucket bound,
  * %globaltimer ns at the iteration's start and at its end (as seen by CTA 0),
- * 0, 0}.  Writes up to `cap` records to host memory `rec` and returns the
+ * and two algorithm-specific words: for BFS the end of the main compute phase
+ * and the number of high in-degree pull candidates; for the others the
+ * slowest CTA's time in degree classes (ns, 32 bits each) as (3 << 32 | 2)
+ * and (1 << 32 | 0)}.  Writes up to `cap` records to host memory `rec` and returns the
  * number of iterations of the run in *count. */
 SIMDX_API int simdx_graph_trace(simdx_graph *g, void *stream, int64_t *rec, int64_t cap,
                       int64_t *count);

@@ -50,6 +50,7 @@ struct PhaseSlot {
   unsigned int list_cnt[kClasses];
   unsigned int overflow;
   unsigned int flag;
+  unsigned long long tclass[kClasses];  // max over CTAs of each class's duration (ns)
 };
 
 struct Sync {
@@ -186,7 +187,10 @@ __device__ __forceinline__ void clear_next_slot(Sync* s, const CtaShared& sh) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     PhaseSlot& z = s->slot[slot_of(sh.phase + 1)];
     z.nact = 0; z.mact = 0; z.aux0 = 0; z.aux1 = 0; z.aux2 = 0;
-    for (int c = 0; c < kClasses; ++c) z.list_cnt[c] = 0;
+    for (int c = 0; c < kClasses; ++c) {
+      z.list_cnt[c] = 0;
+      z.tclass[c] = 0;
+    }
     z.overflow = 0; z.flag = 0;
   }
 }
@@ -429,6 +433,21 @@ __device__ void bitmap_filter(int n, const uint32_t* bm, Deg deg, Visit visit, C
   }
 }
 
+// Class timing: thread 0 of each CTA folds the time its CTA spent in a degree
+// class into the phase slot (max over CTAs); the trace reports it.
+struct ClassTimer {
+  PhaseSlot* slot;
+  unsigned long long t;
+  __device__ explicit ClassTimer(PhaseSlot* s) : slot(s), t(threadIdx.x == 0 ? globaltimer() : 0) {}
+  __device__ __forceinline__ void lap(int c) {
+    if (slot && threadIdx.x == 0) {
+      const unsigned long long now = globaltimer();
+      atomicMax(&slot->tclass[c], now - t);
+      t = now;
+    }
+  }
+};
+
 // ------------------------------------------------------- chunked tasks
 // Inclusive prefix (in sh.pref) of the chunk counts ceil(deg / ch) of the nb
 // <= kChunkBatch class-3 tasks `items`.  All threads of the CTA call it.
@@ -476,6 +495,11 @@ __device__ __forceinline__ int chunk_item(const int* pref, int nb, int kc) {
   return lo;
 }
 
+// Type in which a task's chunk sums are combined (FP64 for FP32 sums: a hub
+// cut into hundreds of chunks would otherwise lose precision in the combine).
+template <class A> struct Wide { using T = A; };
+template <> struct Wide<float> { using T = double; };
+
 __device__ __forceinline__ unsigned acc_bits(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ unsigned acc_bits(unsigned x) { return x; }
 __device__ __forceinline__ void acc_from(unsigned b, float& x) { x = __uint_as_float(b); }
@@ -493,8 +517,9 @@ __device__ __forceinline__ void acc_from(unsigned b, unsigned& x) { x = b; }
 template <class OffT, class F>
 __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
                              const int32_t* const* lists, const unsigned* cnt, unsigned grid,
-                             long long ch, CtaShared& sh, long long& evisit) {
+                             long long ch, CtaShared& sh, long long& evisit, PhaseSlot* slot = nullptr) {
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  ClassTimer tm(slot);
   // class 3: every task is cut into chunks of `ch` edges and the chunks of
   // all tasks are dealt round-robin to the CTAs (edge-balanced over the grid)
   for (unsigned b0 = 0; b0 < cnt[3]; b0 += kChunkBatch) {
@@ -515,6 +540,7 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
       if (tid == 0) evisit += end - beg;
     }
   }
+  tm.lap(3);
   // class 2: one CTA per task
   for (unsigned i = blockIdx.x; i < cnt[2]; i += grid) {
     int v = lists[2][i];
@@ -525,6 +551,7 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     for (long long p = beg + tid; p < end; p += kThreads) f.edge(s, v, gload(idx + p), p);
     if (tid == 0) evisit += end - beg;
   }
+  tm.lap(2);
   // class 1: one warp per task
   const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
   for (unsigned i = gw; i < cnt[1]; i += nw) {
@@ -536,6 +563,7 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     for (long long p = beg + lane; p < end; p += 32) f.edge(s, v, gload(idx + p), p);
     if (lane == 0) evisit += end - beg;
   }
+  tm.lap(1);
   // class 0: one thread per task, but the edges of the warp's 32 tasks are
   // walked together, 32 consecutive edge slots per round (coalesced loads,
   // 32 independent loads in flight per warp); each slot finds its task by a
@@ -579,6 +607,7 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     }
     evisit += deg;
   }
+  tm.lap(0);
 }
 
 // ----------------------------------------------------- pull class driver
@@ -599,9 +628,10 @@ __device__ __forceinline__ Acc warp_sum(Acc v) {
 template <class OffT, class F>
 __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const int32_t* const* lists,
                              const unsigned* cnt, unsigned grid, typename F::Acc* red, long long ch,
-                             CtaShared& sh, const Work& w, long long& evisit) {
+                             CtaShared& sh, const Work& w, long long& evisit, PhaseSlot* slot = nullptr) {
   using Acc = typename F::Acc;
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  ClassTimer tm(slot);
   // class 3: chunks of `ch` edges dealt round-robin to the CTAs; each chunk's
   // sum goes to chunk_part, and the CTA that finishes a task's last chunk adds
   // the task's chunk sums in chunk order (fixed) and finishes the task.
@@ -641,7 +671,7 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
           const int done = atomicAdd(&w.chunk_done[b0 + item], 1);
           if (done == nch - 1) {
             __threadfence();
-            Acc tot = f.zero();
+            typename Wide<Acc>::T tot = 0;  // chunk sums added in chunk order, in a wider type
             const volatile unsigned* part = w.chunk_part + gbase + first;
             for (int j = 0; j < nch; ++j) {
               Acc y;
@@ -649,13 +679,14 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
               tot += y;
             }
             w.chunk_done[b0 + item] = 0;
-            f.finish(u, tot);
+            f.finish(u, (Acc)tot);
           }
         }
       }
     }
     gbase += total;
   }
+  tm.lap(3);
   // class 2: one CTA per task
   for (unsigned i = blockIdx.x; i < cnt[2]; i += grid) {
     int u = lists[2][i];
@@ -675,6 +706,7 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
       evisit += end - beg;
     }
   }
+  tm.lap(2);
   const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
   for (unsigned i = gw; i < cnt[1]; i += nw) {
     int u = lists[1][i];
@@ -688,6 +720,7 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
       evisit += end - beg;
     }
   }
+  tm.lap(1);
   // class 0: the warp walks the edges of its 32 tasks together, 32 slots per
   // round.  Within a round the slots of one task are contiguous; they are
   // summed by a fixed shuffle tree (suffix sums toward the task's first slot)
@@ -746,6 +779,7 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
       evisit += deg;
     }
   }
+  tm.lap(0);
 }
 
 // ------------------------------------- deterministic (two-pass) ballot filter
@@ -856,6 +890,17 @@ __device__ __forceinline__ void trace_put(const Work& w, int it, long long a, lo
     r[4] = (long long)t0;
     r[5] = (long long)globaltimer();
     r[6] = 0; r[7] = 0;
+  }
+}
+
+// Trace words 6 and 7: the slowest CTA's time (ns, 32 bits each) in degree
+// classes 3 | 2 and 1 | 0 of the iteration's compute phase.
+__device__ __forceinline__ void trace_classes(const Work& w, int it, const PhaseSlot& p) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && it < w.trace_cap) {
+    auto c32 = [](unsigned long long x) { return x > 0xffffffffull ? 0xffffffffull : x; };
+    long long* r = w.trace + (long long)kTraceWords * it;
+    r[6] = (long long)((c32(p.tclass[3]) << 32) | c32(p.tclass[2]));
+    r[7] = (long long)((c32(p.tclass[1]) << 32) | c32(p.tclass[0]));
   }
 }
 

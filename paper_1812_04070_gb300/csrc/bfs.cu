@@ -22,6 +22,7 @@
 namespace simdx {
 
 enum { kPush = 1, kPull = 2 };
+constexpr int kPullFirst = 8;  // in-edges every pull candidate checks on its own lane
 enum { kOnline = 1, kBallot = 2 };
 
 template <class OffT>
@@ -101,7 +102,7 @@ struct PullShared {
 template <class OffT>
 __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
                          uint32_t* fbm_next, CtaShared& sh, PullShared& ps, unsigned grid,
-                         PhaseSlot& slot, int32_t* big, uint32_t* found,
+                         PhaseSlot& slot, int32_t* big, uint32_t* found_big,
                          unsigned long long& nrec, unsigned long long& mrec, long long& evisit) {
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   const long long nwords = ((long long)a.n + 31) >> 5;
@@ -136,31 +137,33 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
         bit = nth_set_bit(cand_j, kk - excl_j);
         u = (int)((g * 32 + j) * 32 + bit);
         const long long beg = gload(a.ioff + u), end = gload(a.ioff + u + 1);
-        if (end - beg >= a.k.huge_min) {
+        // every candidate first checks its first kPullFirst in-neighbours on
+        // its own lane (sorted adjacency: low ids, the hubs, come first, so
+        // this resolves almost every candidate); only the rest is deferred
+        const long long lim = end - beg < kPullFirst ? end : beg + kPullFirst;
+        bool found = false;
+        long long p = beg;
+        for (; p + 4 <= lim && !found; p += 4) {
+          int v0 = gload(a.iidx + p), v1 = gload(a.iidx + p + 1), v2 = gload(a.iidx + p + 2),
+              v3 = gload(a.iidx + p + 3);
+          found = bm_test(fbm, v0) | bm_test(fbm, v1) | bm_test(fbm, v2) | bm_test(fbm, v3);
+        }
+        for (; p < lim && !found; ++p) found = bm_test(fbm, gload(a.iidx + p));
+        evisit += (p < lim ? p : lim) - beg;
+        if (found) {
+          a.level[u] = next;
+          atomicOr(&ps.newbits[warp][j], 1u << bit);
+          long long od = (long long)gload(a.off + u + 1) - (long long)gload(a.off + u);
+          ++nrec;
+          mrec += (unsigned long long)od;
+          online_record(u, degree_class(od, a.k), sh, a.w, a.k, grid);
+        } else if (end - lim >= a.k.huge_min) {
           // scanned later by the whole grid (bfs_pull_big)
           const unsigned pos = (unsigned)atomicAdd(&slot.aux2, 1ull);
           big[pos] = u;
-          found[pos] = 0u;
-        } else if (end - beg >= a.k.small_max) {
-          deferred = true;
-        } else {
-          bool found = false;
-          long long p = beg;
-          for (; p + 4 <= end && !found; p += 4) {
-            int v0 = gload(a.iidx + p), v1 = gload(a.iidx + p + 1), v2 = gload(a.iidx + p + 2),
-                v3 = gload(a.iidx + p + 3);
-            found = bm_test(fbm, v0) | bm_test(fbm, v1) | bm_test(fbm, v2) | bm_test(fbm, v3);
-          }
-          for (; p < end && !found; ++p) found = bm_test(fbm, gload(a.iidx + p));
-          evisit += (p < end ? p : end) - beg;
-          if (found) {
-            a.level[u] = next;
-            atomicOr(&ps.newbits[warp][j], 1u << bit);
-            long long od = (long long)gload(a.off + u + 1) - (long long)gload(a.off + u);
-            ++nrec;
-            mrec += (unsigned long long)od;
-            online_record(u, degree_class(od, a.k), sh, a.w, a.k, grid);
-          }
+          found_big[pos] = 0u;
+        } else if (end > lim) {
+          deferred = true;  // the warp scans the remaining in-edges
         }
       }
       // warp-cooperative scan of the deferred (higher in-degree) candidates
@@ -174,7 +177,7 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
       const int nd = __popc(dm);
       for (int q = 0; q < nd; ++q) {
         const int v = ps.defer_v[warp][q];
-        const long long beg = gload(a.ioff + v), end = gload(a.ioff + v + 1);
+        const long long beg = gload(a.ioff + v) + kPullFirst, end = gload(a.ioff + v + 1);
         bool found = false;
         long long seen = 0;
         for (long long base = beg; base < end; base += 128) {
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       BfsPush<OffT> f(a.level, a.off, L + 1, sh, a.w, k, grid);
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, nullptr);
       nrec = f.nrec;
       mrec = f.mrec;
       ++push_it;
@@ -398,6 +401,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     bool ovf = p.overflow != 0;
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
     const unsigned nbig = dir == kPull ? (unsigned)p.aux2 : 0u;
+    const unsigned long long t_main = globaltimer();
     if (nbig > 0) {
       // grid-wide pull of the high in-degree candidates
       clear_next_slot(s, sh);
@@ -417,6 +421,10 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       mm += p2.mact;
     }
     trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, L, t_it);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && it < a.w.trace_cap) {
+      a.w.trace[(long long)kTraceWords * it + 6] = (long long)t_main;  // end of the main compute phase
+      a.w.trace[(long long)kTraceWords * it + 7] = (long long)nbig;    // high in-degree pull candidates
+    }
     fsum += (long long)n_f;
     ++it;
     if (nn == 0) break;

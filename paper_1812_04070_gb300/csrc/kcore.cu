@@ -194,13 +194,13 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
     unsigned long long nrec = 0, mrec = 0;
     if (dir == 1) {
       KcorePush<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit, &slot);
       nrec = f.nrec;
       mrec = f.mrec;
       ++push_it;
     } else {
       KcorePull<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
-      pull_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, red_u32, k.huge_min, sh, a.w, evisit);
+      pull_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, red_u32, k.huge_min, sh, a.w, evisit, &slot);
       nrec = f.nrec;
       mrec = f.mrec;
       ++pull_it;
@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     trace_put(a.w, it, dir | (filt << 8), (long long)n_f, (long long)m_f, it, t_it);
+    trace_classes(a.w, it, p);
     for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
     lists_ok = p.overflow == 0;
     m_alive -= p.mact;

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     f.base = base;
     f.d = a.d;
     f.dn = (float)(((double)Dfix / kFix) / (double)n);
-    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_f, k.huge_min, sh, a.w, evisit);
+    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_f, k.huge_min, sh, a.w, evisit, &slot);
     const unsigned long long l1 = cta_sum_u64(f.l1, sh);
     const unsigned long long dg = cta_sum_u64(f.dang, sh);
     if (threadIdx.x == 0) {
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     Dfix = p.aux0;
     l1_last = (double)p.aux1 / kFix;
     trace_put(a.w, t, 2 | (2 << 8), n, 0, (long long)p.aux1, t_it);
+    trace_classes(a.w, t, p);
     ++t;
     if (l1_last < (double)a.tol) break;
   }

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     SsspPush<OffT> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
     const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                       a.w.list[lbuf][3]};
-    push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit);
+    push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
     online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
     unsigned long long tn = cta_sum_u64(f.nrec, sh);
     unsigned long long tm = cta_sum_u64(f.mrec, sh);
@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     trace_put(a.w, it, 1 | (filt << 8), (long long)total, 0, (long long)(T == kInfT ? -1 : (long long)T), t_it);
+    trace_classes(a.w, it, p);
     fsum += total;
     ++it;
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
