@@ -86,11 +86,12 @@ struct Work {
   long long list_cap;
   int32_t* chunk_cnt;            // [chunks][kClasses] for the deterministic ballot filter
   uint32_t* chunk_part;          // per-chunk partial sums of chunked pull tasks
-  int* chunk_done;               // [kChunkBatch] chunks finished per task (reset by the last)
+  int* chunk_done;               // chunks finished per class-3 task (reset by the last)
+  int* warp_start;               // [grid * kWarps + 1] first task of each warp's edge range
   uint32_t* bm_nz;               // vertices with an in-edge (pull candidates)
   uint32_t* bm_vis;              // BFS visited
   uint32_t* bm_f[2];             // BFS frontier bitmaps
-  void* state;                   // per-algorithm vertex state (12 bytes / vertex)
+  void* state;                   // per-algorithm vertex state (20 bytes / vertex)
   Sync* sync;
   DevStats* stats;
   long long* trace;              // [trace_cap][kTraceWords]
@@ -625,6 +626,90 @@ __device__ __forceinline__ Acc warp_sum(Acc v) {
   return v;
 }
 
+// Sum over the in-edges of tasks list[t_begin, t_end) (at most 32 tasks per
+// window), one warp.  The warp walks the concatenated edges of a window of
+// tasks in rounds of 32 edge slots, kSegUnroll rounds at a time: all index
+// loads of those rounds are issued first, then all gathers, then the
+// reductions, so each lane has several independent loads in flight.  Within
+// a round the slots of one task are contiguous and are summed by a fixed
+// shuffle tree toward the task's first slot; that partial is added to the
+// task's accumulator, held by the task's own lane, in round order.  The order
+// of every sum therefore depends only on the task list and the window start.
+constexpr int kSegUnroll = 4;
+
+template <class OffT, class F>
+__device__ void warp_segmented_sum(F& f, const OffT* off, const int32_t* idx, const int32_t* list,
+                                   unsigned t_begin, unsigned t_end, long long& evisit) {
+  using Acc = typename F::Acc;
+  const int lane = lane_id();
+  for (unsigned t0 = t_begin; t0 < t_end; t0 += 32) {
+    const unsigned i = t0 + lane;
+    int u = -1, deg = 0;
+    long long beg = 0;
+    if (i < t_end) {
+      u = list[i];
+      beg = gload(off + u);
+      deg = (int)(gload(off + u + 1) - beg);
+    }
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - deg;
+    Acc acc = f.zero();
+    for (int e0 = 0; e0 < total; e0 += 32 * kSegUnroll) {
+      int jq[kSegUnroll], vq[kSegUnroll], uq[kSegUnroll];
+      long long pq[kSegUnroll];
+#pragma unroll
+      for (int q = 0; q < kSegUnroll; ++q) {
+        const int e = e0 + 32 * q + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          int t = __shfl_sync(kFull, incl, j + step - 1);
+          if (t <= e) j += step;
+        }
+        const long long bj = __shfl_sync(kFull, beg, j);
+        const int xj = __shfl_sync(kFull, excl, j);
+        uq[q] = __shfl_sync(kFull, u, j);
+        pq[q] = bj + (e - xj);
+        jq[q] = e < total ? j : 32;  // 32: no task
+      }
+#pragma unroll
+      for (int q = 0; q < kSegUnroll; ++q) vq[q] = jq[q] < 32 ? gload(idx + pq[q]) : 0;
+      Acc val[kSegUnroll];
+#pragma unroll
+      for (int q = 0; q < kSegUnroll; ++q) {
+        val[q] = f.zero();
+        if (jq[q] < 32) f.edge(val[q], uq[q], vq[q], pq[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kSegUnroll; ++q) {
+        Acc x = val[q];
+        const int j = jq[q];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          Acc y = __shfl_down_sync(kFull, x, d);
+          int jy = __shfl_down_sync(kFull, j, d);
+          if (lane + d < 32 && jy == j) x += y;
+        }
+        const int r0 = e0 + 32 * q;
+        int h = excl - r0;
+        h = h < 0 ? 0 : (h > 31 ? 31 : h);
+        Acc part = __shfl_sync(kFull, x, h);
+        if (deg > 0 && excl < r0 + 32 && incl > r0) acc += part;
+      }
+    }
+    if (u >= 0) {
+      f.finish(u, acc);
+      evisit += deg;
+    }
+  }
+}
+
 template <class OffT, class F>
 __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const int32_t* const* lists,
                              const unsigned* cnt, unsigned grid, typename F::Acc* red, long long ch,
@@ -707,6 +792,7 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
     }
   }
   tm.lap(2);
+  {
   const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
   for (unsigned i = gw; i < cnt[1]; i += nw) {
     int u = lists[1][i];
@@ -720,64 +806,16 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
       evisit += end - beg;
     }
   }
+  }
   tm.lap(1);
-  // class 0: the warp walks the edges of its 32 tasks together, 32 slots per
-  // round.  Within a round the slots of one task are contiguous; they are
-  // summed by a fixed shuffle tree (suffix sums toward the task's first slot)
-  // and that partial is added to the task's accumulator, held by the task's
-  // own lane.  The order of every sum depends only on the task list.
-  for (unsigned base = (blockIdx.x * kWarps + warp) * 32u; base < cnt[0]; base += grid * kWarps * 32u) {
-    const unsigned i = base + lane;
-    int u = -1, deg = 0;
-    long long beg = 0;
-    if (i < cnt[0]) {
-      u = lists[0][i];
-      beg = gload(off + u);
-      deg = (int)(gload(off + u + 1) - beg);
-    }
-    int incl = deg;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - deg;
-    Acc acc = f.zero();
-    for (int e0 = 0; e0 < total; e0 += 32) {
-      const int e = e0 + lane;
-      int j = 0;
-#pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        int t = __shfl_sync(kFull, incl, j + step - 1);
-        if (t <= e) j += step;
-      }
-      const long long bj = __shfl_sync(kFull, beg, j);
-      const int xj = __shfl_sync(kFull, excl, j);
-      const int uj = __shfl_sync(kFull, u, j);
-      Acc val = f.zero();
-      if (e < total) {
-        const long long p = bj + (e - xj);
-        f.edge(val, uj, gload(idx + p), p);
-      } else {
-        j = 32;  // no task
-      }
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        Acc y = __shfl_down_sync(kFull, val, d);
-        int jy = __shfl_down_sync(kFull, j, d);
-        if (lane + d < 32 && jy == j) val += y;
-      }
-      // the task's first slot in this round holds the round's partial
-      int h = excl - e0;
-      h = h < 0 ? 0 : (h > 31 ? 31 : h);
-      Acc part = __shfl_sync(kFull, val, h);
-      if (deg > 0 && excl < e0 + 32 && incl > e0) acc += part;
-    }
-    if (u >= 0) {
-      f.finish(u, acc);
-      evisit += deg;
-    }
+  // class 0: groups of up to 32 consecutive tasks per warp (fewer when the
+  // list is short, so every warp gets work), walked by warp_segmented_sum
+  const unsigned nw = grid * kWarps;
+  unsigned gs = (cnt[0] + nw - 1) / nw;
+  gs = gs < 1 ? 1 : (gs > 32 ? 32 : gs);
+  for (unsigned base = (blockIdx.x * kWarps + warp) * gs; base < cnt[0]; base += nw * gs) {
+    const unsigned lim = base + gs < cnt[0] ? base + gs : cnt[0];
+    warp_segmented_sum<OffT>(f, off, idx, lists[0], base, lim, evisit);
   }
   tm.lap(0);
 }

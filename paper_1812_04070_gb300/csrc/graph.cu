@@ -58,6 +58,7 @@ Work make_work(const simdx_graph* g) {
   w.chunk_cnt = g->chunk_cnt;
   w.chunk_part = g->chunk_part;
   w.chunk_done = g->chunk_done;
+  w.warp_start = g->warp_start;
   long long words = (g->n + 31) / 32 + 1;
   w.bm_nz = g->bitmaps;
   w.bm_vis = g->bitmaps + words;
@@ -228,6 +229,8 @@ static void free_workspace(simdx_graph* g) {
   cudaFree(g->aux3);
   cudaFree(g->chunk_part);
   cudaFree(g->chunk_done);
+  cudaFree(g->warp_start);
+  g->warp_start = nullptr;
   g->bins = nullptr;
   g->lists = nullptr;
   g->aux3 = nullptr;
@@ -259,6 +262,7 @@ static int alloc_workspace(simdx_graph* g) {
   SIMDX_CUDA(cudaMalloc(&g->chunk_part, sizeof(uint32_t) * parts));
   SIMDX_CUDA(cudaMalloc(&g->chunk_done, sizeof(int) * (size_t)(g->n + 16)));
   SIMDX_CUDA(cudaMemset(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16)));
+  SIMDX_CUDA(cudaMalloc(&g->warp_start, sizeof(int) * ((size_t)g->grid_max * kWarps + 1)));
   return SIMDX_OK;
 }
 
@@ -348,7 +352,7 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
   if ((e = cudaMalloc(&g->bitmaps, sizeof(uint32_t) * 4 * (size_t)words)) != cudaSuccess)
     return fail(cuda_status(e, "cudaMalloc(bitmaps)"));
   cudaMemsetAsync(g->bitmaps, 0, sizeof(uint32_t) * 4 * (size_t)words, st);
-  if ((e = cudaMalloc(&g->state, 12 * (size_t)std::max<int64_t>(g->n, 1) + 64)) != cudaSuccess)
+  if ((e = cudaMalloc(&g->state, 20 * (size_t)std::max<int64_t>(g->n, 1) + 64)) != cudaSuccess)
     return fail(cuda_status(e, "cudaMalloc(state)"));
   if ((e = cudaMalloc(&g->sync, sizeof(Sync))) != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(sync)"));
   {

@@ -53,10 +53,18 @@ struct KcorePush {
       : removed_at(r), cnt(c), off(o), kk(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
   __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
   static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
+  // Lanes of a warp that decrement the same vertex (hubs neighbour most
+  // deleted vertices) combine into one atomicSub of their count; the one
+  // subtraction that takes the degree from >= k to < k deletes the vertex.
   __device__ __forceinline__ void edge(const Src&, int, int u, long long) {
-    if (removed_at[u] != INT_MAX || cnt[u] < kk) return;  // stop once below k
-    const unsigned old = atomicSub(&cnt[u], 1u);
-    if (old == kk) {
+    const bool want = removed_at[u] == INT_MAX && cnt[u] >= kk;  // stop once below k
+    const unsigned mask = __activemask();
+    const int key = want ? u : (int)(0x80000000u | lane_id());
+    const unsigned peers = __match_any_sync(mask, key);
+    if (!want || (int)lane_id() != __ffs(peers) - 1) return;
+    const unsigned c = (unsigned)__popc(peers);
+    const unsigned old = atomicSub(&cnt[u], c);
+    if (old >= kk && old - c < kk) {
       removed_at[u] = it;
       long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
       ++nrec;

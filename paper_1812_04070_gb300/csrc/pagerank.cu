@@ -9,7 +9,11 @@
 //
 // All vertices are active in every iteration, so the ballot filter runs once
 // (Sec. 4: PageRank needs the ballot filter exactly at the first iteration)
-// and its sorted task lists are reused.  Each vertex sums its in-neighbours'
+// and its sorted task lists are reused.  Vertices of in-degree < med_max form
+// one list that is cut, once per run, into task-aligned ranges of equal edge
+// count, one per warp (a degree prefix over the list and a binary search per
+// warp); each warp walks its range with warp_segmented_sum.  Higher in-degree
+// vertices keep the CTA-per-task and chunked classes.  Each vertex sums its in-neighbours'
 // contributions in FP32 in a fixed order (small tasks: 32-slot rounds summed
 // by a fixed shuffle tree; warp / CTA tasks: lane-strided partial sums and a
 // fixed tree; chunked tasks: chunk sums added in chunk order).  The two global
@@ -81,6 +85,11 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
 
+  // Task classes for PageRank: every vertex of in-degree < med_max goes to one
+  // list (class 0) that is walked edge-balanced by warps; the rest keep their
+  // CTA / chunked classes.
+  Knobs kp = k;
+  kp.small_max = k.med_max;
   // ---- phase 0: x_0, c_0, D_0 and the per-chunk class counts
   {
     clear_next_slot(s, sh);
@@ -95,17 +104,86 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     }
     dang = cta_sum_u64(dang, sh);
     if (threadIdx.x == 0) atomicAdd(&slot.aux0, dang);
-    det_filter_count(n, all, indeg, sh, a.w, k, grid);
+    det_filter_count(n, all, indeg, sh, a.w, kp, grid);
   }
   if (!grid_sync(s, grid, sh, k)) return;
   unsigned long long Dfix = s->slot[0].aux0;
   // ---- phase 1: sorted task lists of all vertices by in-degree
   unsigned cnt[kClasses];
   clear_next_slot(s, sh);
-  det_filter_write(n, all, indeg, sh, a.w, k, grid, 0, cnt);
+  det_filter_write(n, all, indeg, sh, a.w, kp, grid, 0, cnt);
   if (!grid_sync(s, grid, sh, k)) return;
-
+  // ---- phases 2-4: edge-balanced, task-aligned ranges of list 0 per warp
+  const int32_t* l0 = a.w.list[0][0];
+  const unsigned c0n = cnt[0];
+  long long* pre = reinterpret_cast<long long*>(xalt + 3 * (size_t)n + 2);  // [c0n + 1] task start edges
+  pre = reinterpret_cast<long long*>((reinterpret_cast<uintptr_t>(pre) + 7) & ~(uintptr_t)7);
+  unsigned long long* bsum = reinterpret_cast<unsigned long long*>(a.w.chunk_part);
+  const long long nblk = ((long long)c0n + kBallotChunk - 1) / kBallotChunk;
+  clear_next_slot(s, sh);
+  for (long long b = blockIdx.x; b < nblk; b += grid) {  // block degree sums
+    unsigned long long t = 0;
+    for (long long q = b * kBallotChunk + threadIdx.x; q < (b + 1) * kBallotChunk && q < c0n; q += kThreads)
+      t += (unsigned long long)indeg(l0[q]);
+    t = cta_sum_u64(t, sh);
+    if (threadIdx.x == 0) bsum[b] = t;
+  }
+  if (!grid_sync(s, grid, sh, k)) return;
+  clear_next_slot(s, sh);
+  unsigned long long mtot = 0;
+  {
+    unsigned long long t = 0;
+    for (long long q = threadIdx.x; q < nblk; q += kThreads) t += bsum[q];
+    mtot = cta_sum_u64(t, sh);
+  }
+  for (long long b = blockIdx.x; b < nblk; b += grid) {  // task start edges
+    unsigned long long run = 0;
+    for (long long q = threadIdx.x; q < b; q += kThreads) run += bsum[q];
+    run = cta_sum_u64(run, sh);
+    constexpr int kPer = kBallotChunk / kThreads;  // consecutive tasks per thread
+    const long long t0 = b * kBallotChunk + (long long)threadIdx.x * kPer;
+    unsigned long long mine = 0;
+    for (int q = 0; q < kPer; ++q)
+      if (t0 + q < c0n) mine += (unsigned long long)indeg(l0[t0 + q]);
+    // exclusive scan of `mine` over the CTA
+    unsigned long long incl = mine;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh.red64[warp] = incl;
+    __syncthreads();
+    unsigned long long ex = run + incl - mine;
+    for (int q = 0; q < warp; ++q) ex += sh.red64[q];
+    for (int q = 0; q < kPer; ++q)
+      if (t0 + q < c0n) {
+        pre[t0 + q] = (long long)ex;
+        ex += (unsigned long long)indeg(l0[t0 + q]);
+      }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) pre[c0n] = (long long)mtot;
+  if (!grid_sync(s, grid, sh, k)) return;
+  clear_next_slot(s, sh);
+  const unsigned nwarps = grid * kWarps;
+  for (unsigned wv = blockIdx.x * kThreads + threadIdx.x; wv <= nwarps; wv += grid * kThreads) {
+    // first task whose start edge is >= this warp's share boundary
+    const long long x = (long long)((mtot * (unsigned long long)wv) / nwarps);
+    unsigned lo = 0, hi = c0n;
+    while (lo < hi) {
+      unsigned mid = (lo + hi) >> 1;
+      if (pre[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    a.w.warp_start[wv] = wv == nwarps ? (int)c0n : (int)lo;
+  }
+  if (!grid_sync(s, grid, sh, k)) return;
+  const unsigned my_warp = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const unsigned w_beg = (unsigned)a.w.warp_start[my_warp], w_end = (unsigned)a.w.warp_start[my_warp + 1];
+  const unsigned cnt_big[kClasses] = {0u, 0u, cnt[2], cnt[3]};
   const int32_t* lists[kClasses] = {a.w.list[0][0], a.w.list[0][1], a.w.list[0][2], a.w.list[0][3]};
+
   const float base = (1.0f - a.d) / (float)n;
   int t = 0;
   double l1_last = 0.0;
@@ -125,7 +203,12 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     f.base = base;
     f.d = a.d;
     f.dn = (float)(((double)Dfix / kFix) / (double)n);
-    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_f, k.huge_min, sh, a.w, evisit, &slot);
+    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt_big, grid, red_f, k.huge_min, sh, a.w, evisit, &slot);
+    {
+      ClassTimer tm(&slot);
+      warp_segmented_sum<OffT>(f, ioff, a.iidx, l0, w_beg, w_end, evisit);
+      tm.lap(0);
+    }
     const unsigned long long l1 = cta_sum_u64(f.l1, sh);
     const unsigned long long dg = cta_sum_u64(f.dang, sh);
     if (threadIdx.x == 0) {

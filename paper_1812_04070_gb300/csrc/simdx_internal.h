@@ -46,8 +46,9 @@ struct simdx_graph {
   int32_t* chunk_cnt = nullptr;
   uint32_t* chunk_part = nullptr;
   int* chunk_done = nullptr;
+  int* warp_start = nullptr;
   uint32_t* bitmaps = nullptr;  // [4][words]
-  void* state = nullptr;        // 12 bytes per vertex
+  void* state = nullptr;        // 20 bytes per vertex
   simdx::Sync* sync = nullptr;
   simdx::DevStats* dstats = nullptr;
   long long* trace = nullptr;
