@@ -510,11 +510,45 @@ __device__ __forceinline__ void acc_from(unsigned b, unsigned& x) { x = b; }
 // Visit every edge of every task in the four class lists.  F provides
 //   typename F::Src;                                 per-source state
 //   bool src(int v, Src& s, int cls, unsigned item); read state; false = skip
-//   void edge(const Src& s, int v, int u, long long p);
-// For cls 1 / 2 every lane / thread of the group calls src() and it must
-// return the same answer in all of them (F broadcasts).  Thread / warp / CTA
-// tasks follow Sec. 3.3; class 3 splits each vertex's edges evenly over all
-// CTAs (a GB300 addition for the highest degrees).
+//   static Src shfl(const Src&, int lane);
+//   void edges(const Src (&s)[kPushBatch], const int (&v)[kPushBatch],
+//              const int (&u)[kPushBatch], const long long (&p)[kPushBatch],
+//              unsigned ok);      // bit q of ok: slot q holds edge (v[q] -> u[q])
+// edges() receives kPushBatch edges per lane at once so it can issue all
+// their loads, then all their atomics, before it needs any result.  For
+// cls 1 / 2 every lane / thread of the group calls src() and it must return
+// the same answer in all of them (F broadcasts).  Thread / warp / CTA tasks
+// follow Sec. 3.3; class 3 tasks are cut into chunks of `ch` edges dealt
+// round-robin to all CTAs (a GB300 addition for the highest degrees).
+constexpr int kPushBatch = 4;
+
+template <class F>
+__device__ __forceinline__ void push_strided(F& f, const typename F::Src& s, int v, const int32_t* idx,
+                                             long long beg, long long end, int lane, int width) {
+  typename F::Src ss[kPushBatch];
+  int vv[kPushBatch];
+#pragma unroll
+  for (int q = 0; q < kPushBatch; ++q) {
+    ss[q] = s;
+    vv[q] = v;
+  }
+  for (long long b = beg; b < end; b += (long long)width * kPushBatch) {
+    int u[kPushBatch];
+    long long pp[kPushBatch];
+    unsigned ok = 0;
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      pp[q] = b + lane + (long long)q * width;
+      u[q] = 0;
+      if (pp[q] < end) {
+        u[q] = gload(idx + pp[q]);
+        ok |= 1u << q;
+      }
+    }
+    f.edges(ss, vv, u, pp, ok);
+  }
+}
+
 template <class OffT, class F>
 __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
                              const int32_t* const* lists, const unsigned* cnt, unsigned grid,
@@ -536,8 +570,7 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
       const long long end = beg + ch < ve ? beg + ch : ve;
       typename F::Src s;
       if (!f.src(v, s, 3, b0 + item)) continue;
-#pragma unroll 4
-      for (long long p = beg + tid; p < end; p += kThreads) f.edge(s, v, gload(idx + p), p);
+      push_strided(f, s, v, idx, beg, end, tid, kThreads);
       if (tid == 0) evisit += end - beg;
     }
   }
@@ -548,33 +581,38 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     typename F::Src s;
     if (!f.src(v, s, 2, i)) continue;
     long long beg = gload(off + v), end = gload(off + v + 1);
-#pragma unroll 4
-    for (long long p = beg + tid; p < end; p += kThreads) f.edge(s, v, gload(idx + p), p);
+    push_strided(f, s, v, idx, beg, end, tid, kThreads);
     if (tid == 0) evisit += end - beg;
   }
   tm.lap(2);
   // class 1: one warp per task
-  const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
-  for (unsigned i = gw; i < cnt[1]; i += nw) {
-    int v = lists[1][i];
-    typename F::Src s;
-    if (!f.src(v, s, 1, i)) continue;
-    long long beg = gload(off + v), end = gload(off + v + 1);
-#pragma unroll 4
-    for (long long p = beg + lane; p < end; p += 32) f.edge(s, v, gload(idx + p), p);
-    if (lane == 0) evisit += end - beg;
+  {
+    const unsigned gw = blockIdx.x * kWarps + warp, nw = grid * kWarps;
+    for (unsigned i = gw; i < cnt[1]; i += nw) {
+      int v = lists[1][i];
+      typename F::Src s;
+      if (!f.src(v, s, 1, i)) continue;
+      long long beg = gload(off + v), end = gload(off + v + 1);
+      push_strided(f, s, v, idx, beg, end, lane, 32);
+      if (lane == 0) evisit += end - beg;
+    }
   }
   tm.lap(1);
-  // class 0: one thread per task, but the edges of the warp's 32 tasks are
-  // walked together, 32 consecutive edge slots per round (coalesced loads,
-  // 32 independent loads in flight per warp); each slot finds its task by a
-  // binary search over the warp's inclusive degree scan.
-  for (unsigned base = (blockIdx.x * kWarps + warp) * 32u; base < cnt[0]; base += grid * kWarps * 32u) {
+  // class 0: groups of up to 32 consecutive tasks per warp (fewer when the
+  // list is short, so every warp gets work).  The warp walks the group's
+  // concatenated edges, kPushBatch rounds of 32 edge slots at a time
+  // (coalesced index loads); each slot finds its task by a binary search over
+  // the warp's inclusive degree scan.
+  const unsigned nw0 = grid * kWarps;
+  unsigned gs = (cnt[0] + nw0 - 1) / nw0;
+  gs = gs < 1 ? 1 : (gs > 32 ? 32 : gs);
+  for (unsigned base = (blockIdx.x * kWarps + warp) * gs; base < cnt[0]; base += nw0 * gs) {
+    const unsigned lim = base + gs < cnt[0] ? base + gs : cnt[0];
     const unsigned i = base + lane;
     int v = -1, deg = 0;
     long long beg = 0;
     typename F::Src s{};
-    if (i < cnt[0]) {
+    if (i < lim) {
       v = lists[0][i];
       if (f.src(v, s, 0, i)) {
         beg = gload(off + v);
@@ -589,22 +627,32 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     }
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - deg;
-    for (int e0 = 0; e0 < total; e0 += 32) {
-      const int e = e0 + lane;
-      int j = 0;
+    for (int e0 = 0; e0 < total; e0 += 32 * kPushBatch) {
+      typename F::Src sq[kPushBatch];
+      int vq[kPushBatch], uq[kPushBatch];
+      long long pq[kPushBatch];
+      unsigned ok = 0;
 #pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        int t = __shfl_sync(kFull, incl, j + step - 1);
-        if (t <= e) j += step;
+      for (int q = 0; q < kPushBatch; ++q) {
+        const int e = e0 + 32 * q + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          int t = __shfl_sync(kFull, incl, j + step - 1);
+          if (t <= e) j += step;
+        }
+        const long long bj = __shfl_sync(kFull, beg, j);
+        const int xj = __shfl_sync(kFull, excl, j);
+        vq[q] = __shfl_sync(kFull, v, j);
+        sq[q] = F::shfl(s, j);
+        pq[q] = bj + (e - xj);
+        uq[q] = 0;
+        if (e < total) ok |= 1u << q;
       }
-      const long long bj = __shfl_sync(kFull, beg, j);
-      const int xj = __shfl_sync(kFull, excl, j);
-      const int vj = __shfl_sync(kFull, v, j);
-      const typename F::Src sj = F::shfl(s, j);
-      if (e < total) {
-        const long long p = bj + (e - xj);
-        f.edge(sj, vj, gload(idx + p), p);
-      }
+#pragma unroll
+      for (int q = 0; q < kPushBatch; ++q)
+        if ((ok >> q) & 1u) uq[q] = gload(idx + pq[q]);
+      f.edges(sq, vq, uq, pq, ok);
     }
     evisit += deg;
   }
@@ -616,9 +664,9 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
 // u's in-edges and hand the total to F:
 //   typename F::Acc;  Acc zero();  void edge(Acc&, int u, int v, long long p);
 //   void finish(int u, Acc total);   (called by exactly one thread per task)
-// Thread tasks sum serially in edge order; warp tasks sum lane-strided and
-// reduce with a fixed shuffle tree; CTA tasks (classes 2 and 3) reduce with
-// a fixed block tree.  The order of every sum is therefore fixed.
+// Small tasks are summed by warp_segmented_sum; warp tasks lane-strided with
+// a fixed shuffle tree; CTA tasks with a fixed block tree; chunked tasks add
+// their chunk sums in chunk order.  The order of every sum is therefore fixed.
 template <class Acc>
 __device__ __forceinline__ Acc warp_sum(Acc v) {
 #pragma unroll

@@ -78,13 +78,21 @@ struct BfsPush {
       : level(l), off(o), next(nx), sh(s), w(ww), k(kk), grid(g) {}
   __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
   static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
-  __device__ __forceinline__ void edge(const Src&, int, int u, long long) {
-    if (level[u] == -1) {
-      level[u] = next;  // vote: every writer stores the same value
-      long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
-      ++nrec;
-      mrec += (unsigned long long)d;
-      online_record(u, degree_class(d, k), sh, w, k, grid);
+  __device__ __forceinline__ void edges(const Src (&)[kPushBatch], const int (&)[kPushBatch],
+                                        const int (&u)[kPushBatch], const long long (&)[kPushBatch],
+                                        unsigned ok) {
+    int lv[kPushBatch];
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) lv[q] = ((ok >> q) & 1u) ? level[u[q]] : 0;
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      if (((ok >> q) & 1u) && lv[q] == -1) {
+        level[u[q]] = next;  // vote: every writer stores the same value
+        long long d = (long long)gload(off + u[q] + 1) - (long long)gload(off + u[q]);
+        ++nrec;
+        mrec += (unsigned long long)d;
+        online_record(u[q], degree_class(d, k), sh, w, k, grid);
+      }
     }
   }
 };

@@ -53,23 +53,37 @@ struct KcorePush {
       : removed_at(r), cnt(c), off(o), kk(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
   __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
   static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
-  // Lanes of a warp that decrement the same vertex (hubs neighbour most
-  // deleted vertices) combine into one atomicSub of their count; the one
-  // subtraction that takes the degree from >= k to < k deletes the vertex.
-  __device__ __forceinline__ void edge(const Src&, int, int u, long long) {
-    const bool want = removed_at[u] == INT_MAX && cnt[u] >= kk;  // stop once below k
-    const unsigned mask = __activemask();
-    const int key = want ? u : (int)(0x80000000u | lane_id());
-    const unsigned peers = __match_any_sync(mask, key);
-    if (!want || (int)lane_id() != __ffs(peers) - 1) return;
-    const unsigned c = (unsigned)__popc(peers);
-    const unsigned old = atomicSub(&cnt[u], c);
-    if (old >= kk && old - c < kk) {
-      removed_at[u] = it;
-      long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
-      ++nrec;
-      mrec += (unsigned long long)d;
-      online_record(u, degree_class(d, k), sh, w, k, grid);
+  // State of all the lane's targets is loaded first.  Then, per slot, lanes
+  // of the warp that decrement the same vertex (hubs neighbour most deleted
+  // vertices) combine into one atomicSub of their count; the one subtraction
+  // that takes the degree from >= k to < k deletes the vertex.
+  __device__ __forceinline__ void edges(const Src (&)[kPushBatch], const int (&)[kPushBatch],
+                                        const int (&u)[kPushBatch], const long long (&)[kPushBatch],
+                                        unsigned ok) {
+    bool want[kPushBatch];
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      want[q] = false;
+      if ((ok >> q) & 1u) want[q] = removed_at[u[q]] == INT_MAX;
+    }
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q)
+      if (want[q]) want[q] = cnt[u[q]] >= kk;  // stop once below k
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      const unsigned mask = __activemask();
+      const int key = want[q] ? u[q] : (int)(0x80000000u | lane_id());
+      const unsigned peers = __match_any_sync(mask, key);
+      if (!want[q] || (int)lane_id() != __ffs(peers) - 1) continue;
+      const unsigned c = (unsigned)__popc(peers);
+      const unsigned old = atomicSub(&cnt[u[q]], c);
+      if (old >= kk && old - c < kk) {
+        removed_at[u[q]] = it;
+        long long d = (long long)gload(off + u[q] + 1) - (long long)gload(off + u[q]);
+        ++nrec;
+        mrec += (unsigned long long)d;
+        online_record(u[q], degree_class(d, k), sh, w, k, grid);
+      }
     }
   }
 };

@@ -113,7 +113,9 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
   clear_next_slot(s, sh);
   det_filter_write(n, all, indeg, sh, a.w, kp, grid, 0, cnt);
   if (!grid_sync(s, grid, sh, k)) return;
-  // ---- phases 2-4: edge-balanced, task-aligned ranges of list 0 per warp
+  // ---- phases 2-4: balanced, task-aligned ranges of list 0 per warp.  A task
+  // weighs (in-degree + 1): zero-degree vertices still cost a slot, and they
+  // come in long runs (isolated vertices), so edges alone would not balance.
   const int32_t* l0 = a.w.list[0][0];
   const unsigned c0n = cnt[0];
   long long* pre = reinterpret_cast<long long*>(xalt + 3 * (size_t)n + 2);  // [c0n + 1] task start edges
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
   for (long long b = blockIdx.x; b < nblk; b += grid) {  // block degree sums
     unsigned long long t = 0;
     for (long long q = b * kBallotChunk + threadIdx.x; q < (b + 1) * kBallotChunk && q < c0n; q += kThreads)
-      t += (unsigned long long)indeg(l0[q]);
+      t += (unsigned long long)indeg(l0[q]) + 1ull;
     t = cta_sum_u64(t, sh);
     if (threadIdx.x == 0) bsum[b] = t;
   }
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     const long long t0 = b * kBallotChunk + (long long)threadIdx.x * kPer;
     unsigned long long mine = 0;
     for (int q = 0; q < kPer; ++q)
-      if (t0 + q < c0n) mine += (unsigned long long)indeg(l0[t0 + q]);
+      if (t0 + q < c0n) mine += (unsigned long long)indeg(l0[t0 + q]) + 1ull;
     // exclusive scan of `mine` over the CTA
     unsigned long long incl = mine;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     for (int q = 0; q < kPer; ++q)
       if (t0 + q < c0n) {
         pre[t0 + q] = (long long)ex;
-        ex += (unsigned long long)indeg(l0[t0 + q]);
+        ex += (unsigned long long)indeg(l0[t0 + q]) + 1ull;
       }
     __syncthreads();
   }

@@ -102,18 +102,38 @@ struct SsspPush {
     r.d = __shfl_sync(kFull, s.d, l);
     return r;
   }
-  __device__ __forceinline__ void edge(const Src& s, int, int u, long long p) {
-    const unsigned long long nd64 = (unsigned long long)s.d + gload(wt + p);
-    if (nd64 < dist[u]) {
-      const uint32_t nd = (uint32_t)nd64;
-      const uint32_t old = atomicMin(&dist[u], nd);
-      if (nd < old) {
-        pend[u] = 1;
-        if ((unsigned long long)nd < T) {
-          long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
+  // Weights and current distances of all the lane's edges are loaded first,
+  // then the improving ones land with atomicMin (issued back to back), then
+  // the improved vertices are flagged and recorded.
+  __device__ __forceinline__ void edges(const Src (&s)[kPushBatch], const int (&)[kPushBatch],
+                                        const int (&u)[kPushBatch], const long long (&p)[kPushBatch],
+                                        unsigned ok) {
+    unsigned long long nd[kPushBatch];
+    uint32_t cur[kPushBatch];
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      nd[q] = ~0ull;
+      cur[q] = 0;
+      if ((ok >> q) & 1u) {
+        nd[q] = (unsigned long long)s[q].d + gload(wt + p[q]);
+        cur[q] = dist[u[q]];
+      }
+    }
+    uint32_t old[kPushBatch];
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      old[q] = 0;
+      if (nd[q] < cur[q]) old[q] = atomicMin(&dist[u[q]], (uint32_t)nd[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      if (nd[q] < cur[q] && nd[q] < old[q]) {
+        pend[u[q]] = 1;
+        if (nd[q] < T) {
+          long long d = (long long)gload(off + u[q] + 1) - (long long)gload(off + u[q]);
           ++nrec;
           mrec += (unsigned long long)d;
-          online_record(u, degree_class(d, k), sh, w, k, grid);
+          online_record(u[q], degree_class(d, k), sh, w, k, grid);
         }
       }
     }
