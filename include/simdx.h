@@ -217,6 +217,40 @@ SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
 SIMDX_API int simdx_pagerank(simdx_graph *g, float damping, float l1_tol, int32_t max_iter,
                    float *rank, simdx_stats *stats, void *stream);
 
+/* ---------------------------------------------------------------- batches */
+/* Batched BFS (growth direction (a)): k sources in one persistent launch per
+ * 64 sources.  Each vertex keeps a 64-bit visited mask and a 64-bit frontier
+ * mask; Compute offers a neighbour's frontier mask and Combine is bitwise OR
+ * (a vote combine, Sec. 3.2): the first level pushes from the sources, later
+ * levels pull over the vertices some source has not reached (owner writes,
+ * no atomics).  srcs: host int32[k] in [0, n).  levels: device int32[k*n],
+ * row i = levels from srcs[i] (-1 unreachable), identical to k simdx_bfs
+ * calls.  The first call on a graph allocates the batch state (24 bytes per
+ * vertex); later calls reuse it.  Errors: EINVAL (k <= 0, source out of
+ * range, NULL pointers), ENOMEM. */
+SIMDX_API int simdx_bfs_batch(simdx_graph *g, const int32_t *srcs, int32_t k, int32_t *levels,
+                              simdx_stats *stats, void *stream);
+
+/* Batched SSSP: k sources in one persistent launch.  The k queries run on k
+ * virtual copies of the graph (state id inst * n + v, one CSR), so every
+ * iteration processes all queries' frontiers together.  srcs: host int32[k];
+ * dist: device uint32[k*n], row i = distances from srcs[i], identical to k
+ * simdx_sssp calls.  The first call for a given k allocates the batch state
+ * (about 45 bytes per vertex per query); later calls with the same k reuse
+ * it.  Needs k * n < 2^31.  Errors: EINVAL, ENOMEM. */
+SIMDX_API int simdx_sssp_batch(simdx_graph *g, const int32_t *srcs, int32_t k, uint32_t *dist,
+                               simdx_stats *stats, void *stream);
+
+/* BFS from several roots at once: every root is at level 0 and levels[v] is
+ * the distance to the nearest root.  On a block-diagonal batch of graphs
+ * (graphs packed into one CSR with their vertex ids offset) with one root per
+ * graph, each graph's slice of levels equals a BFS of that graph alone:
+ * growth direction (a)'s many-graphs-in-one-launch.  roots: host int32[k];
+ * levels: device int32[n].  The first call (or a larger k) allocates a small
+ * device copy of the roots.  Errors: EINVAL, ENOMEM. */
+SIMDX_API int simdx_bfs_multi(simdx_graph *g, const int32_t *roots, int32_t k, int32_t *levels,
+                              simdx_stats *stats, void *stream);
+
 /* ------------------------------------------------- no-allocation variant */
 /* BFS for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a deployment convenience).  Some callers cannot call

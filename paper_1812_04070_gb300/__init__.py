@@ -122,6 +122,35 @@ class Graph:
         simdx.simdx_bfs(self.handle, int(src), out.data_ptr(), stats, _stream_handle(stream))
         return out
 
+    def bfs_batch(self, srcs, out=None, stats: simdx_stats | None = None, stream=None):
+        """Levels from every source in `srcs` (one row per source), in one
+        persistent launch per 64 sources."""
+        torch = _torch()
+        k = len(srcs)
+        if out is None:
+            out = torch.empty((k, self.n), dtype=torch.int32, device=self.device)
+        assert out.dtype == torch.int32 and out.is_cuda and out.is_contiguous() and out.numel() >= k * self.n
+        simdx.simdx_bfs_batch(self.handle, srcs, out.data_ptr(), stats, _stream_handle(stream))
+        return out
+
+    def sssp_batch(self, srcs, out=None, stats: simdx_stats | None = None, stream=None):
+        """Distances from every source in `srcs` (one row per source, uint32
+        values in an int32 tensor), all queries in one persistent launch."""
+        torch = _torch()
+        k = len(srcs)
+        if out is None:
+            out = torch.empty((k, self.n), dtype=torch.int32, device=self.device)
+        assert out.dtype == torch.int32 and out.is_cuda and out.is_contiguous() and out.numel() >= k * self.n
+        simdx.simdx_sssp_batch(self.handle, srcs, out.data_ptr(), stats, _stream_handle(stream))
+        return out
+
+    def bfs_multi(self, roots, out=None, stats: simdx_stats | None = None, stream=None):
+        """BFS with all `roots` at level 0 (one root per graph of a packed batch)."""
+        torch = _torch()
+        out = self._out(out, torch.int32)
+        simdx.simdx_bfs_multi(self.handle, roots, out.data_ptr(), stats, _stream_handle(stream))
+        return out
+
     def sssp(self, src: int, out=None, stats: simdx_stats | None = None, stream=None):
         """uint32 distances returned in an int32 tensor (reinterpret with
         ``.view(torch.uint32)`` or mask 0xFFFFFFFF as unreached)."""

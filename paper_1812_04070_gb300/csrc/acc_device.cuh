@@ -85,7 +85,7 @@ struct Work {
   uint32_t* aux3[2];             // per-entry word of the class-3 lists (set to ~0 on append)
   long long list_cap;
   int32_t* chunk_cnt;            // [chunks][kClasses] for the deterministic ballot filter
-  uint32_t* chunk_part;          // per-chunk partial sums of chunked pull tasks
+  unsigned long long* chunk_part;  // per-chunk partial sums of chunked pull tasks
   int* chunk_done;               // chunks finished per class-3 task (reset by the last)
   int* warp_start;               // [grid * kWarps + 1] first task of each warp's edge range
   uint32_t* bm_nz;               // vertices with an in-edge (pull candidates)
@@ -501,16 +501,26 @@ __device__ __forceinline__ int chunk_item(const int* pref, int nb, int kc) {
 template <class A> struct Wide { using T = A; };
 template <> struct Wide<float> { using T = double; };
 
-__device__ __forceinline__ unsigned acc_bits(float x) { return __float_as_uint(x); }
-__device__ __forceinline__ unsigned acc_bits(unsigned x) { return x; }
-__device__ __forceinline__ void acc_from(unsigned b, float& x) { x = __uint_as_float(b); }
-__device__ __forceinline__ void acc_from(unsigned b, unsigned& x) { x = b; }
+__device__ __forceinline__ unsigned long long acc_bits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned long long acc_bits(unsigned x) { return x; }
+__device__ __forceinline__ unsigned long long acc_bits(unsigned long long x) { return x; }
+__device__ __forceinline__ void acc_from(unsigned long long b, float& x) { x = __uint_as_float((unsigned)b); }
+__device__ __forceinline__ void acc_from(unsigned long long b, unsigned& x) { x = (unsigned)b; }
+__device__ __forceinline__ void acc_from(unsigned long long b, unsigned long long& x) { x = b; }
+// Add a chunk sum into a task total: FP32 sums go through FP64, other
+// accumulators use the functor's own combine.
+template <class F>
+__device__ __forceinline__ void wide_combine(const F&, double& t, float y) { t += (double)y; }
+template <class F, class A>
+__device__ __forceinline__ void wide_combine(const F& f, A& t, A y) { f.combine(t, y); }
 
 // ----------------------------------------------------- push class driver
 // Visit every edge of every task in the four class lists.  F provides
 //   typename F::Src;                                 per-source state
 //   bool src(int v, Src& s, int cls, unsigned item); read state; false = skip
 //   static Src shfl(const Src&, int lane);
+//   int rv(int v);      the vertex whose CSR row task v walks (v itself except
+//                       for a batch of virtual graph copies)
 //   void edges(const Src (&s)[kPushBatch], const int (&v)[kPushBatch],
 //              const int (&u)[kPushBatch], const long long (&p)[kPushBatch],
 //              unsigned ok);      // bit q of ok: slot q holds edge (v[q] -> u[q])
@@ -565,7 +575,8 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
       const int item = chunk_item(sh.pref, nb, kc);
       const int first = item ? sh.pref[item - 1] : 0;
       const int v = lists[3][b0 + item];
-      const long long vb = gload(off + v), ve = gload(off + v + 1);
+      const int rv = f.rv(v);
+      const long long vb = gload(off + rv), ve = gload(off + rv + 1);
       const long long beg = vb + (long long)(kc - first) * ch;
       const long long end = beg + ch < ve ? beg + ch : ve;
       typename F::Src s;
@@ -580,7 +591,8 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     int v = lists[2][i];
     typename F::Src s;
     if (!f.src(v, s, 2, i)) continue;
-    long long beg = gload(off + v), end = gload(off + v + 1);
+    const int rv = f.rv(v);
+    long long beg = gload(off + rv), end = gload(off + rv + 1);
     push_strided(f, s, v, idx, beg, end, tid, kThreads);
     if (tid == 0) evisit += end - beg;
   }
@@ -592,7 +604,8 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
       int v = lists[1][i];
       typename F::Src s;
       if (!f.src(v, s, 1, i)) continue;
-      long long beg = gload(off + v), end = gload(off + v + 1);
+      const int rv = f.rv(v);
+      long long beg = gload(off + rv), end = gload(off + rv + 1);
       push_strided(f, s, v, idx, beg, end, lane, 32);
       if (lane == 0) evisit += end - beg;
     }
@@ -615,8 +628,9 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     if (i < lim) {
       v = lists[0][i];
       if (f.src(v, s, 0, i)) {
-        beg = gload(off + v);
-        deg = (int)(gload(off + v + 1) - beg);
+        const int rv = f.rv(v);
+        beg = gload(off + rv);
+        deg = (int)(gload(off + rv + 1) - beg);
       }
     }
     int incl = deg;
@@ -663,14 +677,15 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
 // For every task u in the class lists, combine (sum) a per-edge value over
 // u's in-edges and hand the total to F:
 //   typename F::Acc;  Acc zero();  void edge(Acc&, int u, int v, long long p);
+//   void combine(Acc&, Acc) const;   (commutative, associative: the Combine)
 //   void finish(int u, Acc total);   (called by exactly one thread per task)
 // Small tasks are summed by warp_segmented_sum; warp tasks lane-strided with
 // a fixed shuffle tree; CTA tasks with a fixed block tree; chunked tasks add
 // their chunk sums in chunk order.  The order of every sum is therefore fixed.
-template <class Acc>
-__device__ __forceinline__ Acc warp_sum(Acc v) {
+template <class F, class Acc>
+__device__ __forceinline__ Acc warp_sum(const F& f, Acc v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  for (int o = 16; o > 0; o >>= 1) f.combine(v, __shfl_xor_sync(kFull, v, o));
   return v;
 }
 
@@ -742,13 +757,13 @@ __device__ void warp_segmented_sum(F& f, const OffT* off, const int32_t* idx, co
         for (int d = 1; d < 32; d <<= 1) {
           Acc y = __shfl_down_sync(kFull, x, d);
           int jy = __shfl_down_sync(kFull, j, d);
-          if (lane + d < 32 && jy == j) x += y;
+          if (lane + d < 32 && jy == j) f.combine(x, y);
         }
         const int r0 = e0 + 32 * q;
         int h = excl - r0;
         h = h < 0 ? 0 : (h > 31 ? 31 : h);
         Acc part = __shfl_sync(kFull, x, h);
-        if (deg > 0 && excl < r0 + 32 && incl > r0) acc += part;
+        if (deg > 0 && excl < r0 + 32 && incl > r0) f.combine(acc, part);
       }
     }
     if (u >= 0) {
@@ -787,14 +802,14 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
       Acc a = f.zero();
 #pragma unroll 4
       for (long long p = beg + tid; p < end; p += kThreads) f.edge(a, u, gload(idx + p), p);
-      a = warp_sum(a);
+      a = warp_sum(f, a);
       __syncthreads();
       if (lane == 0) red[warp] = a;
       __syncthreads();
       if (tid == 0) {
         Acc t = f.zero();
 #pragma unroll
-        for (int q = 0; q < kWarps; ++q) t += red[q];
+        for (int q = 0; q < kWarps; ++q) f.combine(t, red[q]);
         evisit += end - beg;
         if (nch == 1) {
           f.finish(u, t);
@@ -804,12 +819,12 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
           const int done = atomicAdd(&w.chunk_done[b0 + item], 1);
           if (done == nch - 1) {
             __threadfence();
-            typename Wide<Acc>::T tot = 0;  // chunk sums added in chunk order, in a wider type
-            const volatile unsigned* part = w.chunk_part + gbase + first;
+            typename Wide<Acc>::T tot = (typename Wide<Acc>::T)f.zero();  // chunk sums in chunk order
+            const volatile unsigned long long* part = w.chunk_part + gbase + first;
             for (int j = 0; j < nch; ++j) {
               Acc y;
               acc_from(part[j], y);
-              tot += y;
+              wide_combine(f, tot, y);
             }
             w.chunk_done[b0 + item] = 0;
             f.finish(u, (Acc)tot);
@@ -827,14 +842,14 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
     Acc a = f.zero();
 #pragma unroll 4
     for (long long p = beg + tid; p < end; p += kThreads) f.edge(a, u, gload(idx + p), p);
-    a = warp_sum(a);
+    a = warp_sum(f, a);
     __syncthreads();
     if (lane == 0) red[warp] = a;
     __syncthreads();
     if (tid == 0) {
       Acc t = f.zero();
 #pragma unroll
-      for (int q = 0; q < kWarps; ++q) t += red[q];
+      for (int q = 0; q < kWarps; ++q) f.combine(t, red[q]);
       f.finish(u, t);
       evisit += end - beg;
     }
@@ -848,7 +863,7 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
     Acc a = f.zero();
 #pragma unroll 4
     for (long long p = beg + lane; p < end; p += 32) f.edge(a, u, gload(idx + p), p);
-    a = warp_sum(a);
+    a = warp_sum(f, a);
     if (lane == 0) {
       f.finish(u, a);
       evisit += end - beg;
@@ -874,14 +889,13 @@ __device__ void pull_classes(F& f, const OffT* off, const int32_t* idx, const in
 // pass 2 writes each chunk at the prefix of the counts of earlier chunks (the
 // prefix-scan concatenation of Sec. 3.3, no atomics).  The caller runs
 // count_pass, grid_sync, write_pass.
-template <class Pred, class Deg>
-__device__ void det_filter_count(int n, Pred pred, Deg deg, CtaShared& sh, const Work& w,
-                                 const Knobs& k, unsigned grid) {
+template <class Pred, class Cls>
+__device__ void det_filter_count(int n, Pred pred, Cls cls_of, CtaShared& sh, const Work& w, unsigned grid) {
   for (long long chunk = blockIdx.x; chunk * kBallotChunk < n; chunk += grid) {
     int my[kClasses] = {0, 0, 0, 0};
     for (int j = threadIdx.x; j < kBallotChunk; j += kThreads) {
       long long v = chunk * kBallotChunk + j;
-      if (v < n && pred((int)v)) my[degree_class(deg((int)v), k)]++;
+      if (v < n && pred((int)v)) my[cls_of((int)v)]++;
     }
 #pragma unroll
     for (int c = 0; c < kClasses; ++c) {
@@ -891,9 +905,9 @@ __device__ void det_filter_count(int n, Pred pred, Deg deg, CtaShared& sh, const
   }
 }
 
-template <class Pred, class Deg>
-__device__ void det_filter_write(int n, Pred pred, Deg deg, CtaShared& sh, const Work& w,
-                                 const Knobs& k, unsigned grid, int nbuf, unsigned* totals) {
+template <class Pred, class Cls>
+__device__ void det_filter_write(int n, Pred pred, Cls cls_of, CtaShared& sh, const Work& w, unsigned grid,
+                                 int nbuf, unsigned* totals) {
   const long long nchunks = ((long long)n + kBallotChunk - 1) / kBallotChunk;
   // totals over all chunks (every CTA computes them; fixed order)
 #pragma unroll
@@ -920,7 +934,7 @@ __device__ void det_filter_write(int n, Pred pred, Deg deg, CtaShared& sh, const
       int cls = 0;
       if (v < n && pred((int)v)) {
         act = true;
-        cls = degree_class(deg((int)v), k);
+        cls = cls_of((int)v);
       }
 #pragma unroll
       for (int c = 0; c < kClasses; ++c) {

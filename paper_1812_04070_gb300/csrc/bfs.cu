@@ -28,6 +28,8 @@ enum { kOnline = 1, kBallot = 2 };
 template <class OffT>
 struct BfsArgs {
   int n, src;
+  const int32_t* roots;  // device [nroots]; when nroots > 0 these replace src
+  int nroots;
   const OffT* off;
   const int32_t* idx;
   const OffT* ioff;
@@ -77,6 +79,7 @@ struct BfsPush {
                      unsigned g)
       : level(l), off(o), next(nx), sh(s), w(ww), k(kk), grid(g) {}
   __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
+  __device__ __forceinline__ int rv(int v) const { return v; }
   static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
   __device__ __forceinline__ void edges(const Src (&)[kPushBatch], const int (&)[kPushBatch],
                                         const int (&u)[kPushBatch], const long long (&)[kPushBatch],
@@ -285,22 +288,44 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   __syncthreads();
 
   // ---- phase 0: reset levels and bitmaps; seed the first task list
-  for (long long v = gtid; v < n; v += gthreads) a.level[v] = (v == a.src) ? 0 : -1;
+  const int src1 = a.nroots > 0 ? -1 : a.src;
+  for (long long v = gtid; v < n; v += gthreads) a.level[v] = (v == src1) ? 0 : -1;
   for (long long wd = gtid; wd < nwords; wd += gthreads) {
-    unsigned m = (wd == (a.src >> 5)) ? (1u << (a.src & 31)) : 0u;
+    unsigned m = (src1 >= 0 && wd == (src1 >> 5)) ? (1u << (src1 & 31)) : 0u;
     a.w.bm_vis[wd] = m;
     a.w.bm_f[0][wd] = m;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    long long d = (long long)a.off[a.src + 1] - (long long)a.off[a.src];
+  if (src1 >= 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    long long d = (long long)a.off[src1 + 1] - (long long)a.off[src1];
     int c = degree_class(d, k);
-    a.w.list[0][c][0] = a.src;
+    a.w.list[0][c][0] = src1;
+    if (c == 3) a.w.aux3[0][0] = 0xffffffffu;
     s->slot[0].list_cnt[c] = 1;
     s->slot[0].nact = 1;
     s->slot[0].mact = (unsigned long long)d;
   }
   clear_next_slot(s, sh);
   if (!grid_sync(s, grid, sh, k)) return;
+  if (a.nroots > 0) {
+    // several roots at level 0 (e.g. one per graph of a block-diagonal batch)
+    clear_next_slot(s, sh);
+    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < a.nroots; i += kThreads) {
+        const int r = a.roots[i];
+        if (atomicExch(&a.level[r], 0) == 0) continue;  // duplicate root
+        atomicOr(&a.w.bm_vis[r >> 5], 1u << (r & 31));
+        atomicOr(&a.w.bm_f[0][r >> 5], 1u << (r & 31));
+        const long long d = (long long)a.off[r + 1] - (long long)a.off[r];
+        const int c = degree_class(d, k);
+        const unsigned pos = atomicAdd(&slot.list_cnt[c], 1u);
+        a.w.list[0][c][pos] = r;
+        if (c == 3) a.w.aux3[0][pos] = 0xffffffffu;
+        atomicAdd(&slot.nact, 1ull);
+        atomicAdd(&slot.mact, (unsigned long long)d);
+      }
+    if (!grid_sync(s, grid, sh, k)) return;
+  }
 
   // uniform loop state (identical in every CTA)
   int L = 0;                 // level of the current frontier
@@ -309,17 +334,14 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   bool bm_ok = true;         // fbm[fb] and bm_vis are valid for level L
   int prev_dir = kPush;
   unsigned cnt[kClasses];
+  unsigned long long n_f, prev_n_f = 0, m_f;
   {
-    const PhaseSlot& p = s->slot[0];
+    const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+    n_f = p.nact;
+    m_f = p.mact;
   }
-  unsigned long long n_f = 1, prev_n_f = 0, m_f = 0;
-  long long m_u = a.m_total;
-  {
-    long long d = (long long)a.off[a.src + 1] - (long long)a.off[a.src];
-    m_f = (unsigned long long)d;
-    m_u -= d;
-  }
+  long long m_u = a.m_total - (long long)m_f;
   int it = 0, push_it = 0, pull_it = 0, ballot_it = 0, online_it = 0;
   long long evisit = 0, fsum = 0;
 
@@ -472,10 +494,13 @@ const void* bfs_kernel_ptr(int off_bits) {
 }
 
 template <class OffT>
-static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* stats, cudaStream_t st) {
+static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* stats, cudaStream_t st,
+                   const int32_t* d_roots = nullptr, int nroots = 0) {
   BfsArgs<OffT> a{};
   a.n = (int)g->n;
   a.src = src;
+  a.roots = d_roots;
+  a.nroots = nroots;
   a.off = (const OffT*)g->off;
   a.idx = g->idx;
   a.ioff = (const OffT*)g->in_off;
@@ -501,13 +526,15 @@ int bfs_launch_raw(int off_bits, int n, long long e, const void* off, const int3
   void* args[1];
   if (off_bits == 32) {
     BfsArgs<int32_t> a{};
-    a.n = n; a.src = src; a.off = (const int32_t*)off; a.idx = idx; a.ioff = a.off; a.iidx = idx;
+    a.n = n; a.src = src; a.roots = nullptr; a.nroots = 0;
+    a.off = (const int32_t*)off; a.idx = idx; a.ioff = a.off; a.iidx = idx;
     a.level = levels; a.m_total = e; a.w = w; a.k = k;
     args[0] = &a;
     return launch_coop((const void*)bfs_kernel<int32_t>, grid, args, st);
   }
   BfsArgs<long long> a{};
-  a.n = n; a.src = src; a.off = (const long long*)off; a.idx = idx; a.ioff = a.off; a.iidx = idx;
+  a.n = n; a.src = src; a.roots = nullptr; a.nroots = 0;
+  a.off = (const long long*)off; a.idx = idx; a.ioff = a.off; a.iidx = idx;
   a.level = levels; a.m_total = e; a.w = w; a.k = k;
   args[0] = &a;
   return launch_coop((const void*)bfs_kernel<long long>, grid, args, st);
@@ -523,4 +550,23 @@ extern "C" int simdx_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_sta
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return g->off_bits == 32 ? run_bfs<int32_t>(g, src, levels, stats, st)
                            : run_bfs<long long>(g, src, levels, stats, st);
+}
+
+extern "C" int simdx_bfs_multi(simdx_graph* g, const int32_t* roots, int32_t k, int32_t* levels, simdx_stats* stats,
+                               void* stream) {
+  if (!g || !roots || !levels || k <= 0 || g->n <= 0) return SIMDX_EINVAL;
+  for (int i = 0; i < k; ++i)
+    if (roots[i] < 0 || roots[i] >= g->n) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((size_t)k > g->roots_cap) {
+    cudaFree(g->d_roots);
+    g->d_roots = nullptr;
+    g->roots_cap = 0;
+    SIMDX_CUDA(cudaMalloc(&g->d_roots, sizeof(int32_t) * (size_t)k));
+    g->roots_cap = (size_t)k;
+  }
+  SIMDX_CUDA(cudaMemcpyAsync(g->d_roots, roots, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  return g->off_bits == 32 ? run_bfs<int32_t>(g, roots[0], levels, stats, st, g->d_roots, k)
+                           : run_bfs<long long>(g, roots[0], levels, stats, st, g->d_roots, k);
 }

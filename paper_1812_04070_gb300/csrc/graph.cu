@@ -259,7 +259,7 @@ static int alloc_workspace(simdx_graph* g) {
   // chunked class-3 tasks: at most e / huge_min + (tasks) chunks per phase
   const long long hm = std::max(1, g->cfg.huge_min);
   const size_t parts = (size_t)(g->e / hm + g->n + 16);
-  SIMDX_CUDA(cudaMalloc(&g->chunk_part, sizeof(uint32_t) * parts));
+  SIMDX_CUDA(cudaMalloc(&g->chunk_part, sizeof(unsigned long long) * parts));
   SIMDX_CUDA(cudaMalloc(&g->chunk_done, sizeof(int) * (size_t)(g->n + 16)));
   SIMDX_CUDA(cudaMemset(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16)));
   SIMDX_CUDA(cudaMalloc(&g->warp_start, sizeof(int) * ((size_t)g->grid_max * kWarps + 1)));
@@ -397,6 +397,9 @@ int simdx_graph_destroy(simdx_graph* g) {
   cudaFree(g->bitmaps);
   cudaFree(g->state);
   cudaFree(g->sync);
+  cudaFree(g->ms_state);
+  cudaFree(g->d_roots);
+  cudaFree(g->sb_state);
   cudaFree(g->chunk_cnt);
   cudaFree(g->dstats);
   cudaFree(g->trace);

@@ -52,6 +52,7 @@ struct KcorePush {
                        const Work& ww, const Knobs& kn, unsigned g)
       : removed_at(r), cnt(c), off(o), kk(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
   __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
+  __device__ __forceinline__ int rv(int v) const { return v; }
   static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
   // State of all the lane's targets is loaded first.  Then, per slot, lanes
   // of the warp that decrement the same vertex (hubs neighbour most deleted
@@ -106,6 +107,7 @@ struct KcorePull {
                        const Work& ww, const Knobs& kn, unsigned g)
       : removed_at(r), removed_w(r), cnt(c), off(o), kk(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
   __device__ __forceinline__ Acc zero() const { return 0u; }
+  __device__ __forceinline__ void combine(Acc& a, Acc b) const { a += b; }
   __device__ __forceinline__ void edge(Acc& a, int, int v, long long) { a += removed_at[v] >= it ? 1u : 0u; }
   __device__ __forceinline__ void finish(int u, Acc c) {
     cnt[u] = c;

@@ -54,6 +54,7 @@ struct PrPull {
   float base, d, dn;
   unsigned long long l1 = 0, dang = 0;  // 2^-60 fixed point, one rounding per vertex
   __device__ __forceinline__ Acc zero() const { return 0.f; }
+  __device__ __forceinline__ void combine(Acc& a, Acc b) const { a += b; }
   __device__ __forceinline__ void edge(Acc& a, int, int v, long long) { a += cin[v]; }
   __device__ __forceinline__ void finish(int u, Acc sum) {
     const float xn = base + d * (sum + dn);
@@ -85,11 +86,15 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
 
-  // Task classes for PageRank: every vertex of in-degree < med_max goes to one
-  // list (class 0) that is walked edge-balanced by warps; the rest keep their
-  // CTA / chunked classes.
-  Knobs kp = k;
-  kp.small_max = k.med_max;
+  // Task classes for PageRank: vertices of in-degree 0 (class 1) only take
+  // the constant teleport + dangling share; every other vertex of in-degree
+  // < med_max goes to one list (class 0) that is walked edge-balanced by
+  // warps; the rest keep their CTA (2) / chunked (3) classes.
+  const int med_max = k.med_max, huge_min = k.huge_min;
+  auto pr_class = [ioff, med_max, huge_min](int v) {
+    const long long d = (long long)gload(ioff + v + 1) - (long long)gload(ioff + v);
+    return d == 0 ? 1 : d < med_max ? 0 : d < huge_min ? 2 : 3;
+  };
   // ---- phase 0: x_0, c_0, D_0 and the per-chunk class counts
   {
     clear_next_slot(s, sh);
@@ -104,14 +109,14 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     }
     dang = cta_sum_u64(dang, sh);
     if (threadIdx.x == 0) atomicAdd(&slot.aux0, dang);
-    det_filter_count(n, all, indeg, sh, a.w, kp, grid);
+    det_filter_count(n, all, pr_class, sh, a.w, grid);
   }
   if (!grid_sync(s, grid, sh, k)) return;
   unsigned long long Dfix = s->slot[0].aux0;
   // ---- phase 1: sorted task lists of all vertices by in-degree
   unsigned cnt[kClasses];
   clear_next_slot(s, sh);
-  det_filter_write(n, all, indeg, sh, a.w, kp, grid, 0, cnt);
+  det_filter_write(n, all, pr_class, sh, a.w, grid, 0, cnt);
   if (!grid_sync(s, grid, sh, k)) return;
   // ---- phases 2-4: balanced, task-aligned ranges of list 0 per warp.  A task
   // weighs (in-degree + 1): zero-degree vertices still cost a slot, and they
@@ -210,6 +215,9 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
       ClassTimer tm(&slot);
       warp_segmented_sum<OffT>(f, ioff, a.iidx, l0, w_beg, w_end, evisit);
       tm.lap(0);
+      for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < cnt[1]; i += grid * kThreads)
+        f.finish(lists[1][i], 0.f);  // in-degree 0
+      tm.lap(1);
     }
     const unsigned long long l1 = cta_sum_u64(f.l1, sh);
     const unsigned long long dg = cta_sum_u64(f.dang, sh);

@@ -44,9 +44,16 @@ struct simdx_graph {
   uint32_t* aux3 = nullptr;  // [2][list_cap]
   long long list_cap = 0;
   int32_t* chunk_cnt = nullptr;
-  uint32_t* chunk_part = nullptr;
+  unsigned long long* chunk_part = nullptr;
   int* chunk_done = nullptr;
   int* warp_start = nullptr;
+  unsigned long long* ms_state = nullptr;  // batched BFS masks (allocated on first use)
+  int32_t* d_roots = nullptr;              // device copy of multi-root BFS roots
+  size_t roots_cap = 0;
+  void* sb_state = nullptr;                // batched SSSP lists and state (first use)
+  size_t sb_bytes = 0;
+  size_t sb_cap = 0;
+  int sb_k = 0;
   uint32_t* bitmaps = nullptr;  // [4][words]
   void* state = nullptr;        // 20 bytes per vertex
   simdx::Sync* sync = nullptr;

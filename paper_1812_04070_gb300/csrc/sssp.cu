@@ -23,9 +23,14 @@
 
 namespace simdx {
 
+// With V (a batch of k SSSP queries) the kernel runs on k virtual copies of
+// the graph: task / state id x = inst * nreal + v, inst = x / nreal; every
+// copy walks the one CSR, and copy inst starts at srcs[inst].
 template <class OffT>
 struct SsspArgs {
-  int n, src;
+  int n, src;           // n: state ids (nreal, or k * nreal for a batch)
+  int nreal, ninst;
+  const int32_t* srcs;  // device [ninst] (batch only)
   const OffT* off;
   const int32_t* idx;
   const uint32_t* wt;
@@ -34,11 +39,13 @@ struct SsspArgs {
   Knobs k;
 };
 
-template <class OffT>
+template <class OffT, bool V>
 struct SsspPush {
   struct Src {
     uint32_t d;
+    int base;  // inst * nreal: state id of the task's graph copy
   };
+  int nreal;
   uint32_t* dist;
   uint32_t* pdist;
   uint8_t* pend;
@@ -53,8 +60,10 @@ struct SsspPush {
   unsigned long long nrec = 0, mrec = 0;
   __device__ SsspPush(SsspArgs<OffT>& a, uint32_t* pd, uint8_t* pe, uint32_t* ax, unsigned long long t,
                       CtaShared& s, unsigned g)
-      : dist(a.dist), pdist(pd), pend(pe), off(a.off), wt(a.wt), aux3(ax), T(t), sh(s), w(a.w), k(a.k),
-        grid(g) {}
+      : nreal(a.nreal), dist(a.dist), pdist(pd), pend(pe), off(a.off), wt(a.wt), aux3(ax), T(t), sh(s), w(a.w),
+        k(a.k), grid(g) {}
+  __device__ __forceinline__ int base_of(int x) const { return V ? (int)(((unsigned)x / (unsigned)nreal) * nreal) : 0; }
+  __device__ __forceinline__ int rv(int x) const { return V ? x - base_of(x) : x; }
 
   // Decide once per task whether v still needs relaxing and with what d.
   __device__ __forceinline__ bool claim(int v, uint32_t& d) {
@@ -64,6 +73,7 @@ struct SsspPush {
     return true;
   }
   __device__ __forceinline__ bool src(int v, Src& s, int cls, unsigned item) {
+    s.base = base_of(v);
     if (cls == 0) return claim(v, s.d);
     if (cls == 1) {
       uint32_t d = 0;
@@ -100,6 +110,7 @@ struct SsspPush {
   static __device__ __forceinline__ Src shfl(const Src& s, int l) {
     Src r;
     r.d = __shfl_sync(kFull, s.d, l);
+    r.base = V ? __shfl_sync(kFull, s.base, l) : 0;
     return r;
   }
   // Weights and current distances of all the lane's edges are loaded first,
@@ -110,37 +121,39 @@ struct SsspPush {
                                         unsigned ok) {
     unsigned long long nd[kPushBatch];
     uint32_t cur[kPushBatch];
+    int x[kPushBatch];
 #pragma unroll
     for (int q = 0; q < kPushBatch; ++q) {
       nd[q] = ~0ull;
       cur[q] = 0;
+      x[q] = s[q].base + u[q];
       if ((ok >> q) & 1u) {
         nd[q] = (unsigned long long)s[q].d + gload(wt + p[q]);
-        cur[q] = dist[u[q]];
+        cur[q] = dist[x[q]];
       }
     }
     uint32_t old[kPushBatch];
 #pragma unroll
     for (int q = 0; q < kPushBatch; ++q) {
       old[q] = 0;
-      if (nd[q] < cur[q]) old[q] = atomicMin(&dist[u[q]], (uint32_t)nd[q]);
+      if (nd[q] < cur[q]) old[q] = atomicMin(&dist[x[q]], (uint32_t)nd[q]);
     }
 #pragma unroll
     for (int q = 0; q < kPushBatch; ++q) {
       if (nd[q] < cur[q] && nd[q] < old[q]) {
-        pend[u[q]] = 1;
+        pend[x[q]] = 1;
         if (nd[q] < T) {
           long long d = (long long)gload(off + u[q] + 1) - (long long)gload(off + u[q]);
           ++nrec;
           mrec += (unsigned long long)d;
-          online_record(u[q], degree_class(d, k), sh, w, k, grid);
+          online_record(x[q], degree_class(d, k), sh, w, k, grid);
         }
       }
     }
   }
 };
 
-template <class OffT>
+template <class OffT, bool V>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
   const unsigned grid = gridDim.x;
@@ -156,18 +169,32 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
 
-  // ---- phase 0: reset state, seed the source
-  for (long long v = gtid; v < n; v += gthreads) {
-    a.dist[v] = (v == a.src) ? 0u : 0xffffffffu;
-    pdist[v] = 0xffffffffu;
-    pend[v] = (v == a.src) ? 1 : 0;  // the source is the first pending vertex
+  const unsigned nreal = (unsigned)a.nreal;
+  // state id -> vertex of the one CSR
+  auto realv = [nreal](long long x) { return V ? (int)((unsigned long long)x % nreal) : (int)x; };
+  // ---- phase 0: reset state, seed the source(s)
+  for (long long x = gtid; x < n; x += gthreads) {
+    bool is_src;
+    if (V) {
+      const long long inst = x / nreal;
+      is_src = (x - inst * nreal) == a.srcs[inst];
+    } else {
+      is_src = x == a.src;
+    }
+    a.dist[x] = is_src ? 0u : 0xffffffffu;
+    pdist[x] = 0xffffffffu;
+    pend[x] = is_src ? 1 : 0;  // the source is the first pending vertex
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    long long d = (long long)a.off[a.src + 1] - (long long)a.off[a.src];
-    int c = degree_class(d, k);
-    a.w.list[0][c][0] = a.src;
-    if (c == 3) a.w.aux3[0][0] = 0xffffffffu;
-    s->slot[0].list_cnt[c] = 1;
+  if (blockIdx.x == 0) {
+    const int nsrc = V ? a.ninst : 1;
+    for (int i = threadIdx.x; i < nsrc; i += kThreads) {
+      const int v = V ? a.srcs[i] : a.src;
+      long long d = (long long)a.off[v + 1] - (long long)a.off[v];
+      int c = degree_class(d, k);
+      const unsigned pos = atomicAdd(&s->slot[0].list_cnt[c], 1u);
+      a.w.list[0][c][pos] = V ? i * (int)nreal + v : v;
+      if (c == 3) a.w.aux3[0][pos] = 0xffffffffu;
+    }
   }
   clear_next_slot(s, sh);
   if (!grid_sync(s, grid, sh, k)) return;
@@ -199,7 +226,10 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
         const uint32_t d = dist[v];
         return d < pdist[v] && (unsigned long long)d < TT;
       };
-      auto deg = [off = a.off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+      auto deg = [off = a.off, realv](int x) {
+        const int v = realv(x);
+        return (long long)gload(off + v + 1) - (long long)gload(off + v);
+      };
       auto visit = [=](int v) { pend[v] = 0; };
       ballot_filter(n, pred, deg, visit, sh, a.w, k, grid, lbuf, slot);
       if (!grid_sync(s, grid, sh, k)) return;
@@ -231,7 +261,10 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
           if (d < mymin) mymin = d;
           return (unsigned long long)d < TT;
         };
-        auto deg = [off = a.off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+        auto deg = [off = a.off, realv](int x) {
+        const int v = realv(x);
+        return (long long)gload(off + v + 1) - (long long)gload(off + v);
+      };
         auto visit = [=](int v) { pend[v] = 0; };
         ballot_filter(n, pred, deg, visit, sh, a.w, k, grid, lbuf, slot);
         unsigned long long c_cnt = cta_sum_u64(mycnt, sh);
@@ -279,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     online_reset(sh);
     __syncthreads();
     PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-    SsspPush<OffT> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
+    SsspPush<OffT, V> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
     const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                       a.w.list[lbuf][3]};
     push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
@@ -321,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
 }
 
 const void* sssp_kernel_ptr(int off_bits) {
-  return off_bits == 32 ? (const void*)sssp_kernel<int32_t> : (const void*)sssp_kernel<long long>;
+  return off_bits == 32 ? (const void*)sssp_kernel<int32_t, false> : (const void*)sssp_kernel<long long, false>;
 }
 
 template <class OffT>
@@ -329,13 +362,73 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
   SsspArgs<OffT> a{};
   a.n = (int)g->n;
   a.src = src;
+  a.nreal = (int)g->n;
+  a.ninst = 1;
+  a.srcs = nullptr;
   a.off = (const OffT*)g->off;
   a.idx = g->idx;
   a.wt = g->w;
   a.dist = dist;
   a.w = make_work(g);
   a.k = make_knobs(g);
-  const void* kern = (const void*)sssp_kernel<OffT>;
+  const void* kern = (const void*)sssp_kernel<OffT, false>;
+  int grid = grid_for(g, kern);
+  int rc = prepare_launch(g, st);
+  if (rc) return rc;
+  void* args[] = {&a};
+  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st);
+}
+
+// Batch state: task lists sized for k * n state ids, the class-3 words, the
+// processed distances and pending flags of every copy, and the sources.
+static int ensure_sssp_batch_state(simdx_graph* g, int k) {
+  const size_t ids = (size_t)k * (size_t)g->n;
+  const size_t cap = std::max<size_t>(ids, (size_t)g->grid_max * (size_t)g->bin_cap) + 64;
+  const size_t bytes = sizeof(int32_t) * 2 * kClasses * cap + sizeof(uint32_t) * 2 * cap +
+                       sizeof(uint32_t) * ids + ids + sizeof(int32_t) * (size_t)k + 256;
+  if (g->sb_state && g->sb_bytes >= bytes && g->sb_k == k) return SIMDX_OK;
+  cudaFree(g->sb_state);
+  g->sb_state = nullptr;
+  g->sb_bytes = 0;
+  SIMDX_CUDA(cudaMalloc(&g->sb_state, bytes));
+  g->sb_bytes = bytes;
+  g->sb_k = k;
+  g->sb_cap = cap;
+  return SIMDX_OK;
+}
+
+template <class OffT>
+static int run_sssp_batch(simdx_graph* g, const int32_t* srcs, int k, uint32_t* dist, simdx_stats* stats,
+                          cudaStream_t st) {
+  const size_t ids = (size_t)k * (size_t)g->n;
+  const size_t cap = g->sb_cap;
+  char* base = static_cast<char*>(g->sb_state);
+  int32_t* lists = reinterpret_cast<int32_t*>(base);
+  uint32_t* aux3 = reinterpret_cast<uint32_t*>(lists + 2 * kClasses * cap);
+  uint32_t* pdist = aux3 + 2 * cap;
+  uint8_t* pend = reinterpret_cast<uint8_t*>(pdist + ids);
+  int32_t* d_srcs = reinterpret_cast<int32_t*>(((uintptr_t)(pend + ids) + 15) & ~(uintptr_t)15);
+  SIMDX_CUDA(cudaMemcpyAsync(d_srcs, srcs, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  SsspArgs<OffT> a{};
+  a.n = (int)ids;
+  a.src = srcs[0];
+  a.nreal = (int)g->n;
+  a.ninst = k;
+  a.srcs = d_srcs;
+  a.off = (const OffT*)g->off;
+  a.idx = g->idx;
+  a.wt = g->w;
+  a.dist = dist;
+  a.w = make_work(g);
+  a.w.list_cap = (long long)cap;
+  for (int b = 0; b < 2; ++b) {
+    for (int c = 0; c < kClasses; ++c) a.w.list[b][c] = lists + ((size_t)b * kClasses + c) * cap;
+    a.w.aux3[b] = aux3 + (size_t)b * cap;
+  }
+  a.w.state = pdist;  // the kernel finds pend right after the ids processed distances
+  a.k = make_knobs(g);
+  const void* kern = (const void*)sssp_kernel<OffT, true>;
   int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
@@ -354,4 +447,18 @@ extern "C" int simdx_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_sta
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return g->off_bits == 32 ? run_sssp<int32_t>(g, src, dist, stats, st)
                            : run_sssp<long long>(g, src, dist, stats, st);
+}
+
+extern "C" int simdx_sssp_batch(simdx_graph* g, const int32_t* srcs, int32_t k, uint32_t* dist, simdx_stats* stats,
+                                void* stream) {
+  if (!g || !srcs || !dist || !g->w || k <= 0 || g->n <= 0) return SIMDX_EINVAL;
+  if ((long long)k * g->n >= (1ll << 31) - 64) return SIMDX_EINVAL;
+  for (int i = 0; i < k; ++i)
+    if (srcs[i] < 0 || srcs[i] >= g->n) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = ensure_sssp_batch_state(g, k);
+  if (rc) return rc;
+  return g->off_bits == 32 ? run_sssp_batch<int32_t>(g, srcs, k, dist, stats, st)
+                           : run_sssp_batch<long long>(g, srcs, k, dist, stats, st);
 }

@@ -81,6 +81,9 @@ SIGNATURES = {
     "simdx_kcore": (ctypes.c_int, [_vp, _u32, _vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_pagerank": (ctypes.c_int, [_vp, _f32, _f32, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_bfs_noalloc": (ctypes.c_int, [ctypes.POINTER(simdx_csr), _i32, _vp, _vp]),
+    "simdx_bfs_batch": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
+    "simdx_sssp_batch": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
+    "simdx_bfs_multi": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
 }
 
 
@@ -196,3 +199,27 @@ def simdx_bfs_noalloc(csr: simdx_csr, src: int, levels_ptr: int, stream: int | N
     """BFS that allocates no device memory (device CSR in, device levels out;
     at most 2^18 vertices).  See include/simdx.h."""
     _check(_lib().simdx_bfs_noalloc(ctypes.byref(csr), src, levels_ptr, stream), "simdx_bfs_noalloc")
+
+
+def simdx_bfs_batch(g: int, srcs, levels_ptr: int, stats: simdx_stats | None, stream: int | None) -> None:
+    """Batched BFS from the host int32 sources `srcs`; levels: device int32[k*n]."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    _check(_lib().simdx_bfs_batch(g, a.ctypes.data, int(a.size), levels_ptr,
+                                  ctypes.byref(stats) if stats is not None else None, stream), "simdx_bfs_batch")
+
+
+def simdx_sssp_batch(g: int, srcs, dist_ptr: int, stats: simdx_stats | None, stream: int | None) -> None:
+    """Batched SSSP from the host int32 sources `srcs`; dist: device uint32[k*n]."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    _check(_lib().simdx_sssp_batch(g, a.ctypes.data, int(a.size), dist_ptr,
+                                   ctypes.byref(stats) if stats is not None else None, stream), "simdx_sssp_batch")
+
+
+def simdx_bfs_multi(g: int, roots, levels_ptr: int, stats: simdx_stats | None, stream: int | None) -> None:
+    """BFS with every root of `roots` at level 0; levels: device int32[n]."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+    _check(_lib().simdx_bfs_multi(g, a.ctypes.data, int(a.size), levels_ptr,
+                                  ctypes.byref(stats) if stats is not None else None, stream), "simdx_bfs_multi")
