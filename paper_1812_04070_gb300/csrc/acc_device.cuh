@@ -452,8 +452,15 @@ struct ClassTimer {
 // ------------------------------------------------------- chunked tasks
 // Inclusive prefix (in sh.pref) of the chunk counts ceil(deg / ch) of the nb
 // <= kChunkBatch class-3 tasks `items`.  All threads of the CTA call it.
-template <class OffT>
-__device__ void chunk_prefix(const int32_t* items, int nb, const OffT* off, long long ch, CtaShared& sh) {
+struct IdentityVertex {
+  __device__ __forceinline__ int operator()(int v) const { return v; }
+};
+
+// `rv` maps a task id to the vertex whose CSR row it walks (the identity
+// except for a batch of virtual graph copies, whose ids exceed n).
+template <class OffT, class RV = IdentityVertex>
+__device__ void chunk_prefix(const int32_t* items, int nb, const OffT* off, long long ch, CtaShared& sh,
+                             RV rv = RV{}) {
   __syncthreads();
   const int b = threadIdx.x * 4;
   int x[4];
@@ -461,7 +468,7 @@ __device__ void chunk_prefix(const int32_t* items, int nb, const OffT* off, long
   for (int q = 0; q < 4; ++q) {
     x[q] = 0;
     if (b + q < nb) {
-      const int v = items[b + q];
+      const int v = rv(items[b + q]);
       const long long d = gload(off + v + 1) - gload(off + v);
       x[q] = (int)((d + ch - 1) / ch);
     }
@@ -567,9 +574,10 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
   ClassTimer tm(slot);
   // class 3: every task is cut into chunks of `ch` edges and the chunks of
   // all tasks are dealt round-robin to the CTAs (edge-balanced over the grid)
+  auto rvf = [&f](int v) { return f.rv(v); };
   for (unsigned b0 = 0; b0 < cnt[3]; b0 += kChunkBatch) {
     const int nb = (int)min((unsigned)kChunkBatch, cnt[3] - b0);
-    chunk_prefix(lists[3] + b0, nb, off, ch, sh);
+    chunk_prefix(lists[3] + b0, nb, off, ch, sh, rvf);
     const int total = sh.pref[nb - 1];
     for (int kc = blockIdx.x; kc < total; kc += grid) {
       const int item = chunk_item(sh.pref, nb, kc);
