@@ -235,9 +235,9 @@ SIMDX_API int simdx_bfs_batch(simdx_graph *g, const int32_t *srcs, int32_t k, in
  * virtual copies of the graph (state id inst * n + v, one CSR), so every
  * iteration processes all queries' frontiers together.  srcs: host int32[k];
  * dist: device uint32[k*n], row i = distances from srcs[i], identical to k
- * simdx_sssp calls.  The first call for a given k allocates the batch state
- * (about 45 bytes per vertex per query); later calls with the same k reuse
- * it.  Needs k * n < 2^31.  Errors: EINVAL, ENOMEM. */
+ * simdx_sssp calls.  The first call (or a larger k than any before)
+ * allocates the batch state (about 45 bytes per vertex per query); later
+ * calls with the same or a smaller k reuse it.  Needs k * n < 2^31.  Errors: EINVAL, ENOMEM. */
 SIMDX_API int simdx_sssp_batch(simdx_graph *g, const int32_t *srcs, int32_t k, uint32_t *dist,
                                simdx_stats *stats, void *stream);
 
@@ -250,6 +250,44 @@ SIMDX_API int simdx_sssp_batch(simdx_graph *g, const int32_t *srcs, int32_t k, u
  * device copy of the roots.  Errors: EINVAL, ENOMEM. */
 SIMDX_API int simdx_bfs_multi(simdx_graph *g, const int32_t *roots, int32_t k, int32_t *levels,
                               simdx_stats *stats, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+/* Query server over resident graphs (growth direction (b)): continuous
+ * batching.  A dispatcher thread keeps `slots` launches in flight on their
+ * own streams; whenever a slot is free it takes the oldest waiting query and
+ * every waiting query compatible with it (same graph and algorithm: up to 64
+ * BFS per bit-parallel launch, up to max_sssp SSSP per batched launch, all
+ * k-core queries with the same k share one run) and launches them.  Queries
+ * arriving while others run are admitted as soon as a slot frees up; the
+ * slots' kernels run concurrently (each slot launches 1/slots of the
+ * co-resident CTAs).  Every result equals the same query run alone.
+ *   graphs      resident symmetric graphs (not owned; keep them alive and do
+ *               not call other entry points on them while the server runs).
+ *   mem_budget  device bytes the server may use; the number of slots is
+ *               min(max_slots, budget / per-slot cost, CTAs per SM); ENOMEM if
+ *               not even one slot fits.  All device memory is allocated here:
+ *               serving allocates nothing.
+ * Results are written to the `out` pointer given at submit time (device
+ * memory or pinned host memory; int32[n] levels for BFS, uint32[n] distances
+ * for SSSP, uint8[n] membership for k-core with arg = k). */
+#define SIMDX_ALGO_BFS 1
+#define SIMDX_ALGO_SSSP 2
+#define SIMDX_ALGO_KCORE 3
+SIMDX_API int simdx_server_create(simdx_graph *const *graphs, int32_t ng, size_t mem_budget,
+                                  int32_t max_slots, int32_t max_sssp, simdx_server **out);
+/* Queue one query; *ticket identifies it.  Thread safe.  EINVAL on a bad
+ * graph index, algorithm or argument. */
+SIMDX_API int simdx_server_submit(simdx_server *s, int32_t graph, int32_t algo, int32_t arg,
+                                  void *out, uint64_t *ticket);
+/* Non-blocking: *done = 1 and SIMDX_OK (or the query's error) once its result
+ * is in `out` (the ticket is then released); SIMDX_ENOTREADY while pending. */
+SIMDX_API int simdx_server_poll(simdx_server *s, uint64_t ticket, int32_t *done);
+/* Block until the query is answered; releases the ticket. */
+SIMDX_API int simdx_server_wait(simdx_server *s, uint64_t ticket);
+SIMDX_API int simdx_server_info(simdx_server *s, int32_t *slots, uint64_t *launches,
+                                uint64_t *served, uint64_t *queued);
+/* Stop the dispatcher, finish launches in flight, free the server. */
+SIMDX_API int simdx_server_destroy(simdx_server *s);
 
 /* ------------------------------------------------- no-allocation variant */
 /* BFS for callers that cannot allocate device memory (the paper has no

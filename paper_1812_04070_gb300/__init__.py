@@ -16,7 +16,7 @@ import numpy as np
 from . import simdx
 from .simdx import SimdxError, simdx_config, simdx_stats
 
-__all__ = ["Graph", "simdx", "SimdxError", "simdx_config", "simdx_stats", "build"]
+__all__ = ["Graph", "Server", "simdx", "SimdxError", "simdx_config", "simdx_stats", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -176,3 +176,38 @@ class Graph:
         simdx.simdx_pagerank(self.handle, float(damping), float(tol), int(max_iter), out.data_ptr(), stats,
                              _stream_handle(stream))
         return out
+
+
+class Server:
+    """Continuous-batching query server over resident graphs (see
+    simdx_server_create in include/simdx.h).  Results land in the tensors
+    passed to submit (CUDA tensors or pinned CPU tensors)."""
+
+    BFS, SSSP, KCORE = simdx.ALGO_BFS, simdx.ALGO_SSSP, simdx.ALGO_KCORE
+
+    def __init__(self, graphs, mem_budget: int = 32 << 30, max_slots: int = 4, max_sssp: int = 8):
+        self.graphs = list(graphs)
+        self.handle = simdx.simdx_server_create([g.handle for g in self.graphs], mem_budget, max_slots, max_sssp)
+
+    def submit(self, graph: int, algo: int, arg: int, out) -> int:
+        return simdx.simdx_server_submit(self.handle, graph, algo, arg, out.data_ptr())
+
+    def poll(self, ticket: int) -> bool:
+        return simdx.simdx_server_poll(self.handle, ticket)
+
+    def wait(self, ticket: int) -> None:
+        simdx.simdx_server_wait(self.handle, ticket)
+
+    def info(self) -> dict:
+        return simdx.simdx_server_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            simdx.simdx_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

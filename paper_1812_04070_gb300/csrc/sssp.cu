@@ -387,7 +387,8 @@ static int ensure_sssp_batch_state(simdx_graph* g, int k) {
   const size_t cap = std::max<size_t>(ids, (size_t)g->grid_max * (size_t)g->bin_cap) + 64;
   const size_t bytes = sizeof(int32_t) * 2 * kClasses * cap + sizeof(uint32_t) * 2 * cap +
                        sizeof(uint32_t) * ids + ids + sizeof(int32_t) * (size_t)k + 256;
-  if (g->sb_state && g->sb_bytes >= bytes && g->sb_k == k) return SIMDX_OK;
+  g->sb_cap = cap;  // the layout follows the current k; any large enough buffer is reused
+  if (g->sb_state && g->sb_bytes >= bytes) return SIMDX_OK;
   cudaFree(g->sb_state);
   g->sb_state = nullptr;
   g->sb_bytes = 0;

@@ -17,6 +17,7 @@ import os
 from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, EBARRIER_TIMEOUT, EUNSUPPORTED, EBUSY, ENOTREADY = range(8)
+ALGO_BFS, ALGO_SSSP, ALGO_KCORE = 1, 2, 3
 INPUT_HOST = 1
 BORROW = 2
 
@@ -84,6 +85,13 @@ SIGNATURES = {
     "simdx_bfs_batch": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_sssp_batch": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_bfs_multi": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
+    "simdx_server_create": (ctypes.c_int, [_vp, _i32, ctypes.c_size_t, _i32, _i32, ctypes.POINTER(_vp)]),
+    "simdx_server_submit": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "simdx_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32)]),
+    "simdx_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "simdx_server_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "simdx_server_destroy": (ctypes.c_int, [_vp]),
 }
 
 
@@ -223,3 +231,41 @@ def simdx_bfs_multi(g: int, roots, levels_ptr: int, stats: simdx_stats | None, s
     a = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
     _check(_lib().simdx_bfs_multi(g, a.ctypes.data, int(a.size), levels_ptr,
                                   ctypes.byref(stats) if stats is not None else None, stream), "simdx_bfs_multi")
+
+
+def simdx_server_create(graphs, mem_budget: int, max_slots: int = 4, max_sssp: int = 8) -> int:
+    arr = (ctypes.c_void_p * len(graphs))(*graphs)
+    h = ctypes.c_void_p()
+    _check(_lib().simdx_server_create(arr, len(graphs), mem_budget, max_slots, max_sssp, ctypes.byref(h)),
+           "simdx_server_create")
+    return h.value
+
+
+def simdx_server_submit(s: int, graph: int, algo: int, arg: int, out_ptr: int) -> int:
+    t = ctypes.c_uint64()
+    _check(_lib().simdx_server_submit(s, graph, algo, arg, out_ptr, ctypes.byref(t)), "simdx_server_submit")
+    return t.value
+
+
+def simdx_server_poll(s: int, ticket: int) -> bool:
+    done = ctypes.c_int32()
+    rc = _lib().simdx_server_poll(s, ticket, ctypes.byref(done))
+    if rc == ENOTREADY:
+        return False
+    _check(rc, "simdx_server_poll")
+    return True
+
+
+def simdx_server_wait(s: int, ticket: int) -> None:
+    _check(_lib().simdx_server_wait(s, ticket), "simdx_server_wait")
+
+
+def simdx_server_info(s: int) -> dict:
+    sl, la, se, qu = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib().simdx_server_info(s, ctypes.byref(sl), ctypes.byref(la), ctypes.byref(se), ctypes.byref(qu)),
+           "simdx_server_info")
+    return {"slots": sl.value, "launches": la.value, "served": se.value, "queued": qu.value}
+
+
+def simdx_server_destroy(s: int) -> None:
+    _check(_lib().simdx_server_destroy(s), "simdx_server_destroy")
