@@ -54,6 +54,15 @@ WORKLOADS = {
                          desc="4096x4096 4-neighbour grid: BFS from corner 0"),
     "grid4096-sssp": dict(kind="grid", rows=4096, bits=64, algs=["sssp"], wmax=1000,
                           desc="4096x4096 4-neighbour grid, w in [1,1000]: SSSP from corner 0"),
+    "batch22": dict(kind="batch", scale=22, bits=32,
+                    desc="R-MAT scale 22 (n=4,194,304, ef 16, w in [1,64]): 64 BFS + 64 SSSP sources uniform over "
+                         "non-isolated vertices (seed 0xBA7C4), batched vs one call per query; plus 256 R-MAT "
+                         "graphs (n log-uniform in [1k,100k], ef 8..32) packed block-diagonally, multi-root BFS vs "
+                         "256 calls"),
+    "serve": dict(kind="serve", bits=32,
+                  desc="8 resident R-MAT graphs (scales 14,15,16,17,18,19,20,22; w in [1,64]); Poisson arrivals "
+                       "1k..50k/s; mix 50% BFS / 40% SSSP / 10% k-core(16); graph uniform; source uniform "
+                       "non-isolated (seed 0x5E77E); continuous-batching server vs one call per query"),
 }
 
 
@@ -393,6 +402,152 @@ def run_e2e(args, g, w, bits, algs, edges_step, world):
             "note": "host pinned CSR -> simdx_graph_create -> algorithms -> results to host, per step"}
 
 
+# ------------------------------------------------------------ batch / serve
+def _ev_time(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_batch(args, rank, world, local):
+    """Queries per second of the batched entry points vs one call per query
+    (configuration of the batching workload; identical outputs are checked)."""
+    import torch
+    import graphgen as gg
+    from paper_1812_04070_gb300 import Graph, build
+    torch.cuda.set_device(local)
+    build()
+    wl = WORKLOADS[args.workload]
+    g = gg.rmat(wl["scale"])
+    w = gg.weights(g, gg.weight_seed(wl["scale"]), 1, 64)
+    G = Graph(g.offsets.astype(np.int32), g.indices, weights=w)
+    srcs = [int(x) for x in gg.pick_sources(g, 64, 0xBA7C4)]
+    ob = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+    o1 = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+    reps = max(1, min(args.steps, 5))
+    res = {}
+    for name, bat, one in [("bfs", lambda: G.bfs_batch(srcs, out=ob), lambda: [G.bfs(s, out=o1[i]) for i, s in enumerate(srcs)]),
+                           ("sssp", lambda: G.sssp_batch(srcs, out=ob), lambda: [G.sssp(s, out=o1[i]) for i, s in enumerate(srcs)])]:
+        tb = _ev_time(bat, reps)
+        ts = _ev_time(one, reps)
+        same = bool(torch.equal(ob, o1))
+        res[name] = {"batched_qps": round(64 / tb * 1e3, 1), "per_query_qps": round(64 / ts * 1e3, 1),
+                     "batched_ms": round(tb, 3), "per_query_ms": round(ts, 3), "identical": same}
+    G.close()
+    graphs, gsrc = gg.multigraph_batch(count=256)
+    packed, bases = gg.pack(graphs)
+    roots = [int(x) for x in (gsrc.astype(np.int64) + bases[:-1])]
+    P = Graph(packed.offsets.astype(np.int32), packed.indices)
+    op = torch.empty(packed.n, dtype=torch.int32, device="cuda")
+    Gs = [Graph(x.offsets.astype(np.int32), x.indices) for x in graphs]
+    outs = [torch.empty(x.n, dtype=torch.int32, device="cuda") for x in graphs]
+    tb = _ev_time(lambda: P.bfs_multi(roots, out=op), reps)
+    ts = _ev_time(lambda: [Gi.bfs(int(s), out=o) for Gi, s, o in zip(Gs, gsrc, outs)], reps)
+    same = all(torch.equal(op[int(bases[i]):int(bases[i + 1])], outs[i]) for i in range(len(graphs)))
+    res["multigraph_bfs"] = {"batched_qps": round(256 / tb * 1e3, 1), "per_query_qps": round(256 / ts * 1e3, 1),
+                             "batched_ms": round(tb, 3), "per_query_ms": round(ts, 3), "identical": same}
+    for Gi in Gs:
+        Gi.close()
+    P.close()
+    tot_b = 64 / res["bfs"]["batched_qps"] + 64 / res["sssp"]["batched_qps"] + 256 / res["multigraph_bfs"]["batched_qps"]
+    value = (64 + 64 + 256) / tot_b
+    return {"metric": "queries/s (batched)", "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
+            "steps": reps, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic (seeded R-MAT)", "config": {"workload": args.workload,
+                                                                          "description": wl["desc"]},
+            "batches": res}
+
+
+def run_serve(args, rank, world, local):
+    """Open-loop Poisson serving: queries/s and p50/p99 latency (arrival to
+    result ready) per offered rate, vs one call per query."""
+    import torch
+    import graphgen as gg
+    from paper_1812_04070_gb300 import Graph, Server, build
+    torch.cuda.set_device(local)
+    build()
+    wl = WORKLOADS[args.workload]
+    scales = [14, 15, 16, 17, 18, 19, 20, 22]
+    raw = [gg.rmat(sc) for sc in scales]
+    ws = [gg.weights(g, gg.weight_seed(sc), 1, 64) for g, sc in zip(raw, scales)]
+    Gs = [Graph(g.offsets.astype(np.int32), g.indices, weights=w) for g, w in zip(raw, ws)]
+    srcs = [gg.pick_sources(g, 256, 0x5E77E + i) for i, g in enumerate(raw)]
+    rng = np.random.default_rng(0x5E77E)
+
+    def make(m):
+        q = []
+        for _ in range(m):
+            gi = int(rng.integers(0, len(raw)))
+            r = rng.random()
+            algo = Server.BFS if r < 0.5 else Server.SSSP if r < 0.9 else Server.KCORE
+            arg = 16 if algo == Server.KCORE else int(srcs[gi][int(rng.integers(0, len(srcs[gi])))])
+            q.append((gi, algo, arg))
+        return q
+
+    qs = make(400)
+    o32 = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in raw]
+    o8 = [torch.empty(g.n, dtype=torch.uint8, device="cuda") for g in raw]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for gi, a, arg in qs:
+        if a == Server.BFS:
+            Gs[gi].bfs(arg, out=o32[gi])
+        elif a == Server.SSSP:
+            Gs[gi].sssp(arg, out=o32[gi])
+        else:
+            Gs[gi].kcore(arg, out=o8[gi])
+    torch.cuda.synchronize()
+    per_query = len(qs) / (time.perf_counter() - t0)
+    srv = Server(Gs, mem_budget=64 << 30, max_slots=4, max_sssp=8)
+    rates = []
+    for rate in [1000, 2000, 5000, 10000, 20000, 50000]:
+        m = min(4000, rate * 2)
+        q = make(m)
+        bufs = [torch.empty(raw[gi].n, dtype=(torch.uint8 if a == Server.KCORE else torch.int32), device="cuda")
+                for gi, a, _ in q]
+        gaps = rng.exponential(1.0 / rate, size=m)
+        t_sub, t_done, tk = np.zeros(m), np.zeros(m), [None] * m
+        pending, i = set(), 0
+        start = time.perf_counter()
+        nxt = start
+        while i < m or pending:
+            now = time.perf_counter()
+            while i < m and now >= nxt:
+                gi, a, arg = q[i]
+                tk[i] = srv.submit(gi, a, arg, bufs[i])
+                t_sub[i] = nxt
+                pending.add(i)
+                nxt += gaps[i]
+                i += 1
+            for j in list(pending):
+                if srv.poll(tk[j]):
+                    t_done[j] = time.perf_counter()
+                    pending.discard(j)
+        tot = time.perf_counter() - start
+        lat = (t_done - t_sub) * 1e3
+        rates.append({"offered_qps": rate, "served_qps": round(m / tot, 1),
+                      "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                      "p99_ms": round(float(np.percentile(lat, 99)), 3)})
+    info = srv.info()
+    srv.close()
+    for G in Gs:
+        G.close()
+    best = max(r["served_qps"] for r in rates)
+    return {"metric": "queries/s (served)", "value": best, "unit": "queries/s", "n_gpus": world, "steps": len(rates),
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded R-MAT)", "config": {"workload": args.workload, "description": wl["desc"]},
+            "per_query_qps": round(per_query, 1), "rates": rates, "server": info}
+
+
 # ------------------------------------------------------------ CPU oracle legs
 def cpu_baseline(workload, g, w, budget_s=15.0):
     """The oracle as it stands (single thread), on a bounded sample of the
@@ -454,6 +609,10 @@ def main():
         dist.init_process_group("gloo")
     if args.impl == "reference":
         res = run_reference(args, rank, world)
+    elif WORKLOADS[args.workload]["kind"] == "batch":
+        res = run_batch(args, rank, world, local)
+    elif WORKLOADS[args.workload]["kind"] == "serve":
+        res = run_serve(args, rank, world, local)
     else:
         res = run_simdx(args, rank, world, local)
     if rank == 0 and res is not None:
