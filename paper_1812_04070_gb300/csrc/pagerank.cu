@@ -9,13 +9,11 @@
 //
 // All vertices are active in every iteration, so the ballot filter runs once
 // (Sec. 4: PageRank needs the ballot filter exactly at the first iteration)
-// and its sorted task lists are reused.  Vertices of in-degree in
-// [1, huge_min) form one list that is cut, once per run, into task-aligned
-// ranges of equal work (in-degree + 1 per task), one per warp, and each
-// warp's range into 32 equal lane ranges (a merge path: tasks may straddle
-// lanes).  Each lane sums its slots sequentially; a task split across lanes
-// is completed by a fixed-order segmented scan of the lanes' carries.  The
-// highest in-degrees are chunked over the whole grid.  Each vertex sums its in-neighbours'
+// and its sorted task lists are reused.  Vertices of in-degree < med_max form
+// one list that is cut, once per run, into task-aligned ranges of equal edge
+// count, one per warp (a degree prefix over the list and a binary search per
+// warp); each warp walks its range with warp_segmented_sum.  Higher in-degree
+// vertices keep the CTA-per-task and chunked classes.  Each vertex sums its in-neighbours'
 // contributions in FP32 in a fixed order (small tasks: 32-slot rounds summed
 // by a fixed shuffle tree; warp / CTA tasks: lane-strided partial sums and a
 // fixed tree; chunked tasks: chunk sums added in chunk order).  The two global
@@ -31,77 +29,6 @@ namespace simdx {
 constexpr double kFix = 1152921504606846976.0;  // 2^60
 
 __device__ __forceinline__ unsigned long long to_fix(double x) { return __double2ull_rn(x * kFix); }
-
-// One lane's share of a warp's merge path over list-0 tasks.  Task t owns
-// slots [pre[t], pre[t+1]): its in-edges, then one finish slot.  The lane
-// walks its slots [s, s_end) in order, summing each task's contributions
-// sequentially (unrolled by 4, independent loads); a task it both starts and
-// finishes is finished on the spot.  What crosses the lane's bounds is
-// returned: the task whose finish slot it reached but that began in an
-// earlier lane (tail) and the task still open at its end (carry).
-template <class OffT, class F>
-__device__ __forceinline__ void lane_merge_walk(F& f, const OffT* ioff, const int32_t* iidx, const int32_t* l0,
-                                                const long long* pre, int t, long long s, long long s_end,
-                                                int& tail_t, int& tail_u, float& tail_acc, int& open_t,
-                                                float& open_acc, long long& evisit) {
-  tail_t = -1;
-  tail_u = -1;
-  open_t = -1;
-  tail_acc = 0.f;
-  open_acc = 0.f;
-  if (s >= s_end) return;
-  long long ts = pre[t], te = pre[t + 1];
-  int u = l0[t];
-  long long beg = gload(ioff + u);
-  bool here = ts >= s;
-  float acc = 0.f;
-  while (true) {
-    const long long stop = te - 1 < s_end ? te - 1 : s_end;  // edge slots of t in this lane
-    long long x = s;
-    for (; x + 4 <= stop; x += 4) {
-      const long long p = beg + (x - ts);
-      const int v0 = gload(iidx + p), v1 = gload(iidx + p + 1), v2 = gload(iidx + p + 2), v3 = gload(iidx + p + 3);
-      float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-      f.edge(c0, u, v0, p);
-      f.edge(c1, u, v1, p + 1);
-      f.edge(c2, u, v2, p + 2);
-      f.edge(c3, u, v3, p + 3);
-      acc += c0;
-      acc += c1;
-      acc += c2;
-      acc += c3;
-    }
-    for (; x < stop; ++x) {
-      float c = 0.f;
-      f.edge(c, u, gload(iidx + beg + (x - ts)), beg + (x - ts));
-      acc += c;
-    }
-    evisit += stop - s;
-    s = stop;
-    if (s == s_end) {  // the lane ends inside t (before its finish slot)
-      open_t = t;
-      open_acc = acc;
-      return;
-    }
-    // s is t's finish slot
-    if (here) {
-      f.finish(u, acc);
-    } else {
-      tail_t = t;
-      tail_u = u;
-      tail_acc = acc;
-    }
-    ++s;
-    ++t;
-    acc = 0.f;
-    here = true;
-    if (s >= s_end) return;
-    ts = te;
-    te = pre[t + 1];
-    u = l0[t];
-    beg = gload(ioff + u);
-  }
-}
 
 template <class OffT>
 struct PrArgs {
@@ -161,12 +88,12 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
 
   // Task classes for PageRank: vertices of in-degree 0 (class 1) only take
   // the constant teleport + dangling share; every other vertex of in-degree
-  // < huge_min goes to one list (class 0) walked by the merge path; the
-  // highest in-degrees keep the chunked class 3.
-  const int huge_min = k.huge_min;
-  auto pr_class = [ioff, huge_min](int v) {
+  // < med_max goes to one list (class 0) that is walked edge-balanced by
+  // warps; the rest keep their CTA (2) / chunked (3) classes.
+  const int med_max = k.med_max, huge_min = k.huge_min;
+  auto pr_class = [ioff, med_max, huge_min](int v) {
     const long long d = (long long)gload(ioff + v + 1) - (long long)gload(ioff + v);
-    return d == 0 ? 1 : d < huge_min ? 0 : 3;
+    return d == 0 ? 1 : d < med_max ? 0 : d < huge_min ? 2 : 3;
   };
   // ---- phase 0: x_0, c_0, D_0 and the per-chunk class counts
   {
@@ -261,24 +188,6 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
   if (!grid_sync(s, grid, sh, k)) return;
   const unsigned my_warp = blockIdx.x * kWarps + (threadIdx.x >> 5);
   const unsigned w_beg = (unsigned)a.w.warp_start[my_warp], w_end = (unsigned)a.w.warp_start[my_warp + 1];
-  // this lane's slots of the warp's merge path and the task holding the first
-  long long m_s = 0, m_end = 0;
-  int m_t = (int)w_beg;
-  {
-    const int lane = lane_id();
-    const long long S0 = pre[w_beg], S1 = pre[w_end];
-    const long long L = (S1 - S0 + 31) / 32;
-    m_s = S0 + (long long)lane * L;
-    m_end = m_s + L < S1 ? m_s + L : S1;
-    if (m_s < m_end) {  // last task t in [w_beg, w_end) with pre[t] <= m_s
-      unsigned lo = w_beg, hi = w_end;
-      while (hi - lo > 1) {
-        unsigned mid = (lo + hi) >> 1;
-        if (pre[mid] <= m_s) lo = mid; else hi = mid;
-      }
-      m_t = (int)lo;
-    }
-  }
   const unsigned cnt_big[kClasses] = {0u, 0u, cnt[2], cnt[3]};
   const int32_t* lists[kClasses] = {a.w.list[0][0], a.w.list[0][1], a.w.list[0][2], a.w.list[0][3]};
 
@@ -304,27 +213,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     pull_classes<OffT>(f, ioff, a.iidx, lists, cnt_big, grid, red_f, k.huge_min, sh, a.w, evisit, &slot);
     {
       ClassTimer tm(&slot);
-      int tail_t, tail_u, open_t;
-      float tail_acc, open_acc;
-      lane_merge_walk<OffT>(f, ioff, a.iidx, l0, pre, m_t, m_s, m_end, tail_t, tail_u, tail_acc, open_t, open_acc,
-                            evisit);
-      // tasks split across lanes: inclusive segmented scan of the lanes' open
-      // carries (fixed shuffle order), then the lane holding a task's finish
-      // slot adds the carry of the lanes before it to its own tail
-      {
-        const int lane = lane_id();
-        float cv = open_acc;
-        int key = open_t;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const float y = __shfl_up_sync(kFull, cv, d);
-          const int ky = __shfl_up_sync(kFull, key, d);
-          if (lane >= d && ky == key) cv = y + cv;
-        }
-        const float prev = __shfl_up_sync(kFull, cv, 1);
-        const int kprev = __shfl_up_sync(kFull, key, 1);
-        if (tail_t >= 0) f.finish(tail_u, (lane > 0 && kprev == tail_t) ? prev + tail_acc : tail_acc);
-      }
+      warp_segmented_sum<OffT>(f, ioff, a.iidx, l0, w_beg, w_end, evisit);
       tm.lap(0);
       for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < cnt[1]; i += grid * kThreads)
         f.finish(lists[1][i], 0.f);  // in-degree 0
