@@ -400,6 +400,7 @@ int simdx_graph_destroy(simdx_graph* g) {
   cudaFree(g->ms_state);
   cudaFree(g->d_roots);
   cudaFree(g->sb_state);
+  cudaFree(g->pr_ws);
   cudaFree(g->chunk_cnt);
   cudaFree(g->dstats);
   cudaFree(g->trace);

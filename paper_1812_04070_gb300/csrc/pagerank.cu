@@ -8,27 +8,73 @@
 // stopping after the first iteration with ||x_{t+1} - x_t||_1 < tol.
 //
 // All vertices are active in every iteration, so the ballot filter runs once
-// (Sec. 4: PageRank needs the ballot filter exactly at the first iteration)
-// and its sorted task lists are reused.  Vertices of in-degree < med_max form
-// one list that is cut, once per run, into task-aligned ranges of equal edge
-// count, one per warp (a degree prefix over the list and a binary search per
-// warp); each warp walks its range with warp_segmented_sum.  Higher in-degree
-// vertices keep the CTA-per-task and chunked classes.  Each vertex sums its in-neighbours'
-// contributions in FP32 in a fixed order (small tasks: 32-slot rounds summed
-// by a fixed shuffle tree; warp / CTA tasks: lane-strided partial sums and a
-// fixed tree; chunked tasks: chunk sums added in chunk order).  The two global
-// sums (L1 change and dangling rank) add one 2^-60 fixed-point integer per
-// vertex, whose total does not depend on which CTA adds it or when: together
-// with the deterministic task lists this makes every run bit-identical.
-// One grid barrier per iteration: the sums of iteration t are read right
-// after its barrier, before iteration t+1 starts.
+// (Sec. 4: PageRank needs the ballot filter exactly at the first iteration);
+// it splits the vertices into those with in-edges (list 0, vertex order) and
+// those without (list 1).  Because the active set never changes, the compute
+// step does not walk tasks at all: the in-edge array is cut once per run into
+// equal ranges of 128-edge tiles, one range per warp, and each warp streams
+// its range (each lane four consecutive edges, one 16-byte load).  A bit per
+// in-edge marks the first edge of each row; rows are found from these bits,
+// their rank among the marked edges indexing list 0.  Within a tile a lane
+// sums its edges in order, restarting at row starts, and the sums of rows
+// that cross lanes are carried by a segmented scan over the 32 lanes; the
+// part of a row that crosses tiles is carried as an unevaluated FP32 pair
+// (TwoSum), close to FP64 accuracy at the FP32 rate.  A row that crosses a
+// warp boundary is finished by the last of its warps to arrive, which adds the
+// warps' partials in warp order (FP64).  Every sum therefore has a fixed order for a
+// given grid.  The two global sums (L1 change and dangling rank) are summed
+// per thread in FP32, in the thread's fixed order, and each thread's share is
+// added as one 2^-60 fixed-point integer, whose total does not depend on which
+// CTA adds it or when: together with the deterministic lists this makes every
+// run bit-identical.  One grid barrier per iteration: the sums of iteration t are
+// read right after its barrier, before iteration t+1 starts.
+#include <algorithm>
+
 #include "simdx_internal.h"
 
 namespace simdx {
 
 constexpr double kFix = 1152921504606846976.0;  // 2^60
+constexpr int kTile = 128;                       // in-edges per warp tile (4 per lane)
+constexpr int kPrChunk = 2048;                   // tiles per chunk of the cost prefix (8 per thread)
+constexpr int kPrRowCost = 4;                    // a row's finish costs about four in-edges
 
-__device__ __forceinline__ unsigned long long to_fix(double x) { return __double2ull_rn(x * kFix); }
+// round(x * 2^60) for a float 0 <= x < 8, from the float's exponent and
+// mantissa bits (integer arithmetic: FP64 runs at a small fraction of the
+// FP32 rate on this GPU, and this is done once per vertex per iteration).
+// Halves round up; values below 2^-61 give 0.
+__device__ __forceinline__ unsigned long long to_fix(float x) {
+  const unsigned b = __float_as_uint(x);
+  const int e = (int)(b >> 23) & 0xFF;
+  if (e == 0) return 0ull;  // zero or subnormal
+  const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
+  const int sh = e - 90;  // x * 2^60 = m * 2^(e - 127 - 23 + 60)
+  if (sh >= 0) return sh > 39 ? ~0ull >> 1 : m << sh;
+  if (sh < -25) return 0ull;
+  return (m + (1ull << (-sh - 1))) >> (-sh);
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest adds, kept apart
+// from any contraction by the _rn intrinsics).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Per-run layout of the in-edge walk.
+struct PrWalk {
+  uint32_t* head;            // [4 * ntiles + 8] bit p: in-edge p is the first of its row; bit E marks the end
+  unsigned long long* pre;   // [ntiles + 1] exclusive prefix of the tile costs
+  unsigned long long* csum;  // [ceil(ntiles / kPrChunk)] tile cost per chunk of tiles
+  int* tstart;               // [warps + 1] first tile of each warp's range
+  double* tailp;             // [warps] partial of the row left open at the end of a warp's range
+  double* headp;             // [warps] partial of the row that continues into a warp's range
+  int* done;                 // [warps] arrivals for the cross-warp row ending in that warp
+  long long ntiles;          // ceil(E / kTile)
+  int row_cost;              // cost of finishing a row, in in-edges
+  int vec4;                  // in-edge array is 16-byte aligned
+};
 
 template <class OffT>
 struct PrArgs {
@@ -38,64 +84,303 @@ struct PrArgs {
   const OffT* off;   // out-edges (out-degree)
   const OffT* ioff;  // in-edges
   const int32_t* iidx;
+  long long e;       // in-edges
   float* rank;
+  float* inv;        // [n] 1 / outdeg (0 for outdeg 0), set once per run
+  PrWalk wk;
   Work w;
   Knobs k;
 };
 
+// Per-iteration view: where c_t is read and x_{t+1}, c_{t+1} are written,
+// plus this thread's share of the two global sums.
 template <class OffT>
 struct PrPull {
-  using Acc = float;
   const float* cin;
   float* cout;
   const float* xold;
   float* xnew;
-  const OffT* off;
-  float base, d, dn;
-  unsigned long long l1 = 0, dang = 0;  // 2^-60 fixed point, one rounding per vertex
-  __device__ __forceinline__ Acc zero() const { return 0.f; }
-  __device__ __forceinline__ void combine(Acc& a, Acc b) const { a += b; }
-  __device__ __forceinline__ void edge(Acc& a, int, int v, long long) { a += cin[v]; }
-  __device__ __forceinline__ void finish(int u, Acc sum) {
-    const float xn = base + d * (sum + dn);
+  float dn;                             // d * D_t / n folded with the teleport term below
+  float l1 = 0.f, dang = 0.f;  // this thread's share, summed in its own fixed order
+  // x_{t+1}(u) and c_{t+1}(u) from the in-neighbour sum, given 1/outdeg(u)
+  // and x_t(u) already loaded (loads and stores kept apart so that several
+  // rows' loads are in flight together).
+  __device__ __forceinline__ void store(const PrArgs<OffT>& a, float base, int u, float sum, float iv, float xo) {
+    const float xn = base + a.d * (sum + dn);
     xnew[u] = xn;
-    const long long od = (long long)gload(off + u + 1) - (long long)gload(off + u);
-    cout[u] = od > 0 ? xn / (float)od : 0.f;
-    if (od == 0) dang += to_fix((double)xn);
-    l1 += to_fix(fabs((double)xn - (double)xold[u]));
+    cout[u] = xn * iv;
+    if (iv == 0.f) dang += xn;
+    l1 += fabsf(xn - xo);
+  }
+  __device__ __forceinline__ void finish(const PrArgs<OffT>& a, float base, int u, float sum) {
+    store(a, base, u, sum, a.inv[u], xold[u]);
   }
 };
 
+__device__ __forceinline__ float pick4(float s0, float s1, float s2, float s3, int j) {
+  return j == 0 ? s0 : j == 1 ? s1 : j == 2 ? s2 : s3;
+}
+
+struct CrossOut {
+  int u;      // the row's vertex when this warp finishes it, else -1
+  float sum;  // the row's total
+};
+
+// One of the warps w0..w1 covering row list0[rank] hands in its partial:
+// w0, holding the row's first edge, as `tail`, every later one as `head`.
+// `arrivals` counts the warps in w0..w1 with a nonempty range (an empty one
+// holds a zero head partial).  The last to arrive adds the partials in warp
+// order (FP64) and finishes the row.  One lane; rare, so kept out of line.
+__device__ __noinline__ CrossOut pr_cross(const PrWalk* wk, const int32_t* l0, int rank, int tail, double val,
+                                          int gw, int w0, int w1, int arrivals) {
+  (tail ? wk->tailp : wk->headp)[gw] = val;
+  __threadfence();
+  const int seen = atomicAdd(wk->done + w1, 1);
+  CrossOut r{-1, 0.f};
+  if (seen == arrivals - 1) {
+    __threadfence();
+    const volatile double* tp = wk->tailp;
+    const volatile double* hp = wk->headp;
+    double tot = tp[w0];
+    for (int j = w0 + 1; j <= w1; ++j) tot += hp[j];
+    wk->done[w1] = 0;
+    r.u = l0[rank];
+    r.sum = (float)tot;
+  }
+  return r;
+}
+
+// The cross-warp rows of one warp's range: the row that continues into it
+// (head) and the row left open at its end (tail), with the warps that share
+// them.  Set once per run.
+struct PrCross {
+  int head_rank = -2, hw0 = 0, hw1 = 0, hn = 0;  // -2: the range starts with a row start
+  int tail_w1 = 0, tn = 0;                       // hn, tn: arrivals
+};
+
+struct TileIn {
+  float x0, x1, x2, x3;
+  unsigned mw;  // the head word holding this lane's four bits
+  unsigned nx;  // lane 31: the head bit just after the tile
+};
+
 template <class OffT>
-__global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
+__device__ __forceinline__ TileIn pr_load(const PrArgs<OffT>& a, const float* cin, int t) {
+  const int lane = lane_id();
+  const long long p0 = (long long)t * kTile + 4 * lane;
+  const long long E = a.e;
+  TileIn r;
+  if (a.wk.vec4 && (long long)(t + 1) * kTile <= E) {  // a full tile (the usual case)
+    const int4 q = __ldg(reinterpret_cast<const int4*>(a.iidx + p0));
+    r.x0 = cin[q.x];
+    r.x1 = cin[q.y];
+    r.x2 = cin[q.z];
+    r.x3 = cin[q.w];
+  } else {
+    int v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    if (p0 < E) v0 = gload(a.iidx + p0);
+    if (p0 + 1 < E) v1 = gload(a.iidx + p0 + 1);
+    if (p0 + 2 < E) v2 = gload(a.iidx + p0 + 2);
+    if (p0 + 3 < E) v3 = gload(a.iidx + p0 + 3);
+    r.x0 = p0 < E ? cin[v0] : 0.f;
+    r.x1 = p0 + 1 < E ? cin[v1] : 0.f;
+    r.x2 = p0 + 2 < E ? cin[v2] : 0.f;
+    r.x3 = p0 + 3 < E ? cin[v3] : 0.f;
+  }
+  r.mw = a.wk.head[4 * (long long)t + (lane >> 3)];
+  r.nx = lane == 31 ? (a.wk.head[4 * (long long)t + 4] & 1u) : 0u;
+  return r;
+}
+
+// Sum one tile and finish the rows that end in it.  (ch, cl) (the same in
+// every lane) is the partial of the row open at the tile's start, `trank` the
+// number of row starts before the tile; both advance past the tile.
+template <class OffT>
+__device__ __forceinline__ void pr_tile(const PrArgs<OffT>& a, PrPull<OffT>& f, float base, const int32_t* l0, int c0n,
+                                        const TileIn& in, float& ch, float& cl, int& trank, const PrCross& cx, int gw,
+                                        unsigned& end_bit) {
+  const int lane = lane_id();
+  if (!__any_sync(kFull, in.mw | in.nx)) {  // no row starts or ends here: the open row goes on
+    float sum = ((in.x0 + in.x1) + in.x2) + in.x3;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);  // same value in every lane
+    float e;
+    two_sum(ch, sum, ch, e);
+    cl += e;
+    end_bit = 0u;
+    return;
+  }
+  const int sub = (lane & 7) * 4, wi = lane >> 3;
+  const unsigned hb = (in.mw >> sub) & 0xFu;  // row starts among this lane's four edges
+  const unsigned m0 = __shfl_sync(kFull, in.mw, 0), m1 = __shfl_sync(kFull, in.mw, 8);
+  const unsigned m2 = __shfl_sync(kFull, in.mw, 16), m3 = __shfl_sync(kFull, in.mw, 24);
+  int hp = __popc(in.mw & ((1u << sub) - 1u));  // row starts in earlier lanes of the tile
+  if (wi > 0) hp += __popc(m0);
+  if (wi > 1) hp += __popc(m1);
+  if (wi > 2) hp += __popc(m2);
+  unsigned hn = __shfl_down_sync(kFull, hb, 1) & 1u;  // a row starts right after this lane's edges
+  const unsigned nx = __shfl_sync(kFull, in.nx, 31);
+  if (lane == 31) hn = nx;
+  // running sums, restarting at row starts
+  const float s0 = in.x0;
+  const float s1 = (hb & 2u) ? in.x1 : s0 + in.x1;
+  const float s2 = (hb & 4u) ? in.x2 : s1 + in.x2;
+  const float s3 = (hb & 8u) ? in.x3 : s2 + in.x3;
+  const unsigned endm = (hb >> 1) | (hn << 3);  // bit j: edge j ends its row
+  const int first = hb ? __ffs(hb) - 1 : 4;     // first row start in the lane (4: none)
+  // segmented scan of the sums flowing across lanes: a lane is (pass, add),
+  // and the partial entering it leaves as pass ? in + add : add
+  int A = hb == 0 && hn == 0;
+  float B = hn ? 0.f : s3;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float By = __shfl_up_sync(kFull, B, o);
+    const int Ay = __shfl_up_sync(kFull, A, o);
+    if (lane >= o) {
+      if (A) B = By + B;
+      A = A & Ay;
+    }
+  }
+  int Ae = __shfl_up_sync(kFull, A, 1);
+  float Be = __shfl_up_sync(kFull, B, 1);
+  if (lane == 0) {
+    Ae = 1;
+    Be = 0.f;
+  }
+  const int A31 = __shfl_sync(kFull, A, 31);
+  const float B31 = __shfl_sync(kFull, B, 31);
+  // totals of the rows ending at each of the lane's edges: a row that began
+  // in the lane ends with its running sum; the row that entered from the left
+  // (ending at edge first-1) adds the partial carried into the lane
+  float v0 = s0, v1 = s1, v2 = s2, v3 = s3;
+  unsigned ends = endm;
+  const int rb = trank + hp - 1;  // rank of the row open at the lane's start
+  if (first > 0 && ((endm >> (first - 1)) & 1u)) {
+    float hi = Be, lo = 0.f, e1, e2;
+    if (Ae) {
+      two_sum(ch, Be, hi, e1);
+      lo = cl + e1;
+    }
+    two_sum(hi, pick4(s0, s1, s2, s3, first - 1), hi, e2);
+    lo += e2;
+    if (rb == cx.head_rank) {  // a row begun by an earlier warp
+      ends &= ~(1u << (first - 1));
+      const CrossOut c = pr_cross(&a.wk, l0, rb, 0, (double)hi + (double)lo, gw, cx.hw0, cx.hw1, cx.hn);
+      if (c.u >= 0) f.finish(a, base, c.u, c.sum);
+    } else {
+      const float tot = hi + lo;
+      v0 = first == 1 ? tot : v0;
+      v1 = first == 2 ? tot : v1;
+      v2 = first == 3 ? tot : v2;
+      v3 = first == 4 ? tot : v3;
+    }
+  }
+  // finish them: the rows' vertices, then their 1/outdeg and x_t, then stores
+  const int r0 = rb + (int)(hb & 1u), r1 = rb + __popc(hb & 3u), r2 = rb + __popc(hb & 7u), r3 = rb + __popc(hb);
+  const bool f0 = (ends & 1u) && r0 < c0n, f1 = (ends & 2u) && r1 < c0n;
+  const bool f2 = (ends & 4u) && r2 < c0n, f3 = (ends & 8u) && r3 < c0n;
+  int u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+  if (f0) u0 = l0[r0];
+  if (f1) u1 = l0[r1];
+  if (f2) u2 = l0[r2];
+  if (f3) u3 = l0[r3];
+  float i0 = 0.f, i1 = 0.f, i2 = 0.f, i3 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+  if (f0) { i0 = a.inv[u0]; o0 = f.xold[u0]; }
+  if (f1) { i1 = a.inv[u1]; o1 = f.xold[u1]; }
+  if (f2) { i2 = a.inv[u2]; o2 = f.xold[u2]; }
+  if (f3) { i3 = a.inv[u3]; o3 = f.xold[u3]; }
+  if (f0) f.store(a, base, u0, v0, i0, o0);
+  if (f1) f.store(a, base, u1, v1, i1, o1);
+  if (f2) f.store(a, base, u2, v2, i2, o2);
+  if (f3) f.store(a, base, u3, v3, i3, o3);
+  if (A31) {
+    float e;
+    two_sum(ch, B31, ch, e);
+    cl += e;
+  } else {
+    ch = B31;
+    cl = 0.f;
+  }
+  trank += __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+  end_bit = nx;
+}
+
+// One iteration's sums over the in-edges of this warp's tile range
+// [t_beg, t_end).
+template <class OffT>
+__device__ __forceinline__ void pr_walk(const PrArgs<OffT>& a, PrPull<OffT>& f, float base, const int32_t* l0,
+                                        int c0n, int gw, int t_beg, int t_end, int rank0, const PrCross& cx) {
+  if (t_beg >= t_end) return;
+  float ch = 0.f, cl = 0.f;  // the open row's partial, ch + cl unevaluated
+  int trank = rank0;
+  unsigned end_bit = 1;
+  for (int t = t_beg; t < t_end; t += 2) {
+    const TileIn x = pr_load(a, f.cin, t);
+    TileIn y{};
+    const bool two = t + 1 < t_end;
+    if (two) y = pr_load(a, f.cin, t + 1);
+    pr_tile(a, f, base, l0, c0n, x, ch, cl, trank, cx, gw, end_bit);
+    if (two) pr_tile(a, f, base, l0, c0n, y, ch, cl, trank, cx, gw, end_bit);
+  }
+  // the row still open at the range end continues in the next warp
+  if (!end_bit && lane_id() == 0) {
+    const int r = trank - 1;
+    if (r < c0n) {
+      const bool tail = r >= rank0;
+      const CrossOut c = pr_cross(&a.wk, l0, r, tail, (double)ch + (double)cl, gw, tail ? gw : cx.hw0,
+                                  tail ? cx.tail_w1 : cx.hw1, tail ? cx.tn : cx.hn);
+      if (c.u >= 0) f.finish(a, base, c.u, c.sum);
+    }
+  }
+}
+
+// Number of leading positions q in [0, len) where pred(q) holds, pred being
+// true on a prefix (32-ary search by one warp).
+template <class Pred>
+__device__ long long warp_partition_point(long long len, Pred pred) {
+  const int lane = lane_id();
+  long long lo = 0, hi = len;
+  while (lo < hi) {
+    const long long step = (hi - lo + 31) / 32;
+    const long long q = lo + (long long)(lane + 1) * step - 1;
+    const bool in = q < hi && pred(q);
+    const int k = __popc(__ballot_sync(kFull, in));
+    const long long nhi = lo + (long long)(k + 1) * step - 1;
+    lo += (long long)k * step;
+    hi = nhi < hi ? nhi : hi;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ unsigned long long tile_cost(const PrWalk& wk, long long t) {
+  const uint32_t* h = wk.head + 4 * t;
+  return (unsigned long long)kTile +
+         (unsigned long long)wk.row_cost * (unsigned)(__popc(h[0]) + __popc(h[1]) + __popc(h[2]) + __popc(h[3]));
+}
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_constant__ PrArgs<OffT> a) {
   __shared__ CtaShared sh;
-  __shared__ float red_f[kWarps];
   const unsigned grid = gridDim.x;
   Sync* s = a.w.sync;
   const Knobs& k = a.k;
   const int n = a.n;
+  const PrWalk& wk = a.wk;
   const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
   const long long gthreads = (long long)grid * kThreads;
+  const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const long long nwarps = (long long)grid * kWarps;
   float* xalt = reinterpret_cast<float*>(a.w.state);
-  float* cbuf[2] = {xalt + n, xalt + 2 * (size_t)n};
-  float* xbuf[2] = {a.rank, xalt};
+  float* cbuf0 = xalt + n;
+  float* cbuf1 = xalt + 2 * (size_t)n;
   const OffT* off = a.off;
   const OffT* ioff = a.ioff;
-  auto indeg = [ioff](int v) { return (long long)gload(ioff + v + 1) - (long long)gload(ioff + v); };
   auto all = [](int) { return true; };
+  auto pr_class = [ioff](int v) { return gload(ioff + v + 1) == gload(ioff + v) ? 1 : 0; };
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
 
-  // Task classes for PageRank: vertices of in-degree 0 (class 1) only take
-  // the constant teleport + dangling share; every other vertex of in-degree
-  // < med_max goes to one list (class 0) that is walked edge-balanced by
-  // warps; the rest keep their CTA (2) / chunked (3) classes.
-  const int med_max = k.med_max, huge_min = k.huge_min;
-  auto pr_class = [ioff, med_max, huge_min](int v) {
-    const long long d = (long long)gload(ioff + v + 1) - (long long)gload(ioff + v);
-    return d == 0 ? 1 : d < med_max ? 0 : d < huge_min ? 2 : 3;
-  };
-  // ---- phase 0: x_0, c_0, D_0 and the per-chunk class counts
+  // ---- phase 0: x_0, c_0, D_0, the per-chunk class counts; clear the row-start bits
   {
     clear_next_slot(s, sh);
     PhaseSlot& slot = s->slot[0];
@@ -103,60 +388,64 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     unsigned long long dang = 0;
     for (long long v = gtid; v < n; v += gthreads) {
       const long long od = (long long)gload(off + v + 1) - (long long)gload(off + v);
-      xbuf[0][v] = x0;
-      cbuf[0][v] = od > 0 ? x0 / (float)od : 0.f;
-      if (od == 0) dang += to_fix((double)x0);
+      a.rank[v] = x0;
+      cbuf0[v] = od > 0 ? x0 / (float)od : 0.f;
+      a.inv[v] = od > 0 ? 1.0f / (float)od : 0.f;
+      if (od == 0) dang += to_fix(x0);
     }
+    for (long long q = gtid; q < 4 * wk.ntiles + 8; q += gthreads) wk.head[q] = 0u;
+    for (long long q = gtid; q < nwarps; q += gthreads) wk.done[q] = 0;
     dang = cta_sum_u64(dang, sh);
     if (threadIdx.x == 0) atomicAdd(&slot.aux0, dang);
     det_filter_count(n, all, pr_class, sh, a.w, grid);
   }
   if (!grid_sync(s, grid, sh, k)) return;
   unsigned long long Dfix = s->slot[0].aux0;
-  // ---- phase 1: sorted task lists of all vertices by in-degree
+  // ---- phase 1: list 0 (rows with in-edges) and list 1 (none), vertex order;
+  // mark the first in-edge of every row, and the end of the array
   unsigned cnt[kClasses];
   clear_next_slot(s, sh);
   det_filter_write(n, all, pr_class, sh, a.w, grid, 0, cnt);
+  for (long long v = gtid; v < n; v += gthreads) {
+    const long long b = (long long)gload(ioff + v), e = (long long)gload(ioff + v + 1);
+    if (e > b) atomicOr(wk.head + (b >> 5), 1u << (b & 31));
+  }
+  if (gtid == 0) atomicOr(wk.head + (a.e >> 5), 1u << (a.e & 31));
   if (!grid_sync(s, grid, sh, k)) return;
-  // ---- phases 2-4: balanced, task-aligned ranges of list 0 per warp.  A task
-  // weighs (in-degree + 1): zero-degree vertices still cost a slot, and they
-  // come in long runs (isolated vertices), so edges alone would not balance.
-  const int32_t* l0 = a.w.list[0][0];
-  const unsigned c0n = cnt[0];
-  long long* pre = reinterpret_cast<long long*>(xalt + 3 * (size_t)n + 2);  // [c0n + 1] task start edges
-  pre = reinterpret_cast<long long*>((reinterpret_cast<uintptr_t>(pre) + 7) & ~(uintptr_t)7);
-  unsigned long long* bsum = reinterpret_cast<unsigned long long*>(a.w.chunk_part);
-  const long long nblk = ((long long)c0n + kBallotChunk - 1) / kBallotChunk;
+  // ---- phases 2-4: cut the tiles into one range per warp of equal cost
+  // (in-edges plus row_cost per row start): chunk sums, the per-tile prefix,
+  // then each warp searches the prefix for its range
+  const long long ntiles = wk.ntiles;
+  const long long nch = (ntiles + kPrChunk - 1) / kPrChunk;
   clear_next_slot(s, sh);
-  for (long long b = blockIdx.x; b < nblk; b += grid) {  // block degree sums
-    unsigned long long t = 0;
-    for (long long q = b * kBallotChunk + threadIdx.x; q < (b + 1) * kBallotChunk && q < c0n; q += kThreads)
-      t += (unsigned long long)indeg(l0[q]) + 1ull;
-    t = cta_sum_u64(t, sh);
-    if (threadIdx.x == 0) bsum[b] = t;
+  for (long long c = blockIdx.x; c < nch; c += grid) {
+    unsigned long long sum = 0;
+    for (long long q = c * kPrChunk + threadIdx.x; q < (c + 1) * kPrChunk && q < ntiles; q += kThreads)
+      sum += tile_cost(wk, q);
+    sum = cta_sum_u64(sum, sh);
+    if (threadIdx.x == 0) wk.csum[c] = sum;
   }
   if (!grid_sync(s, grid, sh, k)) return;
   clear_next_slot(s, sh);
-  unsigned long long mtot = 0;
+  unsigned long long total = 0;
   {
-    unsigned long long t = 0;
-    for (long long q = threadIdx.x; q < nblk; q += kThreads) t += bsum[q];
-    mtot = cta_sum_u64(t, sh);
+    unsigned long long sum = 0;
+    for (long long q = threadIdx.x; q < nch; q += kThreads) sum += wk.csum[q];
+    total = cta_sum_u64(sum, sh);
   }
-  for (long long b = blockIdx.x; b < nblk; b += grid) {  // task start edges
+  for (long long c = blockIdx.x; c < nch; c += grid) {
     unsigned long long run = 0;
-    for (long long q = threadIdx.x; q < b; q += kThreads) run += bsum[q];
+    for (long long q = threadIdx.x; q < c; q += kThreads) run += wk.csum[q];
     run = cta_sum_u64(run, sh);
-    constexpr int kPer = kBallotChunk / kThreads;  // consecutive tasks per thread
-    const long long t0 = b * kBallotChunk + (long long)threadIdx.x * kPer;
+    constexpr int kPer = kPrChunk / kThreads;
+    const long long q0 = c * kPrChunk + (long long)threadIdx.x * kPer;
     unsigned long long mine = 0;
-    for (int q = 0; q < kPer; ++q)
-      if (t0 + q < c0n) mine += (unsigned long long)indeg(l0[t0 + q]) + 1ull;
-    // exclusive scan of `mine` over the CTA
-    unsigned long long incl = mine;
+    for (int j = 0; j < kPer; ++j)
+      if (q0 + j < ntiles) mine += tile_cost(wk, q0 + j);
+    unsigned long long incl = mine;  // CTA-wide exclusive scan of `mine`
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long y = __shfl_up_sync(kFull, incl, o);
+      const unsigned long long y = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += y;
     }
     __syncthreads();
@@ -164,37 +453,68 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     __syncthreads();
     unsigned long long ex = run + incl - mine;
     for (int q = 0; q < warp; ++q) ex += sh.red64[q];
-    for (int q = 0; q < kPer; ++q)
-      if (t0 + q < c0n) {
-        pre[t0 + q] = (long long)ex;
-        ex += (unsigned long long)indeg(l0[t0 + q]) + 1ull;
+    for (int j = 0; j < kPer; ++j)
+      if (q0 + j < ntiles) {
+        wk.pre[q0 + j] = ex;
+        ex += tile_cost(wk, q0 + j);
       }
     __syncthreads();
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) pre[c0n] = (long long)mtot;
+  if (gtid == 0) wk.pre[ntiles] = total;
   if (!grid_sync(s, grid, sh, k)) return;
   clear_next_slot(s, sh);
-  const unsigned nwarps = grid * kWarps;
-  for (unsigned wv = blockIdx.x * kThreads + threadIdx.x; wv <= nwarps; wv += grid * kThreads) {
-    // first task whose start edge is >= this warp's share boundary
-    const long long x = (long long)((mtot * (unsigned long long)wv) / nwarps);
-    unsigned lo = 0, hi = c0n;
-    while (lo < hi) {
-      unsigned mid = (lo + hi) >> 1;
-      if (pre[mid] < x) lo = mid + 1; else hi = mid;
+  {
+    const unsigned long long target = total * (unsigned long long)gw / (unsigned long long)nwarps;
+    const unsigned long long* pre = wk.pre;
+    const long long tb = warp_partition_point(ntiles, [pre, target](long long q) { return pre[q] < target; });
+    if (lane_id() == 0) {
+      wk.tstart[gw] = (int)tb;
+      if (gw == nwarps - 1) wk.tstart[nwarps] = (int)ntiles;
     }
-    a.w.warp_start[wv] = wv == nwarps ? (int)c0n : (int)lo;
   }
   if (!grid_sync(s, grid, sh, k)) return;
-  const unsigned my_warp = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const unsigned w_beg = (unsigned)a.w.warp_start[my_warp], w_end = (unsigned)a.w.warp_start[my_warp + 1];
-  const unsigned cnt_big[kClasses] = {0u, 0u, cnt[2], cnt[3]};
-  const int32_t* lists[kClasses] = {a.w.list[0][0], a.w.list[0][1], a.w.list[0][2], a.w.list[0][3]};
+  // ---- each warp: rows starting before its range and the cross-warp rows
+  const int32_t* l0 = a.w.list[0][0];
+  const int32_t* l1 = a.w.list[0][1];
+  const int c0n = (int)cnt[0];
+  const int t_beg = wk.tstart[gw], t_end = wk.tstart[gw + 1];
+  int rank0 = 0;
+  PrCross cx;
+  if (t_beg >= t_end) {
+    if (lane_id() == 0) wk.headp[gw] = 0.0;  // an empty range adds nothing to a row crossing it
+  } else {
+    const int* ts = wk.tstart;
+    auto warp_of = [ts, nwarps](long long tile) {
+      return (int)warp_partition_point(nwarps, [ts, tile](long long w) { return ts[w] <= tile; }) - 1;
+    };
+    auto nonempty = [ts](int w0, int w1) {  // warps in [w0, w1] with a nonempty range
+      int c = 0;
+      for (int w = w0 + lane_id(); w <= w1; w += 32) c += ts[w] < ts[w + 1];
+      return (int)warp_sum_u64((unsigned long long)c);
+    };
+    auto rows_before = [ioff, l0, c0n](long long x) {
+      return (int)warp_partition_point(c0n, [ioff, l0, x](long long q) { return (long long)gload(ioff + l0[q]) < x; });
+    };
+    const long long x = (long long)t_beg * kTile;
+    rank0 = rows_before(x);
+    if (!((wk.head[x >> 5] >> (x & 31)) & 1u)) {
+      cx.head_rank = rank0 - 1;
+      const int u = l0[cx.head_rank];
+      cx.hw0 = warp_of((long long)gload(ioff + u) / kTile);
+      cx.hw1 = warp_of(((long long)gload(ioff + u + 1) - 1) / kTile);
+      cx.hn = nonempty(cx.hw0, cx.hw1);
+    }
+    const long long xe = (long long)t_end * kTile;
+    if (xe < a.e && !((wk.head[xe >> 5] >> (xe & 31)) & 1u)) {
+      const int u = l0[rows_before(xe) - 1];
+      cx.tail_w1 = warp_of(((long long)gload(ioff + u + 1) - 1) / kTile);
+      cx.tn = nonempty((int)gw, cx.tail_w1);
+    }
+  }
 
   const float base = (1.0f - a.d) / (float)n;
   int t = 0;
   double l1_last = 0.0;
-  long long evisit = 0;
   while (true) {
     if (t >= a.max_iter) break;
     const unsigned long long t_it = globaltimer();
@@ -202,39 +522,37 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(PrArgs<OffT> a) {
     clear_next_slot(s, sh);
     PhaseSlot& slot = s->slot[slot_of(sh.phase)];
     PrPull<OffT> f;
-    f.cin = cbuf[t & 1];
-    f.cout = cbuf[(t + 1) & 1];
-    f.xold = xbuf[t & 1];
-    f.xnew = xbuf[(t + 1) & 1];
-    f.off = off;
-    f.base = base;
-    f.d = a.d;
-    f.dn = (float)(((double)Dfix / kFix) / (double)n);
-    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt_big, grid, red_f, k.huge_min, sh, a.w, evisit, &slot);
+    f.cin = (t & 1) ? cbuf1 : cbuf0;
+    f.cout = (t & 1) ? cbuf0 : cbuf1;
+    f.xold = (t & 1) ? xalt : a.rank;
+    f.xnew = (t & 1) ? a.rank : xalt;
+    f.dn = __ull2float_rn(Dfix) * 8.67361737988403547e-19f / (float)n;  // D_t / n (2^-60 units)
     {
       ClassTimer tm(&slot);
-      warp_segmented_sum<OffT>(f, ioff, a.iidx, l0, w_beg, w_end, evisit);
+      pr_walk<OffT>(a, f, base, l0, c0n, (int)gw, t_beg, t_end, rank0, cx);
       tm.lap(0);
-      for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < cnt[1]; i += grid * kThreads)
-        f.finish(lists[1][i], 0.f);  // in-degree 0
+      for (unsigned i = (unsigned)gtid; i < cnt[1]; i += (unsigned)gthreads) f.finish(a, base, l1[i], 0.f);
       tm.lap(1);
     }
-    const unsigned long long l1 = cta_sum_u64(f.l1, sh);
-    const unsigned long long dg = cta_sum_u64(f.dang, sh);
+    const unsigned long long l1s = cta_sum_u64(to_fix(f.l1), sh);
+    const unsigned long long dg = cta_sum_u64(to_fix(f.dang), sh);
     if (threadIdx.x == 0) {
       atomicAdd(&slot.aux0, dg);
-      atomicAdd(&slot.aux1, l1);
+      atomicAdd(&slot.aux1, l1s);
     }
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     Dfix = p.aux0;
     l1_last = (double)p.aux1 / kFix;
-    trace_put(a.w, t, 2 | (2 << 8), n, 0, (long long)p.aux1, t_it);
+    trace_put(a.w, t, 2 | (2 << 8), n, a.e, (long long)p.aux1, t_it);
     trace_classes(a.w, t, p);
     ++t;
     if (l1_last < (double)a.tol) break;
   }
-  // ---- result: x_t lives in xbuf[t & 1]
+  long long evisit = 0;  // in-edges this warp summed, every iteration
+  if (lane_id() == 0 && t_beg < t_end)
+    evisit = (long long)t * (min((long long)t_end * kTile, a.e) - (long long)t_beg * kTile);
+  // ---- result: x_t is in rank for even t, in xalt for odd t
   if (t & 1)
     for (long long v = gtid; v < n; v += gthreads) a.rank[v] = xalt[v];
   unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
@@ -271,11 +589,43 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   a.off = (const OffT*)g->off;
   a.ioff = (const OffT*)g->in_off;
   a.iidx = g->in_idx;
+  a.e = g->e;
   a.rank = rank;
+  a.inv = static_cast<float*>(g->state) + 3 * (size_t)g->n;
   a.w = make_work(g);
   a.k = make_knobs(g);
   const void* kern = (const void*)pagerank_kernel<OffT>;
   int grid = grid_for(g, kern);
+  // walk layout: row-start bits, tile cost prefix and chunk sums, warp
+  // ranges, per-warp partials and arrival counters
+  const long long ntiles = (g->e + kTile - 1) / kTile;
+  const long long nw = (long long)grid * kWarps;
+  const long long nch = (ntiles + kPrChunk - 1) / kPrChunk;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t head_b = up(sizeof(uint32_t) * (size_t)(4 * ntiles + 8));
+  const size_t pre_b = up(sizeof(unsigned long long) * (size_t)(ntiles + 1));
+  const size_t csum_b = up(sizeof(unsigned long long) * (size_t)(nch + 1));
+  const size_t ts_b = up(sizeof(int) * (size_t)(nw + 1));
+  const size_t part_b = up(sizeof(double) * (size_t)nw);
+  const size_t bytes = head_b + pre_b + csum_b + ts_b + 2 * part_b + up(sizeof(int) * (size_t)nw);
+  if (!g->pr_ws || g->pr_bytes < bytes) {
+    cudaFree(g->pr_ws);
+    g->pr_ws = nullptr;
+    g->pr_bytes = 0;
+    SIMDX_CUDA(cudaMalloc(&g->pr_ws, bytes));
+    g->pr_bytes = bytes;
+  }
+  char* base = static_cast<char*>(g->pr_ws);
+  a.wk.head = reinterpret_cast<uint32_t*>(base);
+  a.wk.pre = reinterpret_cast<unsigned long long*>(base + head_b);
+  a.wk.csum = reinterpret_cast<unsigned long long*>(base + head_b + pre_b);
+  a.wk.tstart = reinterpret_cast<int*>(base + head_b + pre_b + csum_b);
+  a.wk.tailp = reinterpret_cast<double*>(base + head_b + pre_b + csum_b + ts_b);
+  a.wk.headp = reinterpret_cast<double*>(base + head_b + pre_b + csum_b + ts_b + part_b);
+  a.wk.done = reinterpret_cast<int*>(base + head_b + pre_b + csum_b + ts_b + 2 * part_b);
+  a.wk.ntiles = ntiles;
+  a.wk.row_cost = kPrRowCost;
+  a.wk.vec4 = (reinterpret_cast<uintptr_t>(g->in_idx) & 15) == 0;
   int rc = prepare_launch(g, st);
   if (rc) return rc;
   void* args[] = {&a};

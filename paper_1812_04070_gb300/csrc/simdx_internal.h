@@ -54,6 +54,8 @@ struct simdx_graph {
   size_t sb_bytes = 0;
   size_t sb_cap = 0;
   int sb_k = 0;
+  void* pr_ws = nullptr;                   // PageRank in-edge walk layout (first use)
+  size_t pr_bytes = 0;
   uint32_t* bitmaps = nullptr;  // [4][words]
   void* state = nullptr;        // 20 bytes per vertex
   simdx::Sync* sync = nullptr;
