@@ -85,6 +85,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (a job lasts as long as its slowest
+    rank).  Every rank must call it."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units: all units over the slowest rank's time."""
+    return units_per_rank * world / max_over_ranks(seconds, world)
+
+
 def make_graph(wl):
     import graphgen as gg
     if wl["kind"] == "rmat":
@@ -308,13 +326,9 @@ def run_simdx(args, rank, world, local):
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     kern_ms = {a: [x.elapsed_time(y) for x, y in evs[a]] for a in algs}
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world)
     edges_step = sum(work[a][0] for a in algs)
-    value = edges_step * args.steps * world / (total_ms / 1e3) / 1e9
+    value = job_rate(edges_step * args.steps, total_ms / 1e3, world) / 1e9
     # dominant kernel and its roofline
     mean_k = {a: statistics.mean(kern_ms[a]) for a in algs}
     dom = max(algs, key=lambda a: mean_k[a])
@@ -391,12 +405,8 @@ def run_e2e(args, g, w, bits, algs, edges_step, world):
         t0 = time.perf_counter()
         one()
         ts.append(time.perf_counter() - t0)
-    tot = sum(ts)
-    if world > 1:
-        t = torch.tensor([tot], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = float(t.item())
-    return {"value": round(edges_step * len(ts) * world / tot / 1e9, 3), "unit": "GTEPS",
+    tot = max_over_ranks(sum(ts), world)
+    return {"value": round(job_rate(edges_step * len(ts), tot, world) / 1e9, 3), "unit": "GTEPS",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": round(tot / len(ts) * 1e3, 3),
             "note": "host pinned CSR -> simdx_graph_create -> algorithms -> results to host, per step"}
@@ -459,7 +469,7 @@ def run_batch(args, rank, world, local):
         Gi.close()
     P.close()
     tot_b = 64 / res["bfs"]["batched_qps"] + 64 / res["sssp"]["batched_qps"] + 256 / res["multigraph_bfs"]["batched_qps"]
-    value = (64 + 64 + 256) / tot_b
+    value = job_rate(64 + 64 + 256, tot_b, world)
     return {"metric": "queries/s (batched)", "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
             "steps": reps, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic (seeded R-MAT)", "config": {"workload": args.workload,
@@ -534,7 +544,7 @@ def run_serve(args, rank, world, local):
                     pending.discard(j)
         tot = time.perf_counter() - start
         lat = (t_done - t_sub) * 1e3
-        rates.append({"offered_qps": rate, "served_qps": round(m / tot, 1),
+        rates.append({"offered_qps": rate, "served_qps": round(job_rate(m, tot, world), 1),
                       "p50_ms": round(float(np.percentile(lat, 50)), 3),
                       "p99_ms": round(float(np.percentile(lat, 99)), 3)})
     info = srv.info()

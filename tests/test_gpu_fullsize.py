@@ -1,0 +1,102 @@
+"""GPU parity at the full sizes of the measured workloads, in the launch
+configuration bench.py times (default knobs, grid from the occupancy
+calculator, the same offset widths and weight ranges).
+
+Scale 16 / 20 / 24 R-MAT and the 4096 x 4096 grid are compared with the
+oracle on every vertex; of the scale-22 batches, a sample of rows is compared
+(the oracle runs one query at a time) and the other rows must equal the
+single-query entry point.  Graph generation at scale 24 takes about half a
+minute on the host.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from gpu_util import check_pagerank, make
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    import torch
+    from paper_1812_04070_gb300 import build
+    build()
+    torch.cuda.set_device(0)
+
+
+def _rmat(scale, wmax=64):
+    g = gg.rmat(scale)
+    return g, gg.weights(g, gg.weight_seed(scale), 1, wmax)
+
+
+def test_rmat16_bfs():
+    g, _ = _rmat(16)
+    G = make(g, bits=32)
+    assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
+    G.close()
+
+
+def test_rmat20_sssp_kcore_pagerank():
+    g, w = _rmat(20)
+    G = make(g, w, bits=32)
+    assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
+    for k in (16, 32):
+        inc, resid = G.kcore(k)
+        ei, er = oracle.kcore(g.offsets, g.indices, k)
+        assert np.array_equal(inc.cpu().numpy(), ei)
+        assert np.array_equal(resid.cpu().numpy(), er)
+    rel, t, t_stop, st = check_pagerank(G, g)
+    assert st.status == 0
+    assert rel <= 1e-6, rel
+    assert abs(t - t_stop) <= 1, (t, t_stop)
+    G.close()
+
+
+def test_rmat24_bfs_sssp():
+    g, w = _rmat(24)
+    G = make(g, w, bits=64)
+    assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
+    assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
+    G.close()
+
+
+def test_grid4096_bfs_sssp():
+    g = gg.grid(4096, 4096)
+    w = gg.weights(g, 0x6121D ^ 0xFFFF, 1, 1000)
+    G = make(g, w, bits=64)
+    lev = G.bfs(0).cpu().numpy()
+    assert lev.max() == 8190  # level(r, c) = r + c from the corner
+    assert np.array_equal(lev, oracle.bfs(g.offsets, g.indices, 0))
+    assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
+    G.close()
+
+
+def test_rmat22_batches_sampled():
+    import torch
+    g, w = _rmat(22)
+    G = make(g, w, bits=32)
+    srcs = [int(x) for x in gg.pick_sources(g, 64, 0xBA7C4)]
+    lev = G.bfs_batch(srcs)
+    dist = G.sssp_batch(srcs)
+    one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for i in range(0, 64, 9):  # rows the oracle checks
+        assert np.array_equal(lev[i].cpu().numpy(), oracle.bfs(g.offsets, g.indices, srcs[i])), i
+        assert np.array_equal(dist[i].cpu().numpy().view(np.uint32),
+                              oracle.sssp(g.offsets, g.indices, w, srcs[i])), i
+    for i in range(64):  # every row equals the single-query call
+        assert torch.equal(lev[i], G.bfs(srcs[i], out=one)), i
+        assert torch.equal(dist[i], G.sssp(srcs[i], out=one)), i
+    G.close()
+
+
+def test_256_packed_graphs_bfs():
+    graphs, srcs = gg.multigraph_batch(count=256)
+    packed, bases = gg.pack(graphs)
+    roots = [int(x) for x in (srcs.astype(np.int64) + bases[:-1])]
+    G = make(packed, bits=32)
+    lev = G.bfs_multi(roots).cpu().numpy()
+    for i, x in enumerate(graphs):
+        assert np.array_equal(lev[bases[i]:bases[i + 1]], oracle.bfs(x.offsets, x.indices, int(srcs[i]))), i
+    G.close()
