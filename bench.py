@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--autotune", action="store_true",
+                   help="before warm-up, tune each algorithm's knobs (simdx_autotune) on its own copy of the "
+                        "graph; the timed steps and e2e use the tuned knobs")
     return p.parse_args()
 
 
@@ -181,10 +184,12 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources a kernel is built from: its own file
+    (<algorithm>.cu for <algorithm>_kernel) and the shared device headers."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1812_04070_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in [kernel.replace("_kernel", "") + ".cu", "acc_device.cuh", "simdx_internal.h"]:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -199,7 +204,7 @@ def ncu_traffic(kernel: str, workload: str):
         with open(path) as f:
             d = json.load(f)
         rec = d[f"{workload}:{kernel}"]
-        if rec.get("source_hash") != kernel_source_hash():
+        if rec.get("source_hash") != kernel_source_hash(kernel):
             return None
         return float(rec["bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -248,6 +253,23 @@ def run_simdx(args, rank, world, local):
     G = Graph(off, g.indices, weights=w)
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", local)
+    algs = wl["algs"]
+    graphs = {a: G for a in algs}
+    tuned, tuned_full, tune_s = {}, {}, 0.0
+    if args.autotune:
+        from paper_1812_04070_gb300 import simdx
+        code = {"bfs": simdx.ALGO_BFS, "sssp": simdx.ALGO_SSSP, "kcore": simdx.ALGO_KCORE,
+                "pagerank": simdx.ALGO_PAGERANK}
+        arg = {"bfs": 0, "sssp": 0, "kcore": 16, "pagerank": 0}
+        default = {k: getattr(G.config, k) for k, _ in G.config._fields_ if k != "reserved"}
+        t0 = time.time()
+        for i, a in enumerate(algs):
+            Ga = G if i == 0 else Graph(off, g.indices, weights=w)
+            best, _ = Ga.autotune(code[a], arg[a], reps=3)
+            graphs[a] = Ga
+            tuned_full[a] = best
+            tuned[a] = {k: v for k, v in best.items() if v != default[k]}
+        tune_s = time.time() - t0
     outs = {
         "bfs": torch.empty(g.n, dtype=torch.int32, device=dev),
         "sssp": torch.empty(g.n, dtype=torch.int32, device=dev),
@@ -257,16 +279,16 @@ def run_simdx(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def launch(alg, st=None):
+        Ga = graphs[alg]
         if alg == "bfs":
-            G.bfs(0, out=outs["bfs"], stats=st)
+            Ga.bfs(0, out=outs["bfs"], stats=st)
         elif alg == "sssp":
-            G.sssp(0, out=outs["sssp"], stats=st)
+            Ga.sssp(0, out=outs["sssp"], stats=st)
         elif alg == "kcore":
-            G.kcore(16, out=outs["kcore"][0], resid=outs["kcore"][1], stats=st)
+            Ga.kcore(16, out=outs["kcore"][0], resid=outs["kcore"][1], stats=st)
         else:
-            G.pagerank(0.85, 1e-6, 1000, out=outs["pagerank"], stats=st)
+            Ga.pagerank(0.85, 1e-6, 1000, out=outs["pagerank"], stats=st)
 
-    algs = wl["algs"]
     evs = {a: [] for a in algs}
     step_ev = []
 
@@ -349,13 +371,14 @@ def run_simdx(args, rank, world, local):
                       "grid_ctas": stats[a].grid_ctas}
                   for a in algs}
     # ---- e2e through the C ABI with host buffers (--e2e-steps 0 skips it, for profiling runs)
-    e2e = run_e2e(args, g, w, bits, algs, edges_step, world) if args.e2e_steps > 0 else None
+    e2e = run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full) if args.e2e_steps > 0 else None
     res = {
         "metric": "GTEPS", "value": round(value, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic (seeded R-MAT / grid)",
         "config": {"workload": args.workload, "description": wl["desc"], "n": g.n, "directed_edges": g.e,
-                   "l2": "flushed between steps (512 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "l2": "flushed between steps (512 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "knobs": ({"autotuned": tuned, "tune_s": round(tune_s, 2)} if args.autotune else "defaults")},
         "roofline": roofline, "kernels": per_kernel, "e2e": e2e, "gpu_launches": len(algs) * args.steps,
         "clocks": clocks, "wall_s_timed": round(wall, 3),
     }
@@ -365,7 +388,7 @@ def run_simdx(args, rank, world, local):
     return res
 
 
-def run_e2e(args, g, w, bits, algs, edges_step, world):
+def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
     import torch
     from paper_1812_04070_gb300 import Graph
 
@@ -386,6 +409,8 @@ def run_e2e(args, g, w, bits, algs, edges_step, world):
     def one():
         G = Graph(p_off.numpy(), p_idx.numpy(), weights=p_w.numpy().view(np.uint32) if "sssp" in algs else None)
         for a in algs:
+            if tuned_full:
+                G.set_config(**tuned_full[a])
             if a == "bfs":
                 host_out[a].copy_(G.bfs(0), non_blocking=True)
             elif a == "sssp":

@@ -289,6 +289,29 @@ SIMDX_API int simdx_server_info(simdx_server *s, int32_t *slots, uint64_t *launc
 /* Stop the dispatcher, finish launches in flight, free the server. */
 SIMDX_API int simdx_server_destroy(simdx_server *s);
 
+/* ------------------------------------------------------------ autotuner */
+/* Choose the knobs of simdx_config for one algorithm on one graph by
+ * measurement (growth direction (a): degree-class thresholds (Sec. 4
+ * "Classification"), overflow threshold (Sec. 4), push/pull switch ratios
+ * (Sec. 5), SSSP delta, CTAs per SM (Eq. 1)).  Coordinate descent from the
+ * graph's current knobs: two passes over the knobs that apply to `algo`; each
+ * candidate runs once untimed and then `reps` times timed with CUDA events on
+ * `stream` (median); a candidate replaces the current setting only when it is
+ * at least 2 % faster.  The winner is installed with simdx_graph_set_config
+ * and returned in *best (and its median time in *best_ms, may be NULL).
+ *   algo  SIMDX_ALGO_BFS / SSSP (arg = source vertex), SIMDX_ALGO_KCORE
+ *         (arg = k), SIMDX_ALGO_PAGERANK (arg ignored; damping 0.85, L1
+ *         tolerance 1e-6).
+ *   reps  timed runs per candidate, 1..64.
+ * Blocking; allocates one scratch output of 4 n bytes for its duration and
+ * reallocates the graph's workspace when a knob that sizes it changes.  Knobs
+ * change speed only: BFS, SSSP and k-core results are the same under every
+ * setting.  Errors: EINVAL (bad algo, arg or reps), EUNSUPPORTED (SSSP on a
+ * graph without weights), or the first error an algorithm call returns. */
+#define SIMDX_ALGO_PAGERANK 4
+SIMDX_API int simdx_autotune(simdx_graph *g, int32_t algo, int64_t arg, int32_t reps, simdx_config *best,
+                             float *best_ms, void *stream);
+
 /* ------------------------------------------------- no-allocation variant */
 /* BFS for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a deployment convenience).  Some callers cannot call

@@ -169,6 +169,13 @@ class Graph:
                           _stream_handle(stream))
         return out, resid
 
+    def autotune(self, algo: int, arg: int = 0, reps: int = 5, stream=None) -> tuple[dict, float]:
+        """Measure knob settings for `algo` (simdx.ALGO_*; arg = source or
+        k) on this graph, install the fastest and return it with its median
+        time in ms (simdx_autotune)."""
+        best, ms = simdx.simdx_autotune(self.handle, int(algo), int(arg), int(reps), _stream_handle(stream))
+        return {name: getattr(best, name) for name, _ in best._fields_ if name != "reserved"}, ms
+
     def pagerank(self, damping: float = 0.85, tol: float = 1e-6, max_iter: int = 1000, out=None,
                  stats: simdx_stats | None = None, stream=None):
         torch = _torch()

@@ -17,7 +17,7 @@ import os
 from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, EBARRIER_TIMEOUT, EUNSUPPORTED, EBUSY, ENOTREADY = range(8)
-ALGO_BFS, ALGO_SSSP, ALGO_KCORE = 1, 2, 3
+ALGO_BFS, ALGO_SSSP, ALGO_KCORE, ALGO_PAGERANK = 1, 2, 3, 4
 INPUT_HOST = 1
 BORROW = 2
 
@@ -92,6 +92,8 @@ SIGNATURES = {
     "simdx_server_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "simdx_server_destroy": (ctypes.c_int, [_vp]),
+    "simdx_autotune": (ctypes.c_int, [_vp, _i32, _i64, _i32, ctypes.POINTER(simdx_config),
+                                      ctypes.POINTER(ctypes.c_float), _vp]),
 }
 
 
@@ -269,3 +271,10 @@ def simdx_server_info(s: int) -> dict:
 
 def simdx_server_destroy(s: int) -> None:
     _check(_lib().simdx_server_destroy(s), "simdx_server_destroy")
+
+
+def simdx_autotune(g: int, algo: int, arg: int, reps: int, stream: int | None) -> tuple[simdx_config, float]:
+    best, ms = simdx_config(), ctypes.c_float()
+    _check(_lib().simdx_autotune(g, algo, arg, reps, ctypes.byref(best), ctypes.byref(ms), stream),
+           "simdx_autotune")
+    return best, ms.value
