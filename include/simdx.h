@@ -109,7 +109,9 @@ typedef struct {
     float alpha;             /* BFS push->pull when frontier edges > unexplored edges / alpha [14] */
     float beta;              /* BFS pull->push when frontier vertices < n / beta [24] */
     float kcore_alpha;       /* k-core pull when removed-vertex edges > alive edges / kcore_alpha [8] */
-    uint32_t delta;          /* SSSP delta-stepping bucket width, 0 = unbounded [32] */
+    uint32_t delta;          /* SSSP delta-stepping bucket width, 0 = unbounded [32 in
+                                simdx_config_default; a graph with weights starts at
+                                16 x its largest weight] */
     int32_t ctas_per_sm;     /* 0 = occupancy maximum (Eq. 1); else clamp [0] */
     int32_t barrier_timeout_ms; /* grid-barrier wait limit [2000] */
     int32_t debug_skip_cta;  /* test knob: this CTA skips barrier arrival number

@@ -39,7 +39,7 @@ std::vector<Knob> knobs_for(int algo) {
     k.push_back({"alpha", {4, 7, 14, 28, 56}, SIMDX_KNOB_I(alpha)});
     k.push_back({"beta", {6, 12, 24, 48, 96}, SIMDX_KNOB_I(beta)});
   } else if (algo == SIMDX_ALGO_SSSP) {
-    k.push_back({"delta", {8, 16, 32, 64, 128, 256, 1024, 0}, SIMDX_KNOB_I(delta)});
+    k.push_back({"delta", {16, 64, 256, 1024, 4096, 16384, 65536, 0}, SIMDX_KNOB_I(delta)});
   } else if (algo == SIMDX_ALGO_KCORE) {
     k.push_back({"kcore_alpha", {2, 4, 8, 16, 32}, SIMDX_KNOB_I(kcore_alpha)});
   }
@@ -92,7 +92,7 @@ extern "C" int simdx_autotune(simdx_graph* g, int32_t algo, int64_t arg, int32_t
       default: return simdx_pagerank(g, 0.85f, 1e-6f, 1000, (float*)out, nullptr, st);
     }
   };
-  // median time of `reps` runs after one untimed run; < 0 on error
+  // median time of `reps` runs after one untimed run; the first error otherwise
   auto measure = [&](float& ms) -> int {
     int r = run();
     if (r != SIMDX_OK) return r;

@@ -6,8 +6,12 @@
 //               out-neighbours; pull -- every unvisited vertex looks for one
 //               in-neighbour on the frontier and stops at the first hit
 //               (collaborative early termination, Sec. 3.3 "Comparison").
-// Combine     : vote.  All updates to a vertex carry the same value, so plain
-//               stores suffice (no atomics); the owner writes in pull.
+// Combine     : vote.  All updates to a vertex carry the same value; the owner
+//               writes in pull.  In push the first writer claims the vertex
+//               with one compare-and-swap (only writers that read it
+//               unvisited try), so the next frontier holds each vertex once
+//               and the vertex / edge counts that drive the direction switch
+//               are exact.
 // Direction   : push in the first and last levels, pull in between (Sec. 5).
 //               The switch uses frontier edge / vertex counts folded into the
 //               grid barrier: pull when frontier edges exceed unexplored
@@ -89,8 +93,7 @@ struct BfsPush {
     for (int q = 0; q < kPushBatch; ++q) lv[q] = ((ok >> q) & 1u) ? level[u[q]] : 0;
 #pragma unroll
     for (int q = 0; q < kPushBatch; ++q) {
-      if (((ok >> q) & 1u) && lv[q] == -1) {
-        level[u[q]] = next;  // vote: every writer stores the same value
+      if (((ok >> q) & 1u) && lv[q] == -1 && atomicCAS(&level[u[q]], -1, next) == -1) {
         long long d = (long long)gload(off + u[q] + 1) - (long long)gload(off + u[q]);
         ++nrec;
         mrec += (unsigned long long)d;

@@ -161,6 +161,16 @@ __global__ void validate_kernel(long long n, long long e, const OffT* off, const
   }
 }
 
+// Largest edge weight (for the default SSSP bucket width).
+__global__ void weight_max_kernel(long long e, const uint32_t* w, unsigned* out) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned m = 0;
+  for (long long p = tid; p < e; p += stride) m = max(m, w[p]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 template <class OffT>
 __global__ void nonzero_bitmap_kernel(long long n, const OffT* off, uint32_t* bm) {
   long long words = (n + 31) / 32;
@@ -327,9 +337,9 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
       return fail(rc);
   }
   // validate on the device (also catches bad host input after the copy)
-  int* d_bad = nullptr;
-  if ((e = cudaMalloc(&d_bad, sizeof(int))) != cudaSuccess) return fail(cuda_status(e, "cudaMalloc"));
-  cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  int* d_bad = nullptr;  // [0] validation flags, [1] largest weight
+  if ((e = cudaMalloc(&d_bad, 2 * sizeof(int))) != cudaSuccess) return fail(cuda_status(e, "cudaMalloc"));
+  cudaMemsetAsync(d_bad, 0, 2 * sizeof(int), st);
   int vblocks = std::max(1, std::min(4 * g->num_sms, (int)((g->e + g->n) / 256 + 1)));
   const simdx_csr* parts[2] = {csr, csc};
   for (int pi = 0; pi < 2; ++pi) {
@@ -341,12 +351,18 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
     else
       validate_kernel<long long><<<vblocks, 256, 0, st>>>(g->n, g->e, (const long long*)o, ix, d_bad);
   }
-  int h_bad = 0;
-  e = cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (g->w && g->e > 0)
+    weight_max_kernel<<<vblocks, 256, 0, st>>>(g->e, g->w, reinterpret_cast<unsigned*>(d_bad + 1));
+  int h_bad[2] = {0, 0};
+  e = cudaMemcpyAsync(h_bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(d_bad);
   if (e != cudaSuccess) return fail(cuda_status(e, "graph validation"));
-  if (h_bad) return fail(SIMDX_EINVAL);
+  if (h_bad[0]) return fail(SIMDX_EINVAL);
+  // default bucket width: 16 x the largest weight (a few buckets cover the
+  // distances of a low-diameter graph; a long path gets wide buckets)
+  const unsigned wmax = static_cast<unsigned>(h_bad[1]);
+  if (wmax) g->cfg.delta = wmax >= (1u << 26) ? (1u << 30) : 16u * wmax;
   // workspace
   long long words = (g->n + 31) / 32 + 1;
   if ((e = cudaMalloc(&g->bitmaps, sizeof(uint32_t) * 4 * (size_t)words)) != cudaSuccess)
