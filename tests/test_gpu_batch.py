@@ -69,3 +69,49 @@ def test_bfs_multigraph_pack(mode):
     lev1 = G.bfs_multi([int(roots[0]), int(roots[0])]).cpu().numpy()
     assert np.array_equal(lev1, G.bfs(int(roots[0])).cpu().numpy())
     G.close()
+
+
+@pytest.mark.parametrize("k", [1, 33, 64, 70])
+def test_sssp_batch_sizes(k):
+    """k <= 32 uses 32 state slots per vertex, 33..64 use 64 (two instances per
+    lane), more than 64 runs one launch per 64 sources."""
+    g = gg.rmat(11)
+    w = gg.weights(g, 99, 1, 64)
+    srcs = np.resize(gg.pick_sources(g, 50, seed=k), k)
+    G = make(g, w, bits=32)
+    out = G.sssp_batch([int(s) for s in srcs]).cpu().numpy().view(np.uint32)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(out[i], oracle.sssp(g.offsets, g.indices, w, int(s))), (k, i)
+    G.close()
+
+
+def test_sssp_batch_directed():
+    """Batched SSSP relaxes out-edges, so a directed graph (CSR + CSC) works."""
+    import torch
+    from paper_1812_04070_gb300 import Graph
+    n = 400
+    rng = np.random.default_rng(4)
+    src = rng.integers(0, n, 3000)
+    dst = rng.integers(0, n, 3000)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    pair = np.unique(np.stack([src, dst], 1), axis=0)
+    src, dst = pair[:, 0], pair[:, 1]
+    off = np.zeros(n + 1, np.int64)
+    np.add.at(off, src + 1, 1)
+    off = np.cumsum(off)
+    idx = dst.astype(np.int32)
+    wt = (rng.integers(1, 50, len(idx))).astype(np.uint32)
+    co = np.lexsort((src, dst))
+    ioff = np.zeros(n + 1, np.int64)
+    np.add.at(ioff, dst + 1, 1)
+    ioff = np.cumsum(ioff)
+    G = Graph(off, idx, weights=wt, csc=(ioff, src[co].astype(np.int32)))
+    srcs = [0, 5, 77]
+    out = G.sssp_batch(srcs).cpu().numpy().view(np.uint32)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(out[i], oracle.sssp(off, idx, wt, s)), i
+        assert torch.equal(torch.from_numpy(out[i].view(np.int32)), G.sssp(s).cpu())
+    G.close()
