@@ -73,12 +73,12 @@ extern "C" int simdx_autotune(simdx_graph* g, int32_t algo, int64_t arg, int32_t
   const size_t n = (size_t)std::max<int64_t>(g->n, 1);
   void* out = nullptr;
   void* resid = nullptr;
-  SIMDX_CUDA(cudaMalloc(&out, 4 * n));
+  SIMDX_CUDA(simdx::dev_alloc(&out, 4 * n, st));
   if (algo == SIMDX_ALGO_KCORE) {
-    cudaError_t e = cudaMalloc(&resid, 4 * n);
+    cudaError_t e = simdx::dev_alloc(&resid, 4 * n, st);
     if (e != cudaSuccess) {
-      cudaFree(out);
-      return cuda_status(e, "cudaMalloc(autotune resid)");
+      simdx::dev_free(out, st);
+      return cuda_status(e, "dev_alloc(autotune resid)");
     }
   }
   Timer tm;
@@ -150,9 +150,9 @@ extern "C" int simdx_autotune(simdx_graph* g, int32_t algo, int64_t arg, int32_t
     }
   } while (false);
   if (rc == SIMDX_OK) rc = simdx_graph_set_config(g, &cur);
+  simdx::dev_free(out, st);
+  simdx::dev_free(resid, st);
   cudaStreamSynchronize(st);
-  cudaFree(out);
-  cudaFree(resid);
   if (rc != SIMDX_OK) return rc;
   *best = cur;
   if (best_ms) *best_ms = cur_ms;

@@ -563,10 +563,10 @@ extern "C" int simdx_bfs_multi(simdx_graph* g, const int32_t* roots, int32_t k, 
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((size_t)k > g->roots_cap) {
-    cudaFree(g->d_roots);
+    dev_free(g->d_roots, st);
     g->d_roots = nullptr;
     g->roots_cap = 0;
-    SIMDX_CUDA(cudaMalloc(&g->d_roots, sizeof(int32_t) * (size_t)k));
+    SIMDX_CUDA(dev_alloc((void**)&g->d_roots, sizeof(int32_t) * (size_t)k, st));
     g->roots_cap = (size_t)k;
   }
   SIMDX_CUDA(cudaMemcpyAsync(g->d_roots, roots, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));

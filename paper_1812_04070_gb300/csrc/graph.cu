@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <vector>
 
 #include "simdx_internal.h"
 
@@ -20,6 +21,64 @@ const void* kcore_kernel_ptr(int off_bits);
 const void* pagerank_kernel_ptr(int off_bits);
 
 static thread_local char g_last_cuda[256] = "";
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaMemPool_t pool_of(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pl = nullptr;
+    if (cudaMemPoolCreate(&pl, &props) != cudaSuccess) return nullptr;
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pl;
+  }
+  return g_pool[dev];
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pl = pool_of(dev);
+  if (!pl) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 1), pl, st);
+}
+
+void dev_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+static std::mutex g_stage_mu;
+static std::vector<HostStage*> g_stage_free;
+
+HostStage* host_stage_get() {
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  if (g_stage_free.empty()) {
+    constexpr int kChunk = 64;
+    void* blk = nullptr;
+    if (cudaHostAlloc(&blk, sizeof(HostStage) * kChunk, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    for (int i = 0; i < kChunk; ++i) g_stage_free.push_back(static_cast<HostStage*>(blk) + i);
+  }
+  HostStage* h = g_stage_free.back();
+  g_stage_free.pop_back();
+  std::memset(h, 0, sizeof(HostStage));
+  return h;
+}
+
+void host_stage_put(HostStage* h) {
+  if (!h) return;
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  g_stage_free.push_back(h);
+}
 
 int cuda_status(cudaError_t e, const char* what) {
   snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", what, cudaGetErrorString(e));
@@ -233,13 +292,13 @@ int64_t simdx_eq1_ctas(int64_t regs_per_sm, int64_t regs_per_thread, int64_t thr
   return (regs_per_sm / (regs_per_thread * threads_per_cta)) * n_sm;
 }
 
-static void free_workspace(simdx_graph* g) {
-  cudaFree(g->bins);
-  cudaFree(g->lists);
-  cudaFree(g->aux3);
-  cudaFree(g->chunk_part);
-  cudaFree(g->chunk_done);
-  cudaFree(g->warp_start);
+static void free_workspace(simdx_graph* g, cudaStream_t st) {
+  dev_free(g->bins, st);
+  dev_free(g->lists, st);
+  dev_free(g->aux3, st);
+  dev_free(g->chunk_part, st);
+  dev_free(g->chunk_done, st);
+  dev_free(g->warp_start, st);
   g->warp_start = nullptr;
   g->bins = nullptr;
   g->lists = nullptr;
@@ -248,8 +307,8 @@ static void free_workspace(simdx_graph* g) {
   g->chunk_done = nullptr;
 }
 
-static int alloc_workspace(simdx_graph* g) {
-  free_workspace(g);
+static int alloc_workspace(simdx_graph* g, cudaStream_t st) {
+  free_workspace(g, st);
   int per_sm = 0;
   const void* ks[4] = {bfs_kernel_ptr(g->off_bits), sssp_kernel_ptr(g->off_bits),
                        kcore_kernel_ptr(g->off_bits), pagerank_kernel_ptr(g->off_bits)};
@@ -263,16 +322,16 @@ static int alloc_workspace(simdx_graph* g) {
   g->list_cap = std::max<long long>(g->n, online_total) + 64;
   size_t bins_bytes = sizeof(int32_t) * (size_t)kClasses * g->grid_max * std::max(1, g->bin_cap);
   size_t list_bytes = sizeof(int32_t) * (size_t)2 * kClasses * g->list_cap;
-  SIMDX_CUDA(cudaMalloc(&g->bins, bins_bytes));
-  SIMDX_CUDA(cudaMalloc(&g->lists, list_bytes));
-  SIMDX_CUDA(cudaMalloc(&g->aux3, sizeof(uint32_t) * 2 * (size_t)g->list_cap));
+  SIMDX_CUDA(dev_alloc((void**)&g->bins, bins_bytes, st));
+  SIMDX_CUDA(dev_alloc((void**)&g->lists, list_bytes, st));
+  SIMDX_CUDA(dev_alloc((void**)&g->aux3, sizeof(uint32_t) * 2 * (size_t)g->list_cap, st));
   // chunked class-3 tasks: at most e / huge_min + (tasks) chunks per phase
   const long long hm = std::max(1, g->cfg.huge_min);
   const size_t parts = (size_t)(g->e / hm + g->n + 16);
-  SIMDX_CUDA(cudaMalloc(&g->chunk_part, sizeof(unsigned long long) * parts));
-  SIMDX_CUDA(cudaMalloc(&g->chunk_done, sizeof(int) * (size_t)(g->n + 16)));
-  SIMDX_CUDA(cudaMemset(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16)));
-  SIMDX_CUDA(cudaMalloc(&g->warp_start, sizeof(int) * ((size_t)g->grid_max * kWarps + 1)));
+  SIMDX_CUDA(dev_alloc((void**)&g->chunk_part, sizeof(unsigned long long) * parts, st));
+  SIMDX_CUDA(dev_alloc((void**)&g->chunk_done, sizeof(int) * (size_t)(g->n + 16), st));
+  SIMDX_CUDA(cudaMemsetAsync(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16), st));
+  SIMDX_CUDA(dev_alloc((void**)&g->warp_start, sizeof(int) * ((size_t)g->grid_max * kWarps + 1), st));
   return SIMDX_OK;
 }
 
@@ -315,8 +374,8 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
       *dst = const_cast<void*>(src);
       return SIMDX_OK;
     }
-    cudaError_t ee = cudaMalloc(dst, bytes);
-    if (ee != cudaSuccess) return cuda_status(ee, "cudaMalloc(graph)");
+    cudaError_t ee = dev_alloc(dst, bytes, st);
+    if (ee != cudaSuccess) return cuda_status(ee, "dev_alloc(graph)");
     if (src && bytes) {
       ee = cudaMemcpyAsync(*dst, src, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
       if (ee != cudaSuccess) return cuda_status(ee, "cudaMemcpyAsync(graph)");
@@ -338,7 +397,7 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
   }
   // validate on the device (also catches bad host input after the copy)
   int* d_bad = nullptr;  // [0] validation flags, [1] largest weight
-  if ((e = cudaMalloc(&d_bad, 2 * sizeof(int))) != cudaSuccess) return fail(cuda_status(e, "cudaMalloc"));
+  if ((e = dev_alloc((void**)&d_bad, 2 * sizeof(int), st)) != cudaSuccess) return fail(cuda_status(e, "dev_alloc"));
   cudaMemsetAsync(d_bad, 0, 2 * sizeof(int), st);
   int vblocks = std::max(1, std::min(4 * g->num_sms, (int)((g->e + g->n) / 256 + 1)));
   const simdx_csr* parts[2] = {csr, csc};
@@ -355,8 +414,8 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
     weight_max_kernel<<<vblocks, 256, 0, st>>>(g->e, g->w, reinterpret_cast<unsigned*>(d_bad + 1));
   int h_bad[2] = {0, 0};
   e = cudaMemcpyAsync(h_bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  dev_free(d_bad, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(d_bad);
   if (e != cudaSuccess) return fail(cuda_status(e, "graph validation"));
   if (h_bad[0]) return fail(SIMDX_EINVAL);
   // default bucket width: 16 x the largest weight (a few buckets cover the
@@ -365,28 +424,26 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
   if (wmax) g->cfg.delta = wmax >= (1u << 26) ? (1u << 30) : 16u * wmax;
   // workspace
   long long words = (g->n + 31) / 32 + 1;
-  if ((e = cudaMalloc(&g->bitmaps, sizeof(uint32_t) * 4 * (size_t)words)) != cudaSuccess)
-    return fail(cuda_status(e, "cudaMalloc(bitmaps)"));
+  if ((e = dev_alloc((void**)&g->bitmaps, sizeof(uint32_t) * 4 * (size_t)words, st)) != cudaSuccess)
+    return fail(cuda_status(e, "dev_alloc(bitmaps)"));
   cudaMemsetAsync(g->bitmaps, 0, sizeof(uint32_t) * 4 * (size_t)words, st);
-  if ((e = cudaMalloc(&g->state, 20 * (size_t)std::max<int64_t>(g->n, 1) + 64)) != cudaSuccess)
-    return fail(cuda_status(e, "cudaMalloc(state)"));
-  if ((e = cudaMalloc(&g->sync, sizeof(Sync))) != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(sync)"));
+  if ((e = dev_alloc(&g->state, 20 * (size_t)std::max<int64_t>(g->n, 1) + 64, st)) != cudaSuccess)
+    return fail(cuda_status(e, "dev_alloc(state)"));
+  if ((e = dev_alloc((void**)&g->sync, sizeof(Sync), st)) != cudaSuccess) return fail(cuda_status(e, "dev_alloc(sync)"));
   {
     long long chunks = (g->n + kBallotChunk - 1) / kBallotChunk + 1;
-    if ((e = cudaMalloc(&g->chunk_cnt, sizeof(int32_t) * kClasses * (size_t)chunks)) != cudaSuccess)
-      return fail(cuda_status(e, "cudaMalloc(chunk_cnt)"));
+    if ((e = dev_alloc((void**)&g->chunk_cnt, sizeof(int32_t) * kClasses * (size_t)chunks, st)) != cudaSuccess)
+      return fail(cuda_status(e, "dev_alloc(chunk_cnt)"));
   }
-  if ((e = cudaMalloc(&g->dstats, sizeof(DevStats))) != cudaSuccess)
-    return fail(cuda_status(e, "cudaMalloc(stats)"));
+  if ((e = dev_alloc((void**)&g->dstats, sizeof(DevStats), st)) != cudaSuccess)
+    return fail(cuda_status(e, "dev_alloc(stats)"));
   cudaMemsetAsync(g->dstats, 0, sizeof(DevStats), st);
   g->trace_cap = 1 << 16;
-  if ((e = cudaMalloc(&g->trace, sizeof(long long) * kTraceWords * (size_t)g->trace_cap)) != cudaSuccess)
-    return fail(cuda_status(e, "cudaMalloc(trace)"));
-  if ((e = cudaHostAlloc(&g->h_stats, sizeof(HostStage), cudaHostAllocDefault)) != cudaSuccess)
-    return fail(cuda_status(e, "cudaHostAlloc"));
-  std::memset(g->h_stats, 0, sizeof(HostStage));
+  if ((e = dev_alloc((void**)&g->trace, sizeof(long long) * kTraceWords * (size_t)g->trace_cap, st)) != cudaSuccess)
+    return fail(cuda_status(e, "dev_alloc(trace)"));
+  if (!(g->h_stats = host_stage_get())) return fail(SIMDX_ENOMEM);
   cudaMemsetAsync(g->sync, 0, sizeof(Sync), st);
-  if ((rc = alloc_workspace(g)) != SIMDX_OK) return fail(rc);
+  if ((rc = alloc_workspace(g, st)) != SIMDX_OK) return fail(rc);
   int nb = std::max(1, std::min(4 * g->num_sms, (int)(words / 256 + 1)));
   if (g->off_bits == 32)
     nonzero_bitmap_kernel<int32_t><<<nb, 256, 0, st>>>(g->n, (const int32_t*)g->in_off, g->bitmaps);
@@ -399,28 +456,29 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
 
 int simdx_graph_destroy(simdx_graph* g) {
   if (!g) return SIMDX_EINVAL;
-  cudaDeviceSynchronize();
+  cudaDeviceSynchronize();  // no call on this graph is in flight past here
+  cudaStream_t st = 0;
   if (!g->borrowed) {
-    cudaFree(g->off);
-    cudaFree(g->idx);
+    dev_free(g->off, st);
+    dev_free(g->idx, st);
     if (!g->symmetric) {
-      cudaFree(g->in_off);
-      cudaFree(g->in_idx);
+      dev_free(g->in_off, st);
+      dev_free(g->in_idx, st);
     }
-    cudaFree(g->w);
+    dev_free(g->w, st);
   }
-  free_workspace(g);
-  cudaFree(g->bitmaps);
-  cudaFree(g->state);
-  cudaFree(g->sync);
-  cudaFree(g->ms_state);
-  cudaFree(g->d_roots);
-  cudaFree(g->sb_state);
-  cudaFree(g->pr_ws);
-  cudaFree(g->chunk_cnt);
-  cudaFree(g->dstats);
-  cudaFree(g->trace);
-  if (g->h_stats) cudaFreeHost(g->h_stats);
+  free_workspace(g, st);
+  dev_free(g->bitmaps, st);
+  dev_free(g->state, st);
+  dev_free(g->sync, st);
+  dev_free(g->ms_state, st);
+  dev_free(g->d_roots, st);
+  dev_free(g->sb_state, st);
+  dev_free(g->pr_ws, st);
+  dev_free(g->chunk_cnt, st);
+  dev_free(g->dstats, st);
+  dev_free(g->trace, st);
+  host_stage_put(g->h_stats);
   delete g;
   return SIMDX_OK;
 }
@@ -452,7 +510,12 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
                     cfg->huge_min != g->cfg.huge_min;
   cudaDeviceSynchronize();
   g->cfg = *cfg;
-  if (realloc_ws) return alloc_workspace(g);
+  if (realloc_ws) {
+    int rc = alloc_workspace(g, 0);
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (rc == SIMDX_OK && e != cudaSuccess) rc = cuda_status(e, "set_config");
+    return rc;
+  }
   return SIMDX_OK;
 }
 

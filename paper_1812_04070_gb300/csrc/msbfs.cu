@@ -288,9 +288,10 @@ const void* msbfs_kernel_ptr(int off_bits) {
 
 // Batch state: visit + two frontier masks per vertex, and the device copy of
 // the sources.  Allocated on the first batched call, kept with the graph.
-int ensure_msbfs_state(simdx_graph* g) {
+int ensure_msbfs_state(simdx_graph* g, cudaStream_t st) {
   if (g->ms_state) return SIMDX_OK;
-  SIMDX_CUDA(cudaMalloc(&g->ms_state, sizeof(unsigned long long) * 3 * (size_t)(g->n + 1) + 64 * sizeof(int32_t)));
+  SIMDX_CUDA(dev_alloc((void**)&g->ms_state, sizeof(unsigned long long) * 3 * (size_t)(g->n + 1) + 64 * sizeof(int32_t),
+                       st));
   return SIMDX_OK;
 }
 
@@ -332,7 +333,7 @@ extern "C" int simdx_bfs_batch(simdx_graph* g, const int32_t* srcs, int32_t k, i
     if (srcs[i] < 0 || srcs[i] >= g->n) return SIMDX_EINVAL;
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = ensure_msbfs_state(g);
+  int rc = ensure_msbfs_state(g, st);
   if (rc) return rc;
   int32_t* d_src = reinterpret_cast<int32_t*>(g->ms_state + 3 * (size_t)(g->n + 1));
   for (int b = 0; b < k; b += 64) {

@@ -609,10 +609,10 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   const size_t part_b = up(sizeof(double) * (size_t)nw);
   const size_t bytes = head_b + pre_b + csum_b + ts_b + 2 * part_b + up(sizeof(int) * (size_t)nw);
   if (!g->pr_ws || g->pr_bytes < bytes) {
-    cudaFree(g->pr_ws);
+    dev_free(g->pr_ws, st);
     g->pr_ws = nullptr;
     g->pr_bytes = 0;
-    SIMDX_CUDA(cudaMalloc(&g->pr_ws, bytes));
+    SIMDX_CUDA(dev_alloc(&g->pr_ws, bytes, st));
     g->pr_bytes = bytes;
   }
   char* base = static_cast<char*>(g->pr_ws);

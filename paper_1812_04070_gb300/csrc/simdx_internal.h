@@ -95,6 +95,17 @@ int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st);
 
 int cuda_status(cudaError_t e, const char* what);
 
+// Device memory of the library comes from one stream-ordered pool per device
+// that keeps the blocks it is given back (no release threshold), so graph
+// creation, destruction and batch-state growth reuse memory instead of going
+// to the driver each time.  dev_alloc / dev_free are ordered on `st`.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+
+// Pinned host staging of run statistics, recycled across graphs.
+HostStage* host_stage_get();
+void host_stage_put(HostStage* h);
+
 }  // namespace simdx
 
 #define SIMDX_CUDA(call)                                             \

@@ -382,17 +382,17 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
 
 // Batch state: task lists sized for k * n state ids, the class-3 words, the
 // processed distances and pending flags of every copy, and the sources.
-static int ensure_sssp_batch_state(simdx_graph* g, int k) {
+static int ensure_sssp_batch_state(simdx_graph* g, int k, cudaStream_t st) {
   const size_t ids = (size_t)k * (size_t)g->n;
   const size_t cap = std::max<size_t>(ids, (size_t)g->grid_max * (size_t)g->bin_cap) + 64;
   const size_t bytes = sizeof(int32_t) * 2 * kClasses * cap + sizeof(uint32_t) * 2 * cap +
                        sizeof(uint32_t) * ids + ids + sizeof(int32_t) * (size_t)k + 256;
   g->sb_cap = cap;  // the layout follows the current k; any large enough buffer is reused
   if (g->sb_state && g->sb_bytes >= bytes) return SIMDX_OK;
-  cudaFree(g->sb_state);
+  dev_free(g->sb_state, st);
   g->sb_state = nullptr;
   g->sb_bytes = 0;
-  SIMDX_CUDA(cudaMalloc(&g->sb_state, bytes));
+  SIMDX_CUDA(dev_alloc(&g->sb_state, bytes, st));
   g->sb_bytes = bytes;
   g->sb_k = k;
   g->sb_cap = cap;
@@ -458,7 +458,7 @@ extern "C" int simdx_sssp_batch(simdx_graph* g, const int32_t* srcs, int32_t k, 
     if (srcs[i] < 0 || srcs[i] >= g->n) return SIMDX_EINVAL;
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = ensure_sssp_batch_state(g, k);
+  int rc = ensure_sssp_batch_state(g, k, st);
   if (rc) return rc;
   return g->off_bits == 32 ? run_sssp_batch<int32_t>(g, srcs, k, dist, stats, st)
                            : run_sssp_batch<long long>(g, srcs, k, dist, stats, st);
