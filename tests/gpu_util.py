@@ -68,3 +68,30 @@ def check_pagerank(G, g, d=0.85, tol=1e-6, max_iter=1000):
     rel = np.abs(x - ex).sum() / denom if denom > 0 else 0.0
     _, t_stop, _ = oracle.pagerank(g.offsets, g.indices, d=d, tol=tol, max_iter=max_iter)
     return rel, t, t_stop, st
+
+
+def directed_graph(n, m, seed, wmax=64):
+    """A seeded random directed graph: CSR (out-edges), CSC (in-edges) and
+    weights in CSR order.  Some vertices have only out-edges, some only
+    in-edges, some none."""
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, n, m)
+    dst = rng.integers(0, n, m)
+    # a band of sources-only and sinks-only vertices
+    k = max(1, n // 10)
+    dst = np.where(dst < k, dst + k, dst)          # vertices [0, k) get no in-edges
+    src = np.where((src >= n - k) & (n > 2 * k), src - k, src)  # vertices [n-k, n) get no out-edges
+    keep = src != dst
+    pairs = np.unique(np.stack([src[keep], dst[keep]], 1), axis=0)
+    s, d = pairs[:, 0].astype(np.int64), pairs[:, 1].astype(np.int64)
+    off = np.zeros(n + 1, np.int64)
+    np.add.at(off, s + 1, 1)
+    off = np.cumsum(off)
+    idx = d.astype(np.int32)
+    order = np.lexsort((s, d))
+    ioff = np.zeros(n + 1, np.int64)
+    np.add.at(ioff, d + 1, 1)
+    ioff = np.cumsum(ioff)
+    iidx = s[order].astype(np.int32)
+    w = rng.integers(1, wmax + 1, idx.size).astype(np.uint32)
+    return off, idx, ioff, iidx, w
