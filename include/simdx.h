@@ -104,7 +104,8 @@ typedef struct {
                                 round-robin over all CTAs; CTA list below [4096] */
     int32_t bin_per_thread;  /* online-filter overflow threshold per thread [64] (Sec. 4
                                 "Overflow thresholds"); 0 forces the ballot filter */
-    int32_t direction;       /* 0 auto, 1 push only, 2 pull only [0] (Sec. 5) */
+    int32_t direction;       /* 0 auto, 1 push only, 2 pull only [0] (Sec. 5); SSSP's
+                                automatic choice is push (pull is forced by 2) */
     int32_t filter;          /* 0 JIT (online, ballot on overflow), 2 ballot only [0] (Sec. 4) */
     float alpha;             /* BFS push->pull when frontier edges > unexplored edges / alpha [14] */
     float beta;              /* BFS pull->push when frontier vertices < n / beta [24] */

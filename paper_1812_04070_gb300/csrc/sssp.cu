@@ -30,6 +30,7 @@ template <class OffT>
 struct SsspArgs {
   int n, src;           // n: state ids (nreal, or k * nreal for a batch)
   int nreal, ninst;
+  int pull_ok;          // symmetric graph: in-edge weights are the CSR weights, pull allowed
   const int32_t* srcs;  // device [ninst] (batch only)
   const OffT* off;
   const int32_t* idx;
@@ -153,9 +154,55 @@ struct SsspPush {
   }
 };
 
+// Pull (Sec. 5: SSSP pushes in the first and last iterations and pulls in
+// between): every vertex with an in-edge takes the min of pdist[v] + w over
+// its in-neighbours v on the frontier (bitmap `fbm`, pdist = the distance v
+// was claimed with) and, the owner, lowers its own distance -- min combine,
+// no atomics.  Symmetric graphs only (the in-edge weight is the CSR weight).
+template <class OffT>
+struct SsspPull {
+  using Acc = unsigned;
+  const uint32_t* fbm;
+  const uint32_t* pdist;
+  const uint32_t* wt;
+  uint32_t* dist;
+  uint8_t* pend;
+  const OffT* off;
+  unsigned long long T;
+  CtaShared& sh;
+  const Work& w;
+  const Knobs& k;
+  unsigned grid;
+  unsigned long long nrec = 0, mrec = 0;
+  __device__ SsspPull(const uint32_t* fb, const uint32_t* pd, const uint32_t* wts, uint32_t* d, uint8_t* pe,
+                      const OffT* o, unsigned long long t, CtaShared& s, const Work& ww, const Knobs& kk, unsigned g)
+      : fbm(fb), pdist(pd), wt(wts), dist(d), pend(pe), off(o), T(t), sh(s), w(ww), k(kk), grid(g) {}
+  __device__ __forceinline__ Acc zero() const { return 0xffffffffu; }
+  __device__ __forceinline__ void combine(Acc& a, Acc b) const { a = b < a ? b : a; }
+  __device__ __forceinline__ void edge(Acc& a, int, int v, long long p) {
+    if ((fbm[v >> 5] >> (v & 31)) & 1u) {
+      const unsigned long long c = (unsigned long long)pdist[v] + gload(wt + p);
+      if (c < a) a = (unsigned)c;
+    }
+  }
+  __device__ __forceinline__ void finish(int u, Acc best) {
+    if (best < dist[u]) {
+      dist[u] = best;
+      pend[u] = 1;
+      if ((unsigned long long)best < T) {
+        const long long d = (long long)gload(off + u + 1) - (long long)gload(off + u);
+        ++nrec;
+        mrec += (unsigned long long)d;
+        online_record(u, degree_class(d, k), sh, w, k, grid);
+      }
+    }
+  }
+};
+
 template <class OffT, bool V>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
+  __shared__ unsigned red_u[kWarps];
   const unsigned grid = gridDim.x;
   Sync* s = a.w.sync;
   const Knobs& k = a.k;
@@ -185,6 +232,11 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     pdist[x] = 0xffffffffu;
     pend[x] = is_src ? 1 : 0;  // the source is the first pending vertex
   }
+  if (!V && a.pull_ok)  // pull frontiers (BFS leaves these bitmaps as it likes)
+    for (long long q = gtid; q < (((long long)n + 31) >> 5); q += gthreads) {
+      a.w.bm_f[0][q] = 0u;
+      a.w.bm_f[1][q] = 0u;
+    }
   if (blockIdx.x == 0) {
     const int nsrc = V ? a.ninst : 1;
     for (int i = threadIdx.x; i < nsrc; i += kThreads) {
@@ -207,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     const PhaseSlot& p = s->slot[0];
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
   }
-  int it = 0, ballot_it = 0, online_it = 0;
+  int it = 0, ballot_it = 0, online_it = 0, pull_it = 0;
   long long evisit = 0, fsum = 0;
   int filt = 1;
 
@@ -307,26 +359,87 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
       if (total == 0) continue;  // (cannot happen: the jump bucket holds the min)
     }
 
-    // -------- compute: push relaxations from the current task lists
-    clear_next_slot(s, sh);
-    online_reset(sh);
-    __syncthreads();
-    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-    SsspPush<OffT, V> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
-    const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
-                                      a.w.list[lbuf][3]};
-    push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
-    online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
-    unsigned long long tn = cta_sum_u64(f.nrec, sh);
-    unsigned long long tm = cta_sum_u64(f.mrec, sh);
-    if (threadIdx.x == 0 && tn) {
-      atomicAdd(&slot.nact, tn);
-      atomicAdd(&slot.mact, tm);
+    // -------- direction: push unless the direction knob forces pull.  A pull
+    // iteration sweeps every in-edge (plus two phases to claim the frontier
+    // and list the pull tasks); on GB300 that costs more than pushing even
+    // the densest frontier of these graphs (R-MAT 20 / 22 / 24, pull in every
+    // iteration with more than n / beta frontier vertices for beta 8..64:
+    // 1.5-1.8x slower), so the automatic choice is push.
+    const bool pull = !V && a.pull_ok && k.direction == 2;
+    unsigned long long tn = 0, tm = 0;
+    if (pull) {
+      uint32_t* fbm = a.w.bm_f[pull_it & 1];
+      uint32_t* other = a.w.bm_f[(pull_it & 1) ^ 1];
+      // claim the frontier into the bitmap (pdist = the distance relaxed
+      // with); clear the other bitmap for the next pull iteration
+      clear_next_slot(s, sh);
+      for (int c = 0; c < kClasses; ++c) {
+        const int32_t* list = a.w.list[lbuf][c];
+        for (long long i = gtid; i < cnt[c]; i += gthreads) {
+          const int v = list[i];
+          const uint32_t d = a.dist[v];
+          if (d < pdist[v] && (unsigned long long)d < T) {
+            pdist[v] = d;
+            atomicOr(&fbm[v >> 5], 1u << (v & 31));
+          }
+        }
+      }
+      for (long long q = gtid; q < (((long long)n + 31) >> 5); q += gthreads) other[q] = 0u;
+      if (!grid_sync(s, grid, sh, k)) return;
+      // the pull tasks: every vertex with an in-edge
+      clear_next_slot(s, sh);
+      {
+        PhaseSlot& slot_c = s->slot[slot_of(sh.phase)];
+        auto deg = [off = a.off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+        auto none = [](int) {};
+        bitmap_filter(n, a.w.bm_nz, deg, none, sh, a.w, k, grid, lbuf, slot_c);
+      }
+      if (!grid_sync(s, grid, sh, k)) return;
+      unsigned cc[kClasses];
+      {
+        const PhaseSlot& pc = s->slot[slot_of(sh.phase - 1)];
+        for (int c = 0; c < kClasses; ++c) cc[c] = pc.list_cnt[c];
+      }
+      clear_next_slot(s, sh);
+      online_reset(sh);
+      __syncthreads();
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      SsspPull<OffT> f(fbm, pdist, a.wt, a.dist, pend, a.off, T, sh, a.w, k, grid);
+      const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                        a.w.list[lbuf][3]};
+      pull_classes<OffT>(f, a.off, a.idx, lists, cc, grid, red_u, k.huge_min, sh, a.w, evisit, &slot);
+      online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
+      tn = cta_sum_u64(f.nrec, sh);
+      tm = cta_sum_u64(f.mrec, sh);
+      if (threadIdx.x == 0 && tn) {
+        atomicAdd(&slot.nact, tn);
+        atomicAdd(&slot.mact, tm);
+      }
+      ++pull_it;
+      ++ballot_it;
+    } else {
+      // -------- compute: push relaxations from the current task lists
+      clear_next_slot(s, sh);
+      online_reset(sh);
+      __syncthreads();
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      SsspPush<OffT, V> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
+      const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                        a.w.list[lbuf][3]};
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
+      online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
+      tn = cta_sum_u64(f.nrec, sh);
+      tm = cta_sum_u64(f.mrec, sh);
+      if (threadIdx.x == 0 && tn) {
+        atomicAdd(&slot.nact, tn);
+        atomicAdd(&slot.mact, tm);
+      }
+      if (filt == 2) ++ballot_it; else ++online_it;
     }
-    if (filt == 2) ++ballot_it; else ++online_it;
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
-    trace_put(a.w, it, 1 | (filt << 8), (long long)total, 0, (long long)(T == kInfT ? -1 : (long long)T), t_it);
+    trace_put(a.w, it, (pull ? 2 : 1) | (filt << 8), (long long)total, 0,
+              (long long)(T == kInfT ? -1 : (long long)T), t_it);
     trace_classes(a.w, it, p);
     fsum += total;
     ++it;
@@ -341,8 +454,8 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     DevStats& st = *a.w.stats;
     st.status = 0;
     st.iterations = it;
-    st.push_iters = it;
-    st.pull_iters = 0;
+    st.push_iters = it - pull_it;
+    st.pull_iters = pull_it;
     st.ballot_iters = ballot_it;
     st.online_iters = online_it;
     st.phases = (int)sh.phase;
@@ -362,6 +475,7 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
   SsspArgs<OffT> a{};
   a.n = (int)g->n;
   a.src = src;
+  a.pull_ok = g->symmetric ? 1 : 0;
   a.nreal = (int)g->n;
   a.ninst = 1;
   a.srcs = nullptr;
