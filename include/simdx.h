@@ -32,6 +32,18 @@
  *     simdx_graph_set_config (when a larger workspace is needed) and the
  *     batch / server entry points that say so; the algorithm calls allocate
  *     nothing.
+ *   - CUDA graphs: simdx_bfs, simdx_sssp, simdx_kcore, simdx_pagerank,
+ *     simdx_bfs_batch, simdx_sssp_batch (up to 64 sources) and
+ *     simdx_bfs_multi can be captured into a CUDA graph (stream capture on
+ *     `stream`) and replayed, each launch a cooperative kernel node, when
+ *     (a) stats is NULL (a captured call with stats returns EUNSUPPORTED),
+ *     (b) a call of the same kind ran on the graph outside the capture
+ *     before (it allocates the batch state; for simdx_bfs_multi with at
+ *     least as many roots), and (c) the replays do not overlap other calls
+ *     on the same graph.  Sources are kernel parameters, so a replay runs
+ *     the captured query; simdx_bfs_multi stages its roots in pinned memory
+ *     that a replay reads again, i.e. it replays the roots of the graph's
+ *     latest captured simdx_bfs_multi call.
  */
 #ifndef SIMDX_H
 #define SIMDX_H

@@ -21,6 +21,8 @@
 //               on overflow (or when forced) the ballot filter rebuilds
 //               sorted, unique lists from the level array or the frontier
 //               bitmap (Sec. 4, JIT control).
+#include <cstring>
+
 #include "simdx_internal.h"
 
 namespace simdx {
@@ -562,14 +564,28 @@ extern "C" int simdx_bfs_multi(simdx_graph* g, const int32_t* roots, int32_t k, 
     if (roots[i] < 0 || roots[i] >= g->n) return SIMDX_EINVAL;
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool cap = capturing(st);
   if ((size_t)k > g->roots_cap) {
+    // growing needs allocations, which a stream capture does not allow:
+    // a captured call must follow an uncaptured one with at least k roots
+    if (cap) return SIMDX_EUNSUPPORTED;
     dev_free(g->d_roots, st);
+    if (g->h_roots) cudaFreeHost(g->h_roots);
     g->d_roots = nullptr;
+    g->h_roots = nullptr;
     g->roots_cap = 0;
     SIMDX_CUDA(dev_alloc((void**)&g->d_roots, sizeof(int32_t) * (size_t)k, st));
+    SIMDX_CUDA(cudaHostAlloc((void**)&g->h_roots, sizeof(int32_t) * (size_t)k, cudaHostAllocDefault));
     g->roots_cap = (size_t)k;
   }
-  SIMDX_CUDA(cudaMemcpyAsync(g->d_roots, roots, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  if (cap) {
+    // a captured copy reads pinned memory when the graph replays: stage the
+    // roots there (a replay uses the roots of the latest captured call)
+    std::memcpy(g->h_roots, roots, sizeof(int32_t) * (size_t)k);
+    SIMDX_CUDA(cudaMemcpyAsync(g->d_roots, g->h_roots, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  } else {
+    SIMDX_CUDA(cudaMemcpyAsync(g->d_roots, roots, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  }
   return g->off_bits == 32 ? run_bfs<int32_t>(g, roots[0], levels, stats, st, g->d_roots, k)
                            : run_bfs<long long>(g, roots[0], levels, stats, st, g->d_roots, k);
 }

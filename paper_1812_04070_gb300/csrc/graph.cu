@@ -158,10 +158,27 @@ int prepare_launch(simdx_graph* g, cudaStream_t st) {
   return SIMDX_OK;
 }
 
+// A cooperative launch through the extensible launch API, which stream
+// capture records as a cooperative kernel node.
 int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st) {
   if (grid <= 0) return SIMDX_EUNSUPPORTED;
-  SIMDX_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kThreads), args, 0, st));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SIMDX_CUDA(cudaLaunchKernelExC(&cfg, kernel, args));
   return SIMDX_OK;
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
 }
 
 struct PendingStats {
@@ -192,6 +209,8 @@ int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st) {
   SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->ds, g->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
   SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->err, &g->sync->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (user) {
+    // the host callback owns a one-shot record: a captured graph would replay it
+    if (capturing(st)) return SIMDX_EUNSUPPORTED;
     PendingStats* ps = new (std::nothrow) PendingStats{g, user};
     if (!ps) return SIMDX_ENOMEM;
     cudaError_t e = cudaLaunchHostFunc(st, stats_cb, ps);
@@ -473,6 +492,7 @@ int simdx_graph_destroy(simdx_graph* g) {
   dev_free(g->sync, st);
   dev_free(g->ms_state, st);
   dev_free(g->d_roots, st);
+  if (g->h_roots) cudaFreeHost(g->h_roots);
   dev_free(g->sb_state, st);
   dev_free(g->pr_ws, st);
   dev_free(g->chunk_cnt, st);

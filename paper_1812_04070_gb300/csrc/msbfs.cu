@@ -21,7 +21,7 @@ namespace simdx {
 template <class OffT>
 struct MsArgs {
   int n, k;
-  const int32_t* srcs;  // device [k]
+  int32_t srcs[64];     // the sources (a kernel parameter: no copy to stage, so a launch can be captured)
   const OffT* off;
   const int32_t* idx;
   const OffT* ioff;
@@ -109,7 +109,7 @@ struct MsPull {
 };
 
 template <class OffT>
-__global__ void __launch_bounds__(kThreads, 4) msbfs_kernel(MsArgs<OffT> a) {
+__global__ void __launch_bounds__(kThreads, 4) msbfs_kernel(const __grid_constant__ MsArgs<OffT> a) {
   __shared__ CtaShared sh;
   __shared__ unsigned long long red_m[kWarps];
   const unsigned grid = gridDim.x;
@@ -296,12 +296,12 @@ int ensure_msbfs_state(simdx_graph* g, cudaStream_t st) {
 }
 
 template <class OffT>
-static int run_msbfs(simdx_graph* g, const int32_t* d_srcs, int k, int32_t* levels, long long ld, simdx_stats* stats,
+static int run_msbfs(simdx_graph* g, const int32_t* srcs, int k, int32_t* levels, long long ld, simdx_stats* stats,
                      cudaStream_t st) {
   MsArgs<OffT> a{};
   a.n = (int)g->n;
   a.k = k;
-  a.srcs = d_srcs;
+  for (int i = 0; i < k; ++i) a.srcs[i] = srcs[i];
   a.off = (const OffT*)g->off;
   a.idx = g->idx;
   a.ioff = (const OffT*)g->in_off;
@@ -335,14 +335,11 @@ extern "C" int simdx_bfs_batch(simdx_graph* g, const int32_t* srcs, int32_t k, i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = ensure_msbfs_state(g, st);
   if (rc) return rc;
-  int32_t* d_src = reinterpret_cast<int32_t*>(g->ms_state + 3 * (size_t)(g->n + 1));
   for (int b = 0; b < k; b += 64) {
     const int kb = k - b < 64 ? k - b : 64;
-    // sources of this pass: a small pageable copy ordered on the stream
-    SIMDX_CUDA(cudaMemcpyAsync(d_src, srcs + b, sizeof(int32_t) * kb, cudaMemcpyHostToDevice, st));
     int32_t* lv = levels + (size_t)b * (size_t)g->n;
-    rc = g->off_bits == 32 ? run_msbfs<int32_t>(g, d_src, kb, lv, g->n, b + kb >= k ? stats : nullptr, st)
-                           : run_msbfs<long long>(g, d_src, kb, lv, g->n, b + kb >= k ? stats : nullptr, st);
+    rc = g->off_bits == 32 ? run_msbfs<int32_t>(g, srcs + b, kb, lv, g->n, b + kb >= k ? stats : nullptr, st)
+                           : run_msbfs<long long>(g, srcs + b, kb, lv, g->n, b + kb >= k ? stats : nullptr, st);
     if (rc) return rc;
   }
   return SIMDX_OK;

@@ -86,38 +86,34 @@ struct PrArgs {
   const int32_t* iidx;
   long long e;       // in-edges
   float* rank;
+  float* inv;        // [n] 1 / outdeg (0 for outdeg 0), set once per run
   PrWalk wk;
   Work w;
   Knobs k;
 };
 
 // Per-iteration view: where c_t is read and x_{t+1}, c_{t+1} are written,
-// plus this thread's share of the two global sums.  x and 1/outdeg of the
-// vertices with in-edges are kept in list-0 order (rank r <-> vertex l0[r]),
-// so finishing a row loads them by rank next to its vertex id instead of
-// after it; only c, gathered by in-neighbour id, stays in vertex order.
+// plus this thread's share of the two global sums.
 template <class OffT>
 struct PrPull {
   const float* cin;
   float* cout;
-  const float* xro;   // x_t by rank
-  float* xrn;         // x_{t+1} by rank
-  const float* invr;  // 1 / outdeg by rank (0 for outdeg 0)
-  float dn;           // D_t / n
+  const float* xold;
+  float* xnew;
+  float dn;                             // d * D_t / n folded with the teleport term below
   float l1 = 0.f, dang = 0.f;  // this thread's share, summed in its own fixed order
-  // x_{t+1} and c_{t+1} of the row of rank r (vertex u) from its in-neighbour
-  // sum, given 1/outdeg and x_t already loaded (loads and stores kept apart
-  // so that several rows' loads are in flight together).
-  __device__ __forceinline__ void store(const PrArgs<OffT>& a, float base, int r, int u, float sum, float iv,
-                                        float xo) {
+  // x_{t+1}(u) and c_{t+1}(u) from the in-neighbour sum, given 1/outdeg(u)
+  // and x_t(u) already loaded (loads and stores kept apart so that several
+  // rows' loads are in flight together).
+  __device__ __forceinline__ void store(const PrArgs<OffT>& a, float base, int u, float sum, float iv, float xo) {
     const float xn = base + a.d * (sum + dn);
-    xrn[r] = xn;
+    xnew[u] = xn;
     cout[u] = xn * iv;
     if (iv == 0.f) dang += xn;
     l1 += fabsf(xn - xo);
   }
-  __device__ __forceinline__ void finish(const PrArgs<OffT>& a, float base, const int32_t* l0, int r, float sum) {
-    store(a, base, r, l0[r], sum, invr[r], xro[r]);
+  __device__ __forceinline__ void finish(const PrArgs<OffT>& a, float base, int u, float sum) {
+    store(a, base, u, sum, a.inv[u], xold[u]);
   }
 };
 
@@ -126,7 +122,7 @@ __device__ __forceinline__ float pick4(float s0, float s1, float s2, float s3, i
 }
 
 struct CrossOut {
-  int r;      // the row's rank when this warp finishes it, else -1
+  int u;      // the row's vertex when this warp finishes it, else -1
   float sum;  // the row's total
 };
 
@@ -148,7 +144,7 @@ __device__ __noinline__ CrossOut pr_cross(const PrWalk* wk, const int32_t* l0, i
     double tot = tp[w0];
     for (int j = w0 + 1; j <= w1; ++j) tot += hp[j];
     wk->done[w1] = 0;
-    r.r = rank;
+    r.u = l0[rank];
     r.sum = (float)tot;
   }
   return r;
@@ -270,7 +266,7 @@ __device__ __forceinline__ void pr_tile(const PrArgs<OffT>& a, PrPull<OffT>& f, 
     if (rb == cx.head_rank) {  // a row begun by an earlier warp
       ends &= ~(1u << (first - 1));
       const CrossOut c = pr_cross(&a.wk, l0, rb, 0, (double)hi + (double)lo, gw, cx.hw0, cx.hw1, cx.hn);
-      if (c.r >= 0) f.finish(a, base, l0, c.r, c.sum);
+      if (c.u >= 0) f.finish(a, base, c.u, c.sum);
     } else {
       const float tot = hi + lo;
       v0 = first == 1 ? tot : v0;
@@ -284,15 +280,19 @@ __device__ __forceinline__ void pr_tile(const PrArgs<OffT>& a, PrPull<OffT>& f, 
   const bool f0 = (ends & 1u) && r0 < c0n, f1 = (ends & 2u) && r1 < c0n;
   const bool f2 = (ends & 4u) && r2 < c0n, f3 = (ends & 8u) && r3 < c0n;
   int u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+  if (f0) u0 = l0[r0];
+  if (f1) u1 = l0[r1];
+  if (f2) u2 = l0[r2];
+  if (f3) u3 = l0[r3];
   float i0 = 0.f, i1 = 0.f, i2 = 0.f, i3 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
-  if (f0) { u0 = l0[r0]; i0 = f.invr[r0]; o0 = f.xro[r0]; }
-  if (f1) { u1 = l0[r1]; i1 = f.invr[r1]; o1 = f.xro[r1]; }
-  if (f2) { u2 = l0[r2]; i2 = f.invr[r2]; o2 = f.xro[r2]; }
-  if (f3) { u3 = l0[r3]; i3 = f.invr[r3]; o3 = f.xro[r3]; }
-  if (f0) f.store(a, base, r0, u0, v0, i0, o0);
-  if (f1) f.store(a, base, r1, u1, v1, i1, o1);
-  if (f2) f.store(a, base, r2, u2, v2, i2, o2);
-  if (f3) f.store(a, base, r3, u3, v3, i3, o3);
+  if (f0) { i0 = a.inv[u0]; o0 = f.xold[u0]; }
+  if (f1) { i1 = a.inv[u1]; o1 = f.xold[u1]; }
+  if (f2) { i2 = a.inv[u2]; o2 = f.xold[u2]; }
+  if (f3) { i3 = a.inv[u3]; o3 = f.xold[u3]; }
+  if (f0) f.store(a, base, u0, v0, i0, o0);
+  if (f1) f.store(a, base, u1, v1, i1, o1);
+  if (f2) f.store(a, base, u2, v2, i2, o2);
+  if (f3) f.store(a, base, u3, v3, i3, o3);
   if (A31) {
     float e;
     two_sum(ch, B31, ch, e);
@@ -329,7 +329,7 @@ __device__ __forceinline__ void pr_walk(const PrArgs<OffT>& a, PrPull<OffT>& f, 
       const bool tail = r >= rank0;
       const CrossOut c = pr_cross(&a.wk, l0, r, tail, (double)ch + (double)cl, gw, tail ? gw : cx.hw0,
                                   tail ? cx.tail_w1 : cx.hw1, tail ? cx.tn : cx.hn);
-      if (c.r >= 0) f.finish(a, base, l0, c.r, c.sum);
+      if (c.u >= 0) f.finish(a, base, c.u, c.sum);
     }
   }
 }
@@ -370,12 +370,9 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
   const long long gthreads = (long long)grid * kThreads;
   const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const long long nwarps = (long long)grid * kWarps;
-  // state (5 n floats): x by rank twice, c by vertex twice, 1/outdeg by rank
-  float* xr0 = reinterpret_cast<float*>(a.w.state);
-  float* xr1 = xr0 + n;
-  float* cbuf0 = xr0 + 2 * (size_t)n;
-  float* cbuf1 = xr0 + 3 * (size_t)n;
-  float* invr = xr0 + 4 * (size_t)n;
+  float* xalt = reinterpret_cast<float*>(a.w.state);
+  float* cbuf0 = xalt + n;
+  float* cbuf1 = xalt + 2 * (size_t)n;
   const OffT* off = a.off;
   const OffT* ioff = a.ioff;
   auto all = [](int) { return true; };
@@ -391,7 +388,9 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     unsigned long long dang = 0;
     for (long long v = gtid; v < n; v += gthreads) {
       const long long od = (long long)gload(off + v + 1) - (long long)gload(off + v);
+      a.rank[v] = x0;
       cbuf0[v] = od > 0 ? x0 / (float)od : 0.f;
+      a.inv[v] = od > 0 ? 1.0f / (float)od : 0.f;
       if (od == 0) dang += to_fix(x0);
     }
     for (long long q = gtid; q < 4 * wk.ntiles + 8; q += gthreads) wk.head[q] = 0u;
@@ -418,33 +417,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
   // then each warp searches the prefix for its range
   const long long ntiles = wk.ntiles;
   const long long nch = (ntiles + kPrChunk - 1) / kPrChunk;
-  const int32_t* l0 = a.w.list[0][0];
-  const int32_t* l1 = a.w.list[0][1];
-  const int c0n = (int)cnt[0], c1n = (int)cnt[1];
   clear_next_slot(s, sh);
-  {
-    // x_0 and 1/outdeg by rank; vertices without in-edges: how many have no
-    // out-edges (their rank is dangling) and how many have some
-    const float x0 = 1.0f / (float)n;
-    for (long long r = gtid; r < c0n; r += gthreads) {
-      const int u = l0[r];
-      const long long od = (long long)gload(off + u + 1) - (long long)gload(off + u);
-      invr[r] = od > 0 ? 1.0f / (float)od : 0.f;
-      xr0[r] = x0;
-    }
-    unsigned long long nd = 0, no = 0;
-    for (long long i = gtid; i < c1n; i += gthreads) {
-      const int u = l1[i];
-      if (gload(off + u + 1) == gload(off + u)) ++nd; else ++no;
-    }
-    nd = cta_sum_u64(nd, sh);
-    no = cta_sum_u64(no, sh);
-    if (threadIdx.x == 0) {
-      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-      if (nd) atomicAdd(&slot.aux0, nd);
-      if (no) atomicAdd(&slot.aux1, no);
-    }
-  }
   for (long long c = blockIdx.x; c < nch; c += grid) {
     unsigned long long sum = 0;
     for (long long q = c * kPrChunk + threadIdx.x; q < (c + 1) * kPrChunk && q < ntiles; q += kThreads)
@@ -453,8 +426,6 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     if (threadIdx.x == 0) wk.csum[c] = sum;
   }
   if (!grid_sync(s, grid, sh, k)) return;
-  const unsigned long long n1_dang = s->slot[slot_of(sh.phase - 1)].aux0;  // no in-edges, no out-edges
-  const unsigned long long n1_out = s->slot[slot_of(sh.phase - 1)].aux1;   // no in-edges, some out-edges
   clear_next_slot(s, sh);
   unsigned long long total = 0;
   {
@@ -503,6 +474,9 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
   }
   if (!grid_sync(s, grid, sh, k)) return;
   // ---- each warp: rows starting before its range and the cross-warp rows
+  const int32_t* l0 = a.w.list[0][0];
+  const int32_t* l1 = a.w.list[0][1];
+  const int c0n = (int)cnt[0];
   const int t_beg = wk.tstart[gw], t_end = wk.tstart[gw + 1];
   int rank0 = 0;
   PrCross cx;
@@ -539,7 +513,6 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
   }
 
   const float base = (1.0f - a.d) / (float)n;
-  float x1 = 1.0f / (float)n;  // x_t of every vertex without in-edges (they all agree)
   int t = 0;
   double l1_last = 0.0;
   while (true) {
@@ -551,35 +524,22 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     PrPull<OffT> f;
     f.cin = (t & 1) ? cbuf1 : cbuf0;
     f.cout = (t & 1) ? cbuf0 : cbuf1;
-    f.xro = (t & 1) ? xr1 : xr0;
-    f.xrn = (t & 1) ? xr0 : xr1;
-    f.invr = invr;
+    f.xold = (t & 1) ? xalt : a.rank;
+    f.xnew = (t & 1) ? a.rank : xalt;
     f.dn = __ull2float_rn(Dfix) * 8.67361737988403547e-19f / (float)n;  // D_t / n (2^-60 units)
-    const float x1n = base + a.d * f.dn;
     {
       ClassTimer tm(&slot);
       pr_walk<OffT>(a, f, base, l0, c0n, (int)gw, t_beg, t_end, rank0, cx);
       tm.lap(0);
-      if (n1_out)  // directed graphs: vertices with out-edges but no in-edges
-        for (long long i = gtid; i < c1n; i += gthreads) {
-          const int u = l1[i];
-          const long long od = (long long)gload(off + u + 1) - (long long)gload(off + u);
-          if (od > 0) f.cout[u] = x1n * (1.0f / (float)od);
-        }
+      for (unsigned i = (unsigned)gtid; i < cnt[1]; i += (unsigned)gthreads) f.finish(a, base, l1[i], 0.f);
       tm.lap(1);
     }
     const unsigned long long l1s = cta_sum_u64(to_fix(f.l1), sh);
     const unsigned long long dg = cta_sum_u64(to_fix(f.dang), sh);
     if (threadIdx.x == 0) {
-      unsigned long long l1x = l1s, dgx = dg;
-      if (blockIdx.x == 0) {  // the vertices without in-edges, all at once
-        l1x += to_fix((float)c1n * fabsf(x1n - x1));
-        dgx += to_fix((float)n1_dang * x1n);
-      }
-      atomicAdd(&slot.aux0, dgx);
-      atomicAdd(&slot.aux1, l1x);
+      atomicAdd(&slot.aux0, dg);
+      atomicAdd(&slot.aux1, l1s);
     }
-    x1 = x1n;
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     Dfix = p.aux0;
@@ -592,12 +552,9 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
   long long evisit = 0;  // in-edges this warp summed, every iteration
   if (lane_id() == 0 && t_beg < t_end)
     evisit = (long long)t * (min((long long)t_end * kTile, a.e) - (long long)t_beg * kTile);
-  // ---- result in vertex order: x_t by rank is in xr1 for odd t, xr0 for even t
-  {
-    const float* xf = (t & 1) ? xr1 : xr0;
-    for (long long r = gtid; r < c0n; r += gthreads) a.rank[l0[r]] = xf[r];
-    for (long long i = gtid; i < c1n; i += gthreads) a.rank[l1[i]] = x1;
-  }
+  // ---- result: x_t is in rank for even t, in xalt for odd t
+  if (t & 1)
+    for (long long v = gtid; v < n; v += gthreads) a.rank[v] = xalt[v];
   unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
   if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
   if (!grid_sync(s, grid, sh, k)) return;
@@ -634,6 +591,7 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   a.iidx = g->in_idx;
   a.e = g->e;
   a.rank = rank;
+  a.inv = static_cast<float*>(g->state) + 3 * (size_t)g->n;
   a.w = make_work(g);
   a.k = make_knobs(g);
   const void* kern = (const void*)pagerank_kernel<OffT>;

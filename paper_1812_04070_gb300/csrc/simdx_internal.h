@@ -49,6 +49,7 @@ struct simdx_graph {
   int* warp_start = nullptr;
   unsigned long long* ms_state = nullptr;  // batched BFS masks (allocated on first use)
   int32_t* d_roots = nullptr;              // device copy of multi-root BFS roots
+  int32_t* h_roots = nullptr;              // pinned staging of the roots (captured calls)
   size_t roots_cap = 0;
   void* sb_state = nullptr;                // batched SSSP lists and state (first use)
   size_t sb_bytes = 0;
@@ -90,8 +91,12 @@ int prepare_launch(simdx_graph* g, cudaStream_t st);
 // Launch `kernel` cooperatively with `grid` CTAs of kThreads threads.
 int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st);
 
-// Enqueue the copy of device statistics into `user` (may be NULL).
+// Enqueue the copy of device statistics into `user` (may be NULL; must be
+// NULL while `st` is being captured into a CUDA graph).
 int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st);
+
+// Whether `st` is being captured into a CUDA graph.
+bool capturing(cudaStream_t st);
 
 int cuda_status(cudaError_t e, const char* what);
 

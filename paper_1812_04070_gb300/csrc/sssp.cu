@@ -31,7 +31,8 @@ struct SsspArgs {
   int n, src;           // n: state ids (nreal, or k * nreal for a batch)
   int nreal, ninst;
   int pull_ok;          // symmetric graph: in-edge weights are the CSR weights, pull allowed
-  const int32_t* srcs;  // device [ninst] (batch only)
+  const int32_t* srcs;  // device [ninst] (batch of more than 64 only)
+  int32_t src_list[64]; // the sources of a batch of up to 64, as a kernel parameter (no copy to stage)
   const OffT* off;
   const int32_t* idx;
   const uint32_t* wt;
@@ -59,7 +60,7 @@ struct SsspPush {
   const Knobs& k;
   unsigned grid;
   unsigned long long nrec = 0, mrec = 0;
-  __device__ SsspPush(SsspArgs<OffT>& a, uint32_t* pd, uint8_t* pe, uint32_t* ax, unsigned long long t,
+  __device__ SsspPush(const SsspArgs<OffT>& a, uint32_t* pd, uint8_t* pe, uint32_t* ax, unsigned long long t,
                       CtaShared& s, unsigned g)
       : nreal(a.nreal), dist(a.dist), pdist(pd), pend(pe), off(a.off), wt(a.wt), aux3(ax), T(t), sh(s), w(a.w),
         k(a.k), grid(g) {}
@@ -200,7 +201,7 @@ struct SsspPull {
 };
 
 template <class OffT, bool V>
-__global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
+__global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
   __shared__ unsigned red_u[kWarps];
   const unsigned grid = gridDim.x;
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
     bool is_src;
     if (V) {
       const long long inst = x / nreal;
-      is_src = (x - inst * nreal) == a.srcs[inst];
+      is_src = (x - inst * nreal) == (a.ninst <= 64 ? a.src_list[inst] : a.srcs[inst]);
     } else {
       is_src = x == a.src;
     }
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(SsspArgs<OffT> a) {
   if (blockIdx.x == 0) {
     const int nsrc = V ? a.ninst : 1;
     for (int i = threadIdx.x; i < nsrc; i += kThreads) {
-      const int v = V ? a.srcs[i] : a.src;
+      const int v = V ? (a.ninst <= 64 ? a.src_list[i] : a.srcs[i]) : a.src;
       long long d = (long long)a.off[v + 1] - (long long)a.off[v];
       int c = degree_class(d, k);
       const unsigned pos = atomicAdd(&s->slot[0].list_cnt[c], 1u);
@@ -524,13 +525,18 @@ static int run_sssp_batch(simdx_graph* g, const int32_t* srcs, int k, uint32_t* 
   uint32_t* pdist = aux3 + 2 * cap;
   uint8_t* pend = reinterpret_cast<uint8_t*>(pdist + ids);
   int32_t* d_srcs = reinterpret_cast<int32_t*>(((uintptr_t)(pend + ids) + 15) & ~(uintptr_t)15);
-  SIMDX_CUDA(cudaMemcpyAsync(d_srcs, srcs, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  if (k <= 64) {
+    d_srcs = nullptr;
+  } else {
+    SIMDX_CUDA(cudaMemcpyAsync(d_srcs, srcs, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  }
   SsspArgs<OffT> a{};
   a.n = (int)ids;
   a.src = srcs[0];
   a.nreal = (int)g->n;
   a.ninst = k;
   a.srcs = d_srcs;
+  for (int i = 0; i < k && i < 64; ++i) a.src_list[i] = srcs[i];
   a.off = (const OffT*)g->off;
   a.idx = g->idx;
   a.wt = g->w;
