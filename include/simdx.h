@@ -205,9 +205,12 @@ SIMDX_API int simdx_bfs(simdx_graph *g, int32_t src, int32_t *levels, simdx_stat
 /* SSSP (Sec. 2.1, Sec. 3.3; aggregation combine = min): dist[v] = length
  * of a shortest path from src with the graph's uint32 weights, UINT32_MAX
  * if unreachable.  Delta-stepping: vertices whose distance changed and is
- * below the current bucket bound are active (Sec. 3.3).  Path lengths must
- * stay below UINT32_MAX.  dist: device uint32[n].  Errors: EINVAL (no
- * weights, src out of range, NULL dist). */
+ * below the current bucket bound are active (Sec. 3.3); the bucket width is
+ * the `delta` knob (a graph starts at 16 x its largest weight).  Push by
+ * default; direction = 2 forces pull iterations (symmetric graphs: every
+ * vertex takes the min over its frontier in-neighbours, Sec. 5).  Path
+ * lengths must stay below UINT32_MAX.  dist: device uint32[n].  Errors:
+ * EINVAL (no weights, src out of range, NULL dist). */
 SIMDX_API int simdx_sssp(simdx_graph *g, int32_t src, uint32_t *dist, simdx_stats *stats,
                void *stream);
 
@@ -225,9 +228,11 @@ SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
  *   x_0 = 1/n;  x_{t+1}(v) = (1-d)/n + d*(sum_{u in N_in(v)} x_t(u)/outdeg(u)
  *                                         + D_t/n),
  * D_t = rank on out-degree-0 vertices.  Stops after the first iteration
- * whose L1 change is < l1_tol, or after max_iter iterations.  FP32 ranks,
- * FP32 per-vertex sums in a fixed order, FP64 global sums: results are
- * identical run to run.  rank: device float[n].
+ * whose L1 change is < l1_tol, or after max_iter iterations.  FP32 ranks;
+ * per-vertex sums in FP32 in a fixed order (cross-tile parts carried as a
+ * TwoSum pair, cross-warp parts added in FP64); the L1 and dangling sums in
+ * 2^-60 fixed point, whose total does not depend on order: results are
+ * identical run to run for a given grid.  rank: device float[n].
  * Errors: EINVAL (NULL rank, damping outside [0,1), max_iter < 0). */
 SIMDX_API int simdx_pagerank(simdx_graph *g, float damping, float l1_tol, int32_t max_iter,
                    float *rank, simdx_stats *stats, void *stream);
@@ -246,9 +251,12 @@ SIMDX_API int simdx_pagerank(simdx_graph *g, float damping, float l1_tol, int32_
 SIMDX_API int simdx_bfs_batch(simdx_graph *g, const int32_t *srcs, int32_t k, int32_t *levels,
                               simdx_stats *stats, void *stream);
 
-/* Batched SSSP: k sources in one persistent launch.  The k queries run on k
- * virtual copies of the graph (state id inst * n + v, one CSR), so every
- * iteration processes all queries' frontiers together.  srcs: host int32[k];
+/* Batched SSSP (growth direction (a)): k sources in one persistent launch.
+ * The k queries run on k virtual copies of the graph (state id inst * n + v,
+ * one CSR) with delta-stepping buckets shared by all copies, so every
+ * iteration processes all queries' frontiers together.  Up to 64 sources
+ * travel as kernel parameters (the call can then be captured into a CUDA
+ * graph); more are copied to the device first.  srcs: host int32[k];
  * dist: device uint32[k*n], row i = distances from srcs[i], identical to k
  * simdx_sssp calls.  The first call (or a larger k than any before)
  * allocates the batch state (about 45 bytes per vertex per query); later
