@@ -30,7 +30,6 @@ template <class OffT>
 struct SsspArgs {
   int n, src;           // n: state ids (nreal, or k * nreal for a batch)
   int nreal, ninst;
-  int pull_ok;          // symmetric graph: in-edge weights are the CSR weights, pull allowed
   const int32_t* srcs;  // device [ninst] (batch of more than 64 only)
   int32_t src_list[64]; // the sources of a batch of up to 64, as a kernel parameter (no copy to stage)
   const OffT* off;
@@ -200,7 +199,7 @@ struct SsspPull {
   }
 };
 
-template <class OffT, bool V>
+template <class OffT, bool V, bool PULL>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
   __shared__ unsigned red_u[kWarps];
@@ -233,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     pdist[x] = 0xffffffffu;
     pend[x] = is_src ? 1 : 0;  // the source is the first pending vertex
   }
-  if (!V && a.pull_ok)  // pull frontiers (BFS leaves these bitmaps as it likes)
+  if (PULL)  // pull frontiers (BFS leaves these bitmaps as it likes)
     for (long long q = gtid; q < (((long long)n + 31) >> 5); q += gthreads) {
       a.w.bm_f[0][q] = 0u;
       a.w.bm_f[1][q] = 0u;
@@ -366,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     // the densest frontier of these graphs (R-MAT 20 / 22 / 24, pull in every
     // iteration with more than n / beta frontier vertices for beta 8..64:
     // 1.5-1.8x slower), so the automatic choice is push.
-    const bool pull = !V && a.pull_ok && k.direction == 2;
+    const bool pull = PULL;  // the pull instantiation runs only when direction forces it
     unsigned long long tn = 0, tm = 0;
     if (pull) {
       uint32_t* fbm = a.w.bm_f[pull_it & 1];
@@ -468,7 +467,8 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
 }
 
 const void* sssp_kernel_ptr(int off_bits) {
-  return off_bits == 32 ? (const void*)sssp_kernel<int32_t, false> : (const void*)sssp_kernel<long long, false>;
+  return off_bits == 32 ? (const void*)sssp_kernel<int32_t, false, false>
+                         : (const void*)sssp_kernel<long long, false, false>;
 }
 
 template <class OffT>
@@ -476,7 +476,6 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
   SsspArgs<OffT> a{};
   a.n = (int)g->n;
   a.src = src;
-  a.pull_ok = g->symmetric ? 1 : 0;
   a.nreal = (int)g->n;
   a.ninst = 1;
   a.srcs = nullptr;
@@ -486,7 +485,10 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
   a.dist = dist;
   a.w = make_work(g);
   a.k = make_knobs(g);
-  const void* kern = (const void*)sssp_kernel<OffT, false>;
+  // pull iterations are compiled into their own instantiation, so that the
+  // push kernel carries none of their registers
+  const bool pull = g->symmetric && g->cfg.direction == 2;
+  const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true> : (const void*)sssp_kernel<OffT, false, false>;
   int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
@@ -549,7 +551,7 @@ static int run_sssp_batch(simdx_graph* g, const int32_t* srcs, int k, uint32_t* 
   }
   a.w.state = pdist;  // the kernel finds pend right after the ids processed distances
   a.k = make_knobs(g);
-  const void* kern = (const void*)sssp_kernel<OffT, true>;
+  const void* kern = (const void*)sssp_kernel<OffT, true, false>;
   int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
