@@ -51,6 +51,14 @@ def test_rmat20_sssp_kcore_pagerank():
     assert st.status == 0
     assert rel <= 1e-6, rel
     assert abs(t - t_stop) <= 1, (t, t_stop)
+    # against the converged fixed point: the 1e-6 L1 stopping rule alone leaves
+    # up to about d / (1 - d) * 1e-6 = 5.7e-6 (relative L1)
+    x = G.pagerank().cpu().numpy().astype(np.float64)
+    xc, _, _ = oracle.pagerank(g.offsets, g.indices, tol=1e-13, max_iter=100000)
+    rel_conv = np.abs(x - xc).sum() / np.abs(xc).sum()
+    print(f"PageRank R-MAT 20: relative L1 {rel:.2e} vs the FP64 oracle after the same {t} iterations, "
+          f"{rel_conv:.2e} vs the converged fixed point")
+    assert rel_conv <= 1e-5, rel_conv
     G.close()
 
 
