@@ -33,7 +33,7 @@ std::vector<Knob> knobs_for(int algo) {
   if (algo == SIMDX_ALGO_PAGERANK) return k;  // all vertices active; no task classes
   k.push_back({"small_max", {8, 16, 32, 64}, SIMDX_KNOB_I(small_max)});
   k.push_back({"med_max", {128, 256, 512, 1024, 2048}, SIMDX_KNOB_I(med_max)});
-  k.push_back({"huge_min", {2048, 4096, 8192, 16384}, SIMDX_KNOB_I(huge_min)});
+  k.push_back({"huge_min", {1024, 2048, 4096, 8192, 16384}, SIMDX_KNOB_I(huge_min)});
   k.push_back({"bin_per_thread", {16, 32, 64, 128}, SIMDX_KNOB_I(bin_per_thread)});
   if (algo == SIMDX_ALGO_BFS) {
     k.push_back({"alpha", {4, 7, 14, 28, 56}, SIMDX_KNOB_I(alpha)});
