@@ -29,6 +29,7 @@ namespace simdx {
 
 enum { kPush = 1, kPull = 2 };
 constexpr int kPullFirst = 8;  // in-edges every pull candidate checks on its own lane
+constexpr int kPullPer = 2;    // pull candidates per lane per round (their loads overlap)
 enum { kOnline = 1, kBallot = 2 };
 
 template <class OffT>
@@ -107,14 +108,22 @@ struct BfsPush {
 
 struct PullShared {
   unsigned newbits[kWarps][32];
-  int defer_v[kWarps][32];
-  int defer_j[kWarps][32];
+  int defer_v[kWarps][32 * kPullPer];
+  int defer_j[kWarps][32 * kPullPer];
 };
 
 // One pull iteration over all unvisited vertices with an in-edge.  Each warp
-// takes 32 bitmap words, compacts their candidates and gives one candidate
-// to each lane; candidates with in-degree >= small_max are scanned by the
-// whole warp, 32 edges at a time, stopping at the first frontier hit.
+// takes 32 bitmap words, compacts their candidates and gives kPullPer of them
+// to each lane per round; all loads that do not depend on one another are
+// issued together (both candidates' in-edge offsets and out-degrees, then
+// their first four in-edges, then the frontier bits of those), so a lane has
+// several chains in flight.  A candidate checks its first kPullFirst
+// in-neighbours on its own lane (sorted adjacency: low ids, the hubs, come
+// first, so this resolves almost every candidate); the rest of a higher
+// in-degree candidate is scanned by the whole warp, 32 edges at a time,
+// stopping at the first frontier hit.  Found vertices go to the next
+// frontier bitmap only: a pull level is nearly always followed by another
+// pull level, and a push level after it lists the frontier from the bitmap.
 template <class OffT>
 __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
                          uint32_t* fbm_next, CtaShared& sh, PullShared& ps, unsigned grid,
@@ -137,87 +146,115 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
     const int total = __shfl_sync(kFull, incl, 31);
     ps.newbits[warp][lane] = 0u;
     __syncwarp();
-    for (int r = 0; r < total; r += 32) {
-      const int kk = r + lane;
-      int j = 0;
+    for (int r = 0; r < total; r += 32 * kPullPer) {
+      int u[kPullPer], jb[kPullPer];
+      long long beg[kPullPer], end[kPullPer], od[kPullPer];
 #pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        int t = __shfl_sync(kFull, incl, j + step - 1);
-        if (t <= kk) j += step;
-      }
-      const int excl_j = __shfl_sync(kFull, incl - c, j);
-      const unsigned cand_j = __shfl_sync(kFull, cand, j);
-      bool deferred = false;
-      int u = -1, bit = 0;
-      if (kk < total) {
-        bit = nth_set_bit(cand_j, kk - excl_j);
-        u = (int)((g * 32 + j) * 32 + bit);
-        const long long beg = gload(a.ioff + u), end = gload(a.ioff + u + 1);
-        // every candidate first checks its first kPullFirst in-neighbours on
-        // its own lane (sorted adjacency: low ids, the hubs, come first, so
-        // this resolves almost every candidate); only the rest is deferred
-        const long long lim = end - beg < kPullFirst ? end : beg + kPullFirst;
-        bool found = false;
-        long long p = beg;
-        for (; p + 4 <= lim && !found; p += 4) {
-          int v0 = gload(a.iidx + p), v1 = gload(a.iidx + p + 1), v2 = gload(a.iidx + p + 2),
-              v3 = gload(a.iidx + p + 3);
-          found = bm_test(fbm, v0) | bm_test(fbm, v1) | bm_test(fbm, v2) | bm_test(fbm, v3);
+      for (int q = 0; q < kPullPer; ++q) {
+        const int kk = r + 32 * q + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          int t = __shfl_sync(kFull, incl, j + step - 1);
+          if (t <= kk) j += step;
         }
-        for (; p < lim && !found; ++p) found = bm_test(fbm, gload(a.iidx + p));
-        evisit += (p < lim ? p : lim) - beg;
-        if (found) {
-          a.level[u] = next;
-          atomicOr(&ps.newbits[warp][j], 1u << bit);
-          long long od = (long long)gload(a.off + u + 1) - (long long)gload(a.off + u);
+        const int excl_j = __shfl_sync(kFull, incl - c, j);
+        const unsigned cand_j = __shfl_sync(kFull, cand, j);
+        u[q] = -1;
+        jb[q] = 0;
+        beg[q] = end[q] = od[q] = 0;
+        if (kk < total) {
+          const int bit = nth_set_bit(cand_j, kk - excl_j);
+          u[q] = (int)((g * 32 + j) * 32 + bit);
+          jb[q] = (j << 5) | bit;
+        }
+      }
+      // the candidates' in-edge ranges and out-degrees
+#pragma unroll
+      for (int q = 0; q < kPullPer; ++q)
+        if (u[q] >= 0) {
+          beg[q] = gload(a.ioff + u[q]);
+          end[q] = gload(a.ioff + u[q] + 1);
+          od[q] = (long long)gload(a.off + u[q] + 1) - (long long)gload(a.off + u[q]);
+        }
+      // their first four in-neighbours, then the frontier bits of those
+      int v[kPullPer][4];
+#pragma unroll
+      for (int q = 0; q < kPullPer; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[q][e] = (u[q] >= 0 && beg[q] + e < end[q]) ? gload(a.iidx + beg[q] + e) : -1;
+      bool found[kPullPer];
+#pragma unroll
+      for (int q = 0; q < kPullPer; ++q) {
+        bool f = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) f |= v[q][e] >= 0 && bm_test(fbm, v[q][e]);
+        found[q] = f;
+      }
+      bool deferred[kPullPer];
+#pragma unroll
+      for (int q = 0; q < kPullPer; ++q) {
+        deferred[q] = false;
+        if (u[q] < 0) continue;
+        // the rest of the first kPullFirst in-neighbours, on this lane
+        const long long lim = end[q] - beg[q] < kPullFirst ? end[q] : beg[q] + kPullFirst;
+        long long p = beg[q] + 4;
+        for (; p < lim && !found[q]; ++p) found[q] = bm_test(fbm, gload(a.iidx + p));
+        const long long upto = found[q] ? (p < beg[q] + 4 ? beg[q] + 4 : p) : lim;
+        evisit += (upto < end[q] ? upto : end[q]) - beg[q];
+        if (found[q]) {
+          a.level[u[q]] = next;
+          atomicOr(&ps.newbits[warp][jb[q] >> 5], 1u << (jb[q] & 31));
           ++nrec;
-          mrec += (unsigned long long)od;
-          online_record(u, degree_class(od, a.k), sh, a.w, a.k, grid);
-        } else if (end - lim >= a.k.huge_min) {
+          mrec += (unsigned long long)od[q];
+        } else if (end[q] - lim >= a.k.huge_min) {
           // scanned later by the whole grid (bfs_pull_big)
           const unsigned pos = (unsigned)atomicAdd(&slot.aux2, 1ull);
-          big[pos] = u;
+          big[pos] = u[q];
           found_big[pos] = 0u;
-        } else if (end > lim) {
-          deferred = true;  // the warp scans the remaining in-edges
+        } else if (end[q] > lim) {
+          deferred[q] = true;  // the warp scans the remaining in-edges
         }
       }
       // warp-cooperative scan of the deferred (higher in-degree) candidates
-      const unsigned dm = __ballot_sync(kFull, deferred);
-      if (deferred) {
-        int slot = __popc(dm & lanemask_lt());
-        ps.defer_v[warp][slot] = u;
-        ps.defer_j[warp][slot] = (j << 5) | bit;
+      int nd = 0;
+#pragma unroll
+      for (int q = 0; q < kPullPer; ++q) {
+        const unsigned dm = __ballot_sync(kFull, deferred[q]);
+        if (deferred[q]) {
+          const int sl = nd + __popc(dm & lanemask_lt());
+          ps.defer_v[warp][sl] = u[q];
+          ps.defer_j[warp][sl] = jb[q];
+        }
+        nd += __popc(dm);
       }
       __syncwarp();
-      const int nd = __popc(dm);
       for (int q = 0; q < nd; ++q) {
-        const int v = ps.defer_v[warp][q];
-        const long long beg = gload(a.ioff + v) + kPullFirst, end = gload(a.ioff + v + 1);
-        bool found = false;
+        const int vq = ps.defer_v[warp][q];
+        const long long b = gload(a.ioff + vq) + kPullFirst, e = gload(a.ioff + vq + 1);
+        bool hit_any = false;
         long long seen = 0;
-        for (long long base = beg; base < end; base += 128) {
+        for (long long base = b; base < e; base += 128) {
           bool hit = false;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const long long p = base + lane + 32 * q;
-            if (p < end) hit |= bm_test(fbm, gload(a.iidx + p));
+          for (int s4 = 0; s4 < 4; ++s4) {
+            const long long p = base + lane + 32 * s4;
+            if (p < e) hit |= bm_test(fbm, gload(a.iidx + p));
           }
           seen += 128;
           if (__any_sync(kFull, hit)) {
-            found = true;
+            hit_any = true;
             break;
           }
         }
-        if (lane == 0) evisit += seen < end - beg ? seen : end - beg;
-        if (found && lane == 0) {
-          a.level[v] = next;
-          const int jb = ps.defer_j[warp][q];
-          atomicOr(&ps.newbits[warp][jb >> 5], 1u << (jb & 31));
-          long long od = (long long)gload(a.off + v + 1) - (long long)gload(a.off + v);
+        if (lane == 0) evisit += seen < e - b ? seen : e - b;
+        if (hit_any && lane == 0) {
+          a.level[vq] = next;
+          const int jj = ps.defer_j[warp][q];
+          atomicOr(&ps.newbits[warp][jj >> 5], 1u << (jj & 31));
+          const long long odq = (long long)gload(a.off + vq + 1) - (long long)gload(a.off + vq);
           ++nrec;
-          mrec += (unsigned long long)od;
-          online_record(v, degree_class(od, a.k), sh, a.w, a.k, grid);
+          mrec += (unsigned long long)odq;
         }
         __syncwarp();
       }
@@ -463,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     fsum += (long long)n_f;
     ++it;
     if (nn == 0) break;
-    lists_ok = !ovf;
+    lists_ok = dir == kPush && !ovf;  // pull levels fill the bitmap, not the lists
     bm_ok = (dir == kPull);
     if (dir == kPull) fb ^= 1;
     lbuf ^= 1;
