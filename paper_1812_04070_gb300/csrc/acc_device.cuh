@@ -451,7 +451,12 @@ struct ClassTimer {
 
 // ------------------------------------------------------- chunked tasks
 // Inclusive prefix (in sh.pref) of the chunk counts ceil(deg / ch) of the nb
-// <= kChunkBatch class-3 tasks `items`.  All threads of the CTA call it.
+// <= kChunkBatch class-3 tasks `items`; returns the chunk size used.  With
+// `spread` > 0 a batch of fewer than `spread` x ch edges (one hub, say) is cut
+// into chunks of ceil(edges / spread), at least kMinChunk, so that it still
+// covers `spread` CTAs.  Every CTA computes the same prefix and size.  All
+// threads of the CTA call it.
+constexpr long long kMinChunk = kThreads;
 struct IdentityVertex {
   __device__ __forceinline__ int operator()(int v) const { return v; }
 };
@@ -459,20 +464,27 @@ struct IdentityVertex {
 // `rv` maps a task id to the vertex whose CSR row it walks (the identity
 // except for a batch of virtual graph copies, whose ids exceed n).
 template <class OffT, class RV = IdentityVertex>
-__device__ void chunk_prefix(const int32_t* items, int nb, const OffT* off, long long ch, CtaShared& sh,
-                             RV rv = RV{}) {
+__device__ long long chunk_prefix(const int32_t* items, int nb, const OffT* off, long long ch, CtaShared& sh,
+                                  RV rv = RV{}, unsigned spread = 0) {
   __syncthreads();
   const int b = threadIdx.x * 4;
-  int x[4];
+  long long d[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    x[q] = 0;
+    d[q] = 0;
     if (b + q < nb) {
       const int v = rv(items[b + q]);
-      const long long d = gload(off + v + 1) - gload(off + v);
-      x[q] = (int)((d + ch - 1) / ch);
+      d[q] = gload(off + v + 1) - gload(off + v);
     }
   }
+  if (spread) {
+    const unsigned long long eb = cta_sum_u64((unsigned long long)(d[0] + d[1] + d[2] + d[3]), sh);
+    const long long even = (long long)((eb + spread - 1) / spread);
+    if (even < ch) ch = even > kMinChunk ? even : kMinChunk;
+  }
+  int x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] = (int)((d[q] + ch - 1) / ch);
   const int tot = x[0] + x[1] + x[2] + x[3];
   int incl = tot;
   const int lane = lane_id(), warp = threadIdx.x >> 5;
@@ -491,6 +503,7 @@ __device__ void chunk_prefix(const int32_t* items, int nb, const OffT* off, long
     if (b + q < nb) sh.pref[b + q] = run;
   }
   __syncthreads();
+  return ch;
 }
 
 // Task of chunk kc: the smallest i with pref[i] > kc.
@@ -572,12 +585,13 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
                              long long ch, CtaShared& sh, long long& evisit, PhaseSlot* slot = nullptr) {
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   ClassTimer tm(slot);
-  // class 3: every task is cut into chunks of `ch` edges and the chunks of
-  // all tasks are dealt round-robin to the CTAs (edge-balanced over the grid)
+  // class 3: every task is cut into chunks of `ch` edges (fewer when the batch
+  // would not fill the grid) and the chunks of all tasks are dealt round-robin
+  // to the CTAs (edge-balanced over the grid)
   auto rvf = [&f](int v) { return f.rv(v); };
   for (unsigned b0 = 0; b0 < cnt[3]; b0 += kChunkBatch) {
     const int nb = (int)min((unsigned)kChunkBatch, cnt[3] - b0);
-    chunk_prefix(lists[3] + b0, nb, off, ch, sh, rvf);
+    const long long cb = chunk_prefix(lists[3] + b0, nb, off, ch, sh, rvf, grid);
     const int total = sh.pref[nb - 1];
     for (int kc = blockIdx.x; kc < total; kc += grid) {
       const int item = chunk_item(sh.pref, nb, kc);
@@ -585,8 +599,8 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
       const int v = lists[3][b0 + item];
       const int rv = f.rv(v);
       const long long vb = gload(off + rv), ve = gload(off + rv + 1);
-      const long long beg = vb + (long long)(kc - first) * ch;
-      const long long end = beg + ch < ve ? beg + ch : ve;
+      const long long beg = vb + (long long)(kc - first) * cb;
+      const long long end = beg + cb < ve ? beg + cb : ve;
       typename F::Src s;
       if (!f.src(v, s, 3, b0 + item)) continue;
       push_strided(f, s, v, idx, beg, end, tid, kThreads);

@@ -132,7 +132,14 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   const long long nwords = ((long long)a.n + 31) >> 5;
   const int next = cur + 1;
-  for (long long g = (long long)blockIdx.x * kWarps + warp; g * 32 < nwords; g += (long long)grid * kWarps) {
+  // Tasks of 32 bitmap words: each warp's first is fixed, the rest are taken
+  // from a counter in the phase slot in increasing order, one task ahead, so
+  // that warps whose candidates resolve fast take more tasks.
+  const long long g0 = (long long)grid * kWarps;
+  long long g = (long long)blockIdx.x * kWarps + warp;
+  while (g * 32 < nwords) {
+    unsigned long long gnext = 0;
+    if (lane == 0) gnext = g0 + atomicAdd(&slot.aux0, 1ull);
     const long long wid = g * 32 + lane;
     unsigned vis = wid < nwords ? a.w.bm_vis[wid] : ~0u;
     unsigned cand = wid < nwords ? (~vis & a.w.bm_nz[wid]) : 0u;
@@ -267,11 +274,13 @@ __device__ void bfs_pull(const BfsArgs<OffT>& a, int cur, const uint32_t* fbm,
       if (nb) a.w.bm_vis[wid] = vis | nb;  // owner of the word
     }
     __syncwarp();
+    g = (long long)__shfl_sync(kFull, gnext, 0);
   }
 }
 
 // Pull for the candidates of in-degree >= huge_min queued by bfs_pull: their
-// edges are cut into chunks of huge_min dealt round-robin over all CTAs; a
+// edges are cut into chunks (huge_min edges, fewer when the batch is small)
+// dealt round-robin over all CTAs; a
 // chunk is skipped once another chunk found a frontier in-neighbour.  The
 // words of the bitmaps were finished by their owners in the previous phase,
 // so the few bits set here use atomicOr.
@@ -283,7 +292,7 @@ __device__ void bfs_pull_big(const BfsArgs<OffT>& a, int cur, const uint32_t* fb
   const long long ch = a.k.huge_min;
   for (unsigned b0 = 0; b0 < nbig; b0 += kChunkBatch) {
     const int nb = (int)min((unsigned)kChunkBatch, nbig - b0);
-    chunk_prefix(big + b0, nb, a.ioff, ch, sh);
+    const long long cb = chunk_prefix(big + b0, nb, a.ioff, ch, sh, IdentityVertex{}, grid);
     const int total = sh.pref[nb - 1];
     for (int kc = blockIdx.x; kc < total; kc += grid) {
       const int item = chunk_item(sh.pref, nb, kc);
@@ -295,8 +304,8 @@ __device__ void bfs_pull_big(const BfsArgs<OffT>& a, int cur, const uint32_t* fb
       __syncthreads();
       if (skip) continue;
       const long long vb = gload(a.ioff + v), ve = gload(a.ioff + v + 1);
-      const long long beg = vb + (long long)(kc - first) * ch;
-      const long long end = beg + ch < ve ? beg + ch : ve;
+      const long long beg = vb + (long long)(kc - first) * cb;
+      const long long end = beg + cb < ve ? beg + cb : ve;
       bool hit = false;
 #pragma unroll 4
       for (long long p = beg + threadIdx.x; p < end; p += kThreads) hit |= bm_test(fbm, gload(a.iidx + p));
