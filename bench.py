@@ -8,7 +8,8 @@ step runs, each as one persistent kernel through the C ABI: SSSP from vertex
 0, k-core with k = 16 and PageRank (d = 0.85, FP32, L1 stop 1e-6).
 Other workloads: --workload rmat24-bfs (BFS from vertex 0 on R-MAT scale 24,
 int64 offsets), rmat16-bfs, rmat24-sssp, rmat24-pagerank, rmat24-kcore,
-rmat22-bfs, grid4096-bfs, grid4096-sssp, batch22, serve.
+rmat22-bfs, rmat22-sssp (profiling sizes), grid4096-bfs, grid4096-sssp,
+batch22, serve.
 
 Metric: GTEPS = traversed undirected edges per second (Graph500 counting:
 BFS / SSSP count the edges of the component reached from the source, k-core
@@ -55,6 +56,8 @@ WORKLOADS = {
                          desc="R-MAT scale 24, int64 offsets: k-core k=16"),
     "rmat22-bfs": dict(kind="rmat", scale=22, bits=32, algs=["bfs"],
                        desc="R-MAT scale 22 (n=4,194,304, ef 16), int32 CSR: BFS src 0 (profiling size)"),
+    "rmat22-sssp": dict(kind="rmat", scale=22, bits=32, algs=["sssp"],
+                        desc="R-MAT scale 22 (n=4,194,304, ef 16), int32 CSR, w in [1,64]: SSSP src 0 (profiling size)"),
     "rmat16-bfs": dict(kind="rmat", scale=16, bits=32, algs=["bfs"],
                        desc="R-MAT scale 16 (n=65,536, ef 16), int32 CSR: BFS src 0"),
     "grid4096-bfs": dict(kind="grid", rows=4096, bits=64, algs=["bfs"],

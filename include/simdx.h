@@ -184,7 +184,8 @@ SIMDX_API int simdx_graph_last_status(simdx_graph *g, void *stream);
 
 /* Per-iteration trace of the last run on this graph (synchronises `stream`).
  * Each record is 8 int64: {direction (1 push, 2 pull) | filter << 8
- * (1 online, 2 ballot), active vertices, active edges, level / bucket bound,
+ * (1 online, 2 ballot) | dense << 16 (SSSP: the iteration only lowered
+ * distances, and the next filter scans every vertex), active vertices, active edges, level / bucket bound,
  * %globaltimer ns at the iteration's start and at its end (as seen by CTA 0),
  * and two algorithm-specific words: for BFS the end of the main compute phase
  * and the number of high in-degree pull candidates; for the others the
@@ -207,8 +208,10 @@ SIMDX_API int simdx_bfs(simdx_graph *g, int32_t src, int32_t *levels, simdx_stat
  * if unreachable.  Delta-stepping: vertices whose distance changed and is
  * below the current bucket bound are active (Sec. 3.3); the bucket width is
  * the `delta` knob (a graph starts at 16 x its largest weight).  Push by
- * default; direction = 2 forces pull iterations (symmetric graphs: every
- * vertex takes the min over its frontier in-neighbours, Sec. 5).  Path
+ * default; a push iteration whose task lists hold over 1/16 of the edges
+ * only lowers distances, and the filter after it scans every vertex.
+ * direction = 2 forces pull iterations (symmetric graphs: every vertex
+ * takes the min over its frontier in-neighbours, Sec. 5).  Path
  * lengths must stay below UINT32_MAX.  dist: device uint32[n].  Errors:
  * EINVAL (no weights, src out of range, NULL dist). */
 SIMDX_API int simdx_sssp(simdx_graph *g, int32_t src, uint32_t *dist, simdx_stats *stats,

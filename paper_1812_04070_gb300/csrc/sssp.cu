@@ -13,9 +13,13 @@
 //              edge (the one atomic of the path; Sec. 3.2 gives no
 //              atomic-free scheme for scattered aggregation).  Improved
 //              vertices below T go to the online-filter bins; every improved
-//              vertex gets its pending flag set (a plain byte store).
+//              vertex gets its pending flag set (a plain byte store).  A
+//              dense iteration (task lists holding over 1/16 of the edges)
+//              lands its improvements only, with no flags or records.
 // Task lists : online filter; on overflow the ballot filter rebuilds sorted
-//              lists from {pending and dist < pdist and dist < T}.
+//              lists from {pending and dist < pdist and dist < T}; after a
+//              dense iteration it scans dist < pdist over every vertex and
+//              flags the ones it leaves for a later bucket.
 // Grid class : a very-high-degree task is relaxed by all CTAs; they agree on
 //              one source distance through a per-entry "first reader wins"
 //              word, so pdist records a distance every slice really used.
@@ -58,6 +62,7 @@ struct SsspPush {
   const Work& w;
   const Knobs& k;
   unsigned grid;
+  bool dense = false;  // land improvements only: no pending flags, no records
   unsigned long long nrec = 0, mrec = 0;
   __device__ SsspPush(const SsspArgs<OffT>& a, uint32_t* pd, uint8_t* pe, uint32_t* ax, unsigned long long t,
                       CtaShared& s, unsigned g)
@@ -133,6 +138,14 @@ struct SsspPush {
         cur[q] = dist[x[q]];
       }
     }
+    if (dense) {
+      // fire-and-forget min; the next filter finds the improved vertices by
+      // scanning dist < pdist
+#pragma unroll
+      for (int q = 0; q < kPushBatch; ++q)
+        if (nd[q] < cur[q]) atomicMin(&dist[x[q]], (uint32_t)nd[q]);
+      return;
+    }
     uint32_t old[kPushBatch];
 #pragma unroll
     for (int q = 0; q < kPushBatch; ++q) {
@@ -199,6 +212,11 @@ struct SsspPull {
   }
 };
 
+// A push iteration whose task lists hold more than 1/kDenseDiv of all edges
+// is dense: most of its improvements would be recorded, and one scan of
+// dist < pdist over all vertices costs less than recording them.
+constexpr unsigned long long kDenseDiv = 16;
+
 template <class OffT, bool V, bool PULL>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
@@ -262,33 +280,51 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
   int it = 0, ballot_it = 0, online_it = 0, pull_it = 0;
   long long evisit = 0, fsum = 0;
   int filt = 1;
+  // Dense push iterations (frontier edges above 1/kDenseDiv of all edges)
+  // only land their improvements; the filter after one scans every vertex.
+  const unsigned long long m_all =
+      (unsigned long long)(gload(a.off + nreal) - gload(a.off)) * (unsigned long long)(V ? a.ninst : 1);
+  unsigned long long mf = 0;  // out-edges of the current task lists
+  bool scan_all = false;
 
   while (true) {
     const unsigned long long t_it = globaltimer();
     unsigned total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     filt = 1;
-    if (!lists_ok || k.filter == 2) {
-      // ballot filter: near active vertices from the metadata
+    if (!lists_ok || k.filter == 2 || scan_all) {
+      // ballot filter: near active vertices from the metadata (pending
+      // flags; after a dense iteration, every vertex)
       clear_next_slot(s, sh);
       PhaseSlot& slot = s->slot[slot_of(sh.phase)];
       const unsigned long long TT = T;
       uint32_t* dist = a.dist;
+      const bool sa = scan_all;
       auto pred = [=](int v) {
-        if (!pend[v]) return false;
+        if (!sa && !pend[v]) return false;
         const uint32_t d = dist[v];
-        return d < pdist[v] && (unsigned long long)d < TT;
+        if (d >= pdist[v]) return false;
+        if ((unsigned long long)d < TT) return true;
+        if (sa) pend[v] = 1;  // improved by the dense iteration, left for a later bucket
+        return false;
       };
-      auto deg = [off = a.off, realv](int x) {
+      unsigned long long msum = 0;
+      auto deg = [off = a.off, realv, &msum](int x) {
         const int v = realv(x);
-        return (long long)gload(off + v + 1) - (long long)gload(off + v);
+        const long long d = (long long)gload(off + v + 1) - (long long)gload(off + v);
+        msum += (unsigned long long)d;
+        return d;
       };
       auto visit = [=](int v) { pend[v] = 0; };
       ballot_filter(n, pred, deg, visit, sh, a.w, k, grid, lbuf, slot);
+      const unsigned long long tms = cta_sum_u64(msum, sh);
+      if (threadIdx.x == 0 && tms) atomicAdd(&slot.mact, tms);
       if (!grid_sync(s, grid, sh, k)) return;
       const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
       for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
       total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+      mf = p.mact;
       lists_ok = true;
+      scan_all = false;
       filt = 2;
     }
     if (total == 0) {
@@ -313,12 +349,17 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
           if (d < mymin) mymin = d;
           return (unsigned long long)d < TT;
         };
-        auto deg = [off = a.off, realv](int x) {
-        const int v = realv(x);
-        return (long long)gload(off + v + 1) - (long long)gload(off + v);
-      };
+        unsigned long long msum = 0;
+        auto deg = [off = a.off, realv, &msum](int x) {
+          const int v = realv(x);
+          const long long d = (long long)gload(off + v + 1) - (long long)gload(off + v);
+          msum += (unsigned long long)d;
+          return d;
+        };
         auto visit = [=](int v) { pend[v] = 0; };
         ballot_filter(n, pred, deg, visit, sh, a.w, k, grid, lbuf, slot);
+        const unsigned long long tms = cta_sum_u64(msum, sh);
+        if (threadIdx.x == 0 && tms) atomicAdd(&slot.mact, tms);
         unsigned long long c_cnt = cta_sum_u64(mycnt, sh);
         // CTA min
         {
@@ -343,6 +384,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
         const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
         for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
         total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+        mf = p.mact;
         const unsigned long long pending = p.aux1;
         if (pending == 0) {
           done = true;
@@ -424,6 +466,8 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       __syncthreads();
       PhaseSlot& slot = s->slot[slot_of(sh.phase)];
       SsspPush<OffT, V> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
+      f.dense = mf * kDenseDiv > m_all;
+      scan_all = f.dense;
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
       push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
@@ -438,12 +482,13 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     }
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
-    trace_put(a.w, it, (pull ? 2 : 1) | (filt << 8), (long long)total, 0,
+    trace_put(a.w, it, (pull ? 2 : 1) | (filt << 8) | (scan_all ? 1 << 16 : 0), (long long)total, 0,
               (long long)(T == kInfT ? -1 : (long long)T), t_it);
     trace_classes(a.w, it, p);
     fsum += total;
     ++it;
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+    mf = p.mact;
     lists_ok = p.overflow == 0;
     lbuf ^= 1;
   }

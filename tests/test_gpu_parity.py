@@ -65,6 +65,27 @@ def test_sssp_delta(delta):
     G.close()
 
 
+@pytest.mark.parametrize("delta", [0, 1, 64, 1024])
+def test_sssp_dense_iterations(delta):
+    """From R-MAT's hub the second iteration holds most of the edges: it is
+    dense (lowers distances with no pending flags or records), and the scan
+    after it must find every improved vertex, flagging those a narrow bucket
+    leaves for later."""
+    g = gg.rmat(14)
+    w = gg.weights(g, 9, 1, 64)
+    G = make(g, w, delta=delta)
+    d = G.sssp(0).cpu().numpy().view(np.uint32)
+    tr = G.trace()
+    assert any((int(r[0]) >> 16) & 1 for r in tr), "no dense iteration"
+    assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, 0))
+    srcs = [0, 1, 2, 3]
+    db = G.sssp_batch(srcs).cpu().numpy().view(np.uint32)
+    assert any((int(r[0]) >> 16) & 1 for r in G.trace()), "no dense iteration in the batch"
+    for i, s in enumerate(srcs):
+        assert np.array_equal(db[i], oracle.sssp(g.offsets, g.indices, w, s)), s
+    G.close()
+
+
 @pytest.mark.parametrize("mode", ["default", "push", "pull", "ballot", "overflow", "all_classes",
                                   "all_classes_pull", "one_cta_per_sm"])
 @pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
