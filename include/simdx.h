@@ -33,7 +33,7 @@
  *     batch / server entry points that say so; the algorithm calls allocate
  *     nothing.
  *   - CUDA graphs: simdx_bfs, simdx_sssp, simdx_kcore, simdx_pagerank,
- *     simdx_bfs_batch, simdx_sssp_batch (up to 64 sources) and
+ *     simdx_bfs_batch, simdx_sssp_batch (groups of up to 64 sources) and
  *     simdx_bfs_multi can be captured into a CUDA graph (stream capture on
  *     `stream`) and replayed, each launch a cooperative kernel node, when
  *     (a) stats is NULL (a captured call with stats returns EUNSUPPORTED),
@@ -113,7 +113,8 @@ typedef struct {
     int32_t med_max;         /* degree < med_max   -> warp list   [512]  (Sec. 4 finds this
                                 separator insensitive in [128, 2048]) */
     int32_t huge_min;        /* degree >= huge_min -> cut into chunks of huge_min edges dealt
-                                round-robin over all CTAs; CTA list below [4096] */
+                                round-robin over all CTAs (push: smaller chunks when the
+                                batch would not fill the grid); CTA list below [4096] */
     int32_t bin_per_thread;  /* online-filter overflow threshold per thread [64] (Sec. 4
                                 "Overflow thresholds"); 0 forces the ballot filter */
     int32_t direction;       /* 0 auto, 1 push only, 2 pull only [0] (Sec. 5); SSSP's
@@ -130,7 +131,9 @@ typedef struct {
     int32_t debug_skip_cta;  /* test knob: this CTA skips barrier arrival number
                                 debug_skip_phase (-1 = off) [-1] */
     int32_t debug_skip_phase;
-    int32_t reserved[8];
+    int32_t batch_group;     /* simdx_sssp_batch: copies per persistent launch; 0 = as many
+                                as keep one launch's distances within 128 MB [0] */
+    int32_t reserved[7];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;
@@ -190,8 +193,10 @@ SIMDX_API int simdx_graph_last_status(simdx_graph *g, void *stream);
  * and two algorithm-specific words: for BFS the end of the main compute phase
  * and the number of high in-degree pull candidates; for the others the
  * slowest CTA's time in degree classes (ns, 32 bits each) as (3 << 32 | 2)
- * and (1 << 32 | 0)}.  Writes up to `cap` records to host memory `rec` and returns the
- * number of iterations of the run in *count. */
+ * and (1 << 32 | 0)}.  A batched SSSP run as several launches (see
+ * batch_group) numbers its records across them.  Writes up to `cap` records
+ * to host memory `rec` and returns the number of iterations of the run in
+ * *count. */
 SIMDX_API int simdx_graph_trace(simdx_graph *g, void *stream, int64_t *rec, int64_t cap,
                       int64_t *count);
 
@@ -254,16 +259,20 @@ SIMDX_API int simdx_pagerank(simdx_graph *g, float damping, float l1_tol, int32_
 SIMDX_API int simdx_bfs_batch(simdx_graph *g, const int32_t *srcs, int32_t k, int32_t *levels,
                               simdx_stats *stats, void *stream);
 
-/* Batched SSSP (growth direction (a)): k sources in one persistent launch.
- * The k queries run on k virtual copies of the graph (state id inst * n + v,
- * one CSR) with delta-stepping buckets shared by all copies, so every
- * iteration processes all queries' frontiers together.  Up to 64 sources
- * travel as kernel parameters (the call can then be captured into a CUDA
- * graph); more are copied to the device first.  srcs: host int32[k];
- * dist: device uint32[k*n], row i = distances from srcs[i], identical to k
- * simdx_sssp calls.  The first call (or a larger k than any before)
- * allocates the batch state (about 45 bytes per vertex per query); later
- * calls with the same or a smaller k reuse it.  Needs k * n < 2^31.  Errors: EINVAL, ENOMEM. */
+/* Batched SSSP (growth direction (a)): k sources, one persistent launch per
+ * group of copies.  The queries of a group run on virtual copies of the
+ * graph (state id inst * n + v, one CSR) with delta-stepping buckets shared
+ * by the group, so every iteration processes the group's frontiers
+ * together.  Groups are of equal size, as large as keeps a group's
+ * distances within 128 MB (all k for graphs up to 32M / k vertices), or of
+ * at most the batch_group knob, and run one after another on `stream`.  Up
+ * to 64 sources per group travel as kernel parameters (the call can then be
+ * captured into a CUDA graph); larger groups copy all k to the device first.
+ * srcs: host int32[k]; dist: device uint32[k*n], row i = distances from
+ * srcs[i], identical to k simdx_sssp calls.  The first call (or a larger
+ * group than any before) allocates the batch state (about 45 bytes per
+ * vertex per copy of a group); later calls reuse it.  Needs k * n < 2^31.
+ * Errors: EINVAL, ENOMEM. */
 SIMDX_API int simdx_sssp_batch(simdx_graph *g, const int32_t *srcs, int32_t k, uint32_t *dist,
                                simdx_stats *stats, void *stream);
 

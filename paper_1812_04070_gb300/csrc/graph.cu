@@ -524,7 +524,7 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
   if (cfg->small_max < 1 || cfg->med_max < cfg->small_max || cfg->huge_min < cfg->med_max ||
       cfg->bin_per_thread < 0 || cfg->bin_per_thread > 4096 || cfg->direction < 0 ||
       cfg->direction > 2 || (cfg->filter != 0 && cfg->filter != 2) || !(cfg->alpha > 0.f) ||
-      !(cfg->beta > 0.f) || !(cfg->kcore_alpha > 0.f) || cfg->ctas_per_sm < 0)
+      !(cfg->beta > 0.f) || !(cfg->kcore_alpha > 0.f) || cfg->ctas_per_sm < 0 || cfg->batch_group < 0)
     return SIMDX_EINVAL;
   bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
                     cfg->huge_min != g->cfg.huge_min;

@@ -54,7 +54,7 @@ class simdx_config(ctypes.Structure):
                 ("kcore_alpha", ctypes.c_float), ("delta", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_int32), ("barrier_timeout_ms", ctypes.c_int32),
                 ("debug_skip_cta", ctypes.c_int32), ("debug_skip_phase", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("batch_group", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 _LIB = None

@@ -73,8 +73,8 @@ def test_bfs_multigraph_pack(mode):
 
 @pytest.mark.parametrize("k", [1, 33, 64, 70])
 def test_sssp_batch_sizes(k):
-    """k <= 32 uses 32 state slots per vertex, 33..64 use 64 (two instances per
-    lane), more than 64 runs one launch per 64 sources."""
+    """Up to 64 sources travel as a kernel parameter, more through device
+    memory."""
     g = gg.rmat(11)
     w = gg.weights(g, 99, 1, 64)
     srcs = np.resize(gg.pick_sources(g, 50, seed=k), k)
@@ -82,6 +82,30 @@ def test_sssp_batch_sizes(k):
     out = G.sssp_batch([int(s) for s in srcs]).cpu().numpy().view(np.uint32)
     for i, s in enumerate(srcs):
         assert np.array_equal(out[i], oracle.sssp(g.offsets, g.indices, w, int(s))), (k, i)
+    G.close()
+
+
+@pytest.mark.parametrize("k,group", [(10, 3), (7, 1), (140, 70)])
+def test_sssp_batch_groups(k, group):
+    """A batch runs its copies in groups, one persistent launch per group (the
+    batch_group knob forces the split that a large graph gets by size); the
+    launches share one stats record, and groups of more than 64 read their
+    sources from device memory at the group's offset."""
+    import torch
+    from paper_1812_04070_gb300 import simdx_stats
+    g = gg.rmat(11)
+    w = gg.weights(g, 98, 1, 64)
+    srcs = [int(s) for s in np.resize(gg.pick_sources(g, 50, seed=k), k)]
+    G = make(g, w, bits=64, batch_group=group)
+    st = simdx_stats()
+    out = G.sssp_batch(srcs, stats=st).cpu().numpy().view(np.uint32)
+    torch.cuda.synchronize()
+    for i, s in enumerate(srcs):
+        assert np.array_equal(out[i], oracle.sssp(g.offsets, g.indices, w, s)), (k, group, i)
+    assert st.status == 0 and G.last_status() == 0
+    assert st.iterations >= -(-k // group)  # every group ran at least one iteration
+    tr = G.trace()  # the group launches number their records on
+    assert tr.shape[0] == st.iterations and (tr[:, 4] > 0).all() and (tr[:, 5] >= tr[:, 4]).all()
     G.close()
 
 

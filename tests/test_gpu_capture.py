@@ -24,7 +24,7 @@ def test_capture_and_replay():
     import torch
     g = gg.rmat(12)
     w = gg.weights(g, 21, 1, 64)
-    G = make(g, w, bits=32)
+    G = make(g, w, bits=32, batch_group=16)  # the SSSP batch runs as three launches
     n = g.n
     srcs = [int(x) for x in gg.pick_sources(g, 40, seed=5)]
     graphs, gsrc = gg.multigraph_batch(count=12, n_lo=50, n_hi=2000, seed=0xBA7C4)
