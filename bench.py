@@ -8,6 +8,7 @@ step runs, each as one persistent kernel through the C ABI: SSSP from vertex
 0, k-core with k = 16 and PageRank (d = 0.85, FP32, L1 stop 1e-6).
 Other workloads: --workload rmat24-bfs (BFS from vertex 0 on R-MAT scale 24,
 int64 offsets), rmat16-bfs, rmat24-sssp, rmat24-pagerank, rmat24-kcore,
+rmat20-coreness, rmat24-coreness (k-core decomposition),
 rmat22-bfs, rmat22-sssp (profiling sizes), grid4096-bfs, grid4096-sssp,
 batch22, serve.
 
@@ -54,6 +55,10 @@ WORKLOADS = {
                             desc="R-MAT scale 24, int64 offsets: PageRank d=0.85 tol 1e-6"),
     "rmat24-kcore": dict(kind="rmat", scale=24, bits=64, algs=["kcore"],
                          desc="R-MAT scale 24, int64 offsets: k-core k=16"),
+    "rmat20-coreness": dict(kind="rmat", scale=20, bits=32, algs=["coreness"],
+                            desc="R-MAT scale 20, int32 CSR: k-core decomposition (coreness of every vertex)"),
+    "rmat24-coreness": dict(kind="rmat", scale=24, bits=64, algs=["coreness"],
+                            desc="R-MAT scale 24, int64 offsets: k-core decomposition (coreness of every vertex)"),
     "rmat22-bfs": dict(kind="rmat", scale=22, bits=32, algs=["bfs"],
                        desc="R-MAT scale 22 (n=4,194,304, ef 16), int32 CSR: BFS src 0 (profiling size)"),
     "rmat22-sssp": dict(kind="rmat", scale=22, bits=32, algs=["sssp"],
@@ -194,12 +199,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_FILES = {"coreness_kernel": "kcore.cu"}  # kernels not in <algorithm>.cu
+
+
 def kernel_source_hash(kernel: str) -> str:
     """Hash of the sources a kernel is built from: its own file
     (<algorithm>.cu for <algorithm>_kernel) and the shared device headers."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1812_04070_gb300", "csrc")
-    for fn in [kernel.replace("_kernel", "") + ".cu", "acc_device.cuh", "simdx_internal.h"]:
+    own = KERNEL_FILES.get(kernel, kernel.replace("_kernel", "") + ".cu")
+    for fn in [own, "acc_device.cuh", "simdx_internal.h"]:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -240,6 +249,8 @@ def algorithmic(alg, g, bits, out, iters):
         return e_c // 2, 8 * e_c + (2 * so + 4 + 8) * n_c
     if alg == "kcore":
         return e // 2, 4 * e + (2 * so + 1) * n
+    if alg == "coreness":
+        return e // 2, 4 * e + (2 * so + 8) * n
     if alg == "pagerank":
         return (e // 2) * iters, (4 * e + (2 * so + 12) * n) * iters
     raise ValueError(alg)
@@ -266,7 +277,7 @@ def run_simdx(args, rank, world, local):
     algs = wl["algs"]
     graphs = {a: G for a in algs}
     tuned, tuned_full, tune_s = {}, {}, 0.0
-    if args.autotune:
+    if args.autotune and "coreness" not in algs:
         from paper_1812_04070_gb300 import simdx
         code = {"bfs": simdx.ALGO_BFS, "sssp": simdx.ALGO_SSSP, "kcore": simdx.ALGO_KCORE,
                 "pagerank": simdx.ALGO_PAGERANK}
@@ -285,6 +296,7 @@ def run_simdx(args, rank, world, local):
         "sssp": torch.empty(g.n, dtype=torch.int32, device=dev),
         "kcore": (torch.empty(g.n, dtype=torch.uint8, device=dev), torch.empty(g.n, dtype=torch.int32, device=dev)),
         "pagerank": torch.empty(g.n, dtype=torch.float32, device=dev),
+        "coreness": torch.empty(g.n, dtype=torch.int32, device=dev),
     }
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -296,6 +308,8 @@ def run_simdx(args, rank, world, local):
             Ga.sssp(0, out=outs["sssp"], stats=st)
         elif alg == "kcore":
             Ga.kcore(16, out=outs["kcore"][0], resid=outs["kcore"][1], stats=st)
+        elif alg == "coreness":
+            Ga.coreness(out=outs["coreness"], stats=st)
         else:
             Ga.pagerank(0.85, 1e-6, 1000, out=outs["pagerank"], stats=st)
 
@@ -334,7 +348,7 @@ def run_simdx(args, rank, world, local):
     work = {}
     for a in algs:
         o = outs[a]
-        if a == "kcore":
+        if a in ("kcore", "coreness"):
             host = None
         elif a == "sssp":
             host = o.cpu().numpy().view(np.uint32)
@@ -410,11 +424,12 @@ def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
                 "sssp": torch.empty(g.n, dtype=torch.int32).pin_memory(),
                 "kcore": (torch.empty(g.n, dtype=torch.uint8).pin_memory(),
                           torch.empty(g.n, dtype=torch.int32).pin_memory()),
-                "pagerank": torch.empty(g.n, dtype=torch.float32).pin_memory()}
+                "pagerank": torch.empty(g.n, dtype=torch.float32).pin_memory(),
+                "coreness": torch.empty(g.n, dtype=torch.int32).pin_memory()}
     h2d = p_off.numel() * p_off.element_size() + p_idx.numel() * 4 + (p_w.numel() * 4 if "sssp" in algs else 0)
     d2h = 0
     for a in algs:
-        d2h += g.n * (4 if a in ("bfs", "sssp", "pagerank") else 5)
+        d2h += g.n * (4 if a in ("bfs", "sssp", "pagerank", "coreness") else 5)
 
     def one():
         G = Graph(p_off.numpy(), p_idx.numpy(), weights=p_w.numpy().view(np.uint32) if "sssp" in algs else None)
@@ -429,6 +444,8 @@ def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
                 ic, rs = G.kcore(16)
                 host_out[a][0].copy_(ic, non_blocking=True)
                 host_out[a][1].copy_(rs, non_blocking=True)
+            elif a == "coreness":
+                host_out[a].copy_(G.coreness(), non_blocking=True)
             else:
                 host_out[a].copy_(G.pagerank(0.85, 1e-6, 1000), non_blocking=True)
         torch.cuda.synchronize()
@@ -615,6 +632,10 @@ def cpu_baseline(workload, g, w, budget_s=15.0):
             oracle.kcore(g.offsets, g.indices, 16)
             m = g.e // 2
             parts.append("kcore full")
+        elif a == "coreness":
+            oracle.coreness(g.offsets, g.indices)
+            m = g.e // 2
+            parts.append("coreness full")
         else:
             iters = 5
             oracle.pagerank(g.offsets, g.indices, fixed_iter=iters)

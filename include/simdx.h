@@ -232,6 +232,20 @@ SIMDX_API int simdx_sssp(simdx_graph *g, int32_t src, uint32_t *dist, simdx_stat
 SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
                 uint32_t *residual_deg, simdx_stats *stats, void *stream);
 
+/* k-core decomposition (Sec. 6 "k-Core", run for every k): coreness[v] =
+ * the largest k such that v belongs to the k-core (0 for isolated
+ * vertices), so simdx_kcore(k) keeps exactly the vertices with coreness >=
+ * k.  One persistent launch peels level after level: at level K every
+ * remaining vertex of residual degree <= K is deleted with coreness K, its
+ * push decrements its remaining neighbours, and the decrement that takes a
+ * neighbour to K deletes it at the same level; a scan of the remaining
+ * vertices opens the next level (K + 1, or the smallest remaining degree).
+ * Trace records carry K as their level word.  coreness: device uint32[n].
+ * Needs a symmetric graph.  Errors: EINVAL (NULL coreness, directed
+ * graph). */
+SIMDX_API int simdx_kcore_decompose(simdx_graph *g, uint32_t *coreness, simdx_stats *stats,
+                                    void *stream);
+
 /* PageRank (Sec. 6 "PageRank"; aggregation combine = sum, pull):
  *   x_0 = 1/n;  x_{t+1}(v) = (1-d)/n + d*(sum_{u in N_in(v)} x_t(u)/outdeg(u)
  *                                         + D_t/n),

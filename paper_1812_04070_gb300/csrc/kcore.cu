@@ -274,6 +274,252 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// k-core decomposition: the coreness of every vertex, i.e. the largest k
+// whose k-core holds it.  Sec. 6 defines the k-core by repeatedly deleting
+// the vertices of degree < k; running that deletion for k = 1, 2, ... on the
+// shrinking graph deletes at level K exactly the vertices of coreness K.  At
+// level K every alive vertex of residual degree <= K is deleted (core = K);
+// its push decrements its alive neighbours (warp-combined atomicSub, as in
+// the fixed-k push), and the one decrement that takes a neighbour from > K
+// to <= K deletes and records it, so lists carry no duplicates.  When a
+// level's lists run dry, one scan of the alive vertices (ballot filter)
+// opens level K + 1, or, if no alive vertex has degree K + 1, a second scan
+// jumps to the smallest alive degree.  All levels run in one persistent
+// launch.
+template <class OffT>
+struct CoreArgs {
+  int n;
+  const OffT* off;
+  const int32_t* idx;
+  uint32_t* core;
+  Work w;
+  Knobs k;
+};
+
+template <class OffT>
+struct CorePush {
+  struct Src {};
+  int32_t* removed_at;
+  uint32_t* cnt;
+  uint32_t* core;
+  const OffT* off;
+  unsigned K;
+  int it;
+  CtaShared& sh;
+  const Work& w;
+  const Knobs& k;
+  unsigned grid;
+  unsigned long long nrec = 0, mrec = 0;
+  __device__ CorePush(int32_t* r, uint32_t* c, uint32_t* co, const OffT* o, unsigned kv, int i, CtaShared& s,
+                      const Work& ww, const Knobs& kn, unsigned g)
+      : removed_at(r), cnt(c), core(co), off(o), K(kv), it(i), sh(s), w(ww), k(kn), grid(g) {}
+  __device__ __forceinline__ bool src(int, Src&, int, unsigned) { return true; }
+  __device__ __forceinline__ int rv(int v) const { return v; }
+  static __device__ __forceinline__ Src shfl(const Src&, int) { return Src{}; }
+  __device__ __forceinline__ void edges(const Src (&)[kPushBatch], const int (&)[kPushBatch],
+                                        const int (&u)[kPushBatch], const long long (&)[kPushBatch],
+                                        unsigned ok) {
+    bool want[kPushBatch];
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      want[q] = false;
+      if ((ok >> q) & 1u) want[q] = removed_at[u[q]] == INT_MAX;
+    }
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q)
+      if (want[q]) want[q] = cnt[u[q]] > K;  // already at or below the level: deleted at it
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q) {
+      const unsigned mask = __activemask();
+      const int key = want[q] ? u[q] : (int)(0x80000000u | lane_id());
+      const unsigned peers = __match_any_sync(mask, key);
+      if (!want[q] || (int)lane_id() != __ffs(peers) - 1) continue;
+      const unsigned c = (unsigned)__popc(peers);
+      const unsigned old = atomicSub(&cnt[u[q]], c);
+      if (old > K && old - c <= K) {
+        removed_at[u[q]] = it;
+        core[u[q]] = K;
+        long long d = (long long)gload(off + u[q] + 1) - (long long)gload(off + u[q]);
+        ++nrec;
+        mrec += (unsigned long long)d;
+        online_record(u[q], degree_class(d, k), sh, w, k, grid);
+      }
+    }
+  }
+};
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a) {
+  __shared__ CtaShared sh;
+  const unsigned grid = gridDim.x;
+  Sync* s = a.w.sync;
+  const Knobs& k = a.k;
+  const int n = a.n;
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long gthreads = (long long)grid * kThreads;
+  int32_t* removed_at = reinterpret_cast<int32_t*>(a.w.state);  // push iteration of the deletion
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(removed_at + n);   // residual degree
+  const OffT* off = a.off;
+  auto deg = [off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+  for (long long v = gtid; v < n; v += gthreads) {
+    cnt[v] = (uint32_t)deg((int)v);
+    removed_at[v] = INT_MAX;
+  }
+  clear_next_slot(s, sh);
+  if (!grid_sync(s, grid, sh, k)) return;
+
+  int lbuf = 0;
+  unsigned cnt_l[kClasses] = {0u, 0u, 0u, 0u};
+  bool lists_ok = true;
+  unsigned long long pending = 0;  // vertices deleted by the last push, still to push
+  long long K = -1;                // current level
+  int it = 0, ballot_it = 0, online_it = 0;
+  long long evisit = 0, fsum = 0;
+  while (true) {
+    const unsigned long long t_it = globaltimer();
+    int filt = 1;
+    if (pending == 0) {
+      // level advance: scan the alive vertices, delete those at the guessed
+      // level, count the alive ones and find their smallest degree
+      bool done = false;
+      unsigned long long Kt = (unsigned long long)(K + 1);
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        clear_next_slot(s, sh);
+        PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+        unsigned long long nalive = 0, mymin = ~0ull;
+        const unsigned kt = (unsigned)Kt;
+        const int prev = it - 1;  // as if deleted by the push before the next one
+        uint32_t* core = a.core;
+        auto pred = [&](int v) {
+          if (removed_at[v] != INT_MAX) return false;
+          const unsigned c = cnt[v];
+          ++nalive;
+          if (c < mymin) mymin = c;
+          if (c > kt) return false;
+          removed_at[v] = prev;
+          core[v] = kt;
+          return true;
+        };
+        auto none = [](int) {};
+        ballot_filter(n, pred, deg, none, sh, a.w, k, grid, lbuf, slot);
+        const unsigned long long ta = cta_sum_u64(nalive, sh);
+        {
+          unsigned long long m = mymin;
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(kFull, m, o);
+            m = y < m ? y : m;
+          }
+          __syncthreads();
+          if (lane_id() == 0) sh.red64[threadIdx.x >> 5] = m;
+          __syncthreads();
+          if (threadIdx.x == 0 && ta) {
+            unsigned long long t = ~0ull;
+            for (int q = 0; q < kWarps; ++q) t = sh.red64[q] < t ? sh.red64[q] : t;
+            atomicAdd(&slot.aux1, ta);
+            atomicMax(&slot.aux2, ~t);  // slots start at 0: keep the min inverted
+          }
+        }
+        if (!grid_sync(s, grid, sh, k)) return;
+        const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+        for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
+        const unsigned total = cnt_l[0] + cnt_l[1] + cnt_l[2] + cnt_l[3];
+        if (p.aux1 == 0) {
+          done = true;
+          break;
+        }
+        if (total > 0) {
+          K = (long long)Kt;
+          pending = total;
+          break;
+        }
+        Kt = ~p.aux2;  // no alive vertex has degree K + 1: jump to the smallest
+      }
+      if (done) break;
+      ++ballot_it;
+      filt = 2;
+      lists_ok = true;
+    } else if (!lists_ok || k.filter == 2) {
+      // the online bins overflowed: list the last push's deletions again
+      clear_next_slot(s, sh);
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      const int prev = it - 1;
+      auto pred = [=](int v) { return removed_at[v] == prev; };
+      auto none = [](int) {};
+      ballot_filter(n, pred, deg, none, sh, a.w, k, grid, lbuf, slot);
+      if (!grid_sync(s, grid, sh, k)) return;
+      const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+      for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
+      ++ballot_it;
+      filt = 2;
+    } else {
+      ++online_it;
+    }
+    clear_next_slot(s, sh);
+    online_reset(sh);
+    __syncthreads();
+    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+    const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                      a.w.list[lbuf][3]};
+    CorePush<OffT> f(removed_at, cnt, a.core, a.off, (unsigned)K, it, sh, a.w, k, grid);
+    push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit, &slot);
+    online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
+    const unsigned long long tn = cta_sum_u64(f.nrec, sh), tm = cta_sum_u64(f.mrec, sh);
+    if (threadIdx.x == 0 && tn) {
+      atomicAdd(&slot.nact, tn);
+      atomicAdd(&slot.mact, tm);
+    }
+    if (!grid_sync(s, grid, sh, k)) return;
+    const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+    trace_put(a.w, it, 1 | (filt << 8), (long long)(cnt_l[0] + cnt_l[1] + cnt_l[2] + cnt_l[3]),
+              (long long)p.mact, K, t_it);
+    trace_classes(a.w, it, p);
+    fsum += (long long)(cnt_l[0] + cnt_l[1] + cnt_l[2] + cnt_l[3]);
+    for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
+    lists_ok = p.overflow == 0;
+    pending = p.nact;
+    lbuf ^= 1;
+    ++it;
+  }
+  unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+  if (!grid_sync(s, grid, sh, k)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats& st = *a.w.stats;
+    st.status = 0;
+    st.iterations = it;
+    st.push_iters = it;
+    st.pull_iters = 0;
+    st.ballot_iters = ballot_it;
+    st.online_iters = online_it;
+    st.phases = (int)sh.phase;
+    st.grid = (int)grid;
+    st.edges_visited = (long long)s->evisit;
+    st.frontier_sum = fsum;
+    st.last_l1 = 0.0;
+  }
+}
+
+template <class OffT>
+static int run_coreness(simdx_graph* g, uint32_t* core, simdx_stats* stats, cudaStream_t st) {
+  CoreArgs<OffT> a{};
+  a.n = (int)g->n;
+  a.off = (const OffT*)g->off;
+  a.idx = g->idx;
+  a.core = core;
+  a.w = make_work(g);
+  a.k = make_knobs(g);
+  const void* kern = (const void*)coreness_kernel<OffT>;
+  int grid = grid_for(g, kern);
+  int rc = prepare_launch(g, st);
+  if (rc) return rc;
+  void* args[] = {&a};
+  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st);
+}
+
 const void* kcore_kernel_ptr(int off_bits) {
   return off_bits == 32 ? (const void*)kcore_kernel<int32_t> : (const void*)kcore_kernel<long long>;
 }
@@ -314,4 +560,16 @@ extern "C" int simdx_kcore(simdx_graph* g, uint32_t k, uint8_t* in_core, uint32_
   }
   return g->off_bits == 32 ? run_kcore<int32_t>(g, k, in_core, residual_deg, stats, st)
                            : run_kcore<long long>(g, k, in_core, residual_deg, stats, st);
+}
+
+extern "C" int simdx_kcore_decompose(simdx_graph* g, uint32_t* coreness, simdx_stats* stats, void* stream) {
+  if (!g || !coreness || !g->symmetric) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g->n == 0) {
+    int rc = prepare_launch(g, st);
+    return rc ? rc : finish_launch(g, stats, st);
+  }
+  return g->off_bits == 32 ? run_coreness<int32_t>(g, coreness, stats, st)
+                           : run_coreness<long long>(g, coreness, stats, st);
 }

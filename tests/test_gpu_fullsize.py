@@ -47,6 +47,7 @@ def test_rmat20_sssp_kcore_pagerank():
         ei, er = oracle.kcore(g.offsets, g.indices, k)
         assert np.array_equal(inc.cpu().numpy(), ei)
         assert np.array_equal(resid.cpu().numpy(), er)
+    assert np.array_equal(G.coreness().cpu().numpy().view(np.uint32), oracle.coreness(g.offsets, g.indices))
     rel, t, t_stop, st = check_pagerank(G, g)
     assert st.status == 0
     assert rel <= 1e-6, rel
