@@ -302,20 +302,32 @@ __device__ __forceinline__ void online_flush(CtaShared& sh, const Work& w, const
 }
 
 // --------------------------------------------------------- ballot filter
-// Scan vertices [0, n) in chunks of kBallotChunk; pred(v) says whether v is
-// active and deg(v) its degree for the class.  Emits, per class, the active
-// vertices of each chunk in increasing order (sorted, unique) into
-// w.list[nbuf][c], reserving each chunk's range with one atomic per class.
-// `visit(v)` is called once for every selected vertex (by the thread that
-// writes it) so callers can fuse per-vertex side effects.
+// 32-vertex steps a warp takes per chunk (at most 32): as many as spread the
+// n vertices over the whole grid, so that a small scan is one or two steps
+// on every CTA instead of 32 dependent steps on a few.
+__device__ __forceinline__ int ballot_steps(long long n, unsigned grid) {
+  const long long per = (long long)grid * kThreads;
+  const long long j = (n + per - 1) / per;
+  return j < 1 ? 1 : (j > 32 ? 32 : (int)j);
+}
+
+// Scan vertices [0, n) in chunks of kThreads x ballot_steps (at most
+// kBallotChunk); pred(v) says whether v is active and deg(v) its degree for
+// the class.  Emits, per class, the active vertices of each chunk in
+// increasing order (sorted, unique) into w.list[nbuf][c], reserving each
+// chunk's range with one atomic per class.  `visit(v)` is called once for
+// every selected vertex (by the thread that writes it) so callers can fuse
+// per-vertex side effects.
 template <class Pred, class Deg, class Visit>
 __device__ void ballot_filter(int n, Pred pred, Deg deg, Visit visit, CtaShared& sh, const Work& w,
                               const Knobs& k, unsigned grid, int nbuf, PhaseSlot& slot) {
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  for (long long chunk = blockIdx.x; chunk * kBallotChunk < n; chunk += grid) {
-    const long long wbase = chunk * kBallotChunk + (long long)warp * 1024;
+  const int J = ballot_steps(n, grid);
+  const long long csz = (long long)kThreads * J;
+  for (long long chunk = blockIdx.x; chunk * csz < n; chunk += grid) {
+    const long long wbase = chunk * csz + (long long)warp * 32 * J;
     unsigned my[kClasses] = {0u, 0u, 0u, 0u};
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < J; ++j) {
       long long v = wbase + j * 32 + lane;
       bool act = false;
       int cls = 0;

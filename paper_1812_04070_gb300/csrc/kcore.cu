@@ -349,9 +349,103 @@ struct CorePush {
   }
 };
 
+// One level scan.  Walks `count` entries of the domain (vertex i, or dom[i]
+// once the remaining vertices are listed) and sorts each into: gone (deleted
+// before), deleted now (residual degree <= kt: core = kt, removed_at = prev;
+// listed by degree class unless it has no edges to push), or kept (appended
+// to `keep`, the next scan's domain).  Counts the remaining vertices,
+// the deleted ones (slot.nact) and the smallest remaining degree.  Each CTA
+// reserves its chunk's entries with one atomic per category, as the ballot
+// filter does.
+constexpr int kCoreCats = kClasses + 1;  // the degree classes, then "kept"
+
+template <class OffT>
+__device__ void core_scan(long long count, const int32_t* dom, int32_t* keep, unsigned kt, int prev,
+                          int32_t* removed_at, const uint32_t* cnt, uint32_t* core, const OffT* off,
+                          const Work& w, const Knobs& k, unsigned grid, int nbuf, PhaseSlot& slot,
+                          int (&cw)[kCoreCats][kWarps], int (&cb)[kCoreCats], unsigned long long& nalive,
+                          unsigned long long& ndel, unsigned long long& mymin) {
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const int J = ballot_steps(count, grid);
+  const long long csz = (long long)kThreads * J;
+  for (long long chunk = blockIdx.x; chunk * csz < count; chunk += grid) {
+    const long long wbase = chunk * csz + (long long)warp * 32 * J;
+    unsigned my[kCoreCats] = {0u, 0u, 0u, 0u, 0u};
+    for (int j = 0; j < J; ++j) {
+      const long long i = wbase + j * 32 + lane;
+      int cat = -1;
+      if (i < count) {
+        const int v = dom ? dom[i] : (int)i;
+        if (removed_at[v] == INT_MAX) {
+          const unsigned c = cnt[v];
+          ++nalive;
+          if (c < mymin) mymin = c;
+          if (c > kt) {
+            cat = kClasses;
+          } else {
+            removed_at[v] = prev;
+            core[v] = kt;
+            ++ndel;
+            const long long d = (long long)gload(off + v + 1) - (long long)gload(off + v);
+            if (d > 0) cat = degree_class(d, k);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kCoreCats; ++c) {
+        const unsigned m = __ballot_sync(kFull, cat == c);
+        if (lane == j) my[c] = m;
+      }
+    }
+    int pre[kCoreCats];
+#pragma unroll
+    for (int c = 0; c < kCoreCats; ++c) {
+      const int x = __popc(my[c]);
+      int incl = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      pre[c] = incl - x;
+      if (lane == 31) cw[c][warp] = incl;
+    }
+    __syncthreads();
+    if (threadIdx.x < kCoreCats) {
+      const int c = threadIdx.x;
+      int run = 0;
+      for (int q = 0; q < kWarps; ++q) {
+        const int t = cw[c][q];
+        cw[c][q] = run;
+        run += t;
+      }
+      int b = 0;
+      if (run > 0)
+        b = c < kClasses ? (int)atomicAdd(&slot.list_cnt[c], (unsigned)run)
+                         : (int)atomicAdd(&slot.aux0, (unsigned long long)run);
+      cb[c] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kCoreCats; ++c) {
+      unsigned m = my[c];
+      int pos = cb[c] + cw[c][warp] + pre[c];
+      int32_t* dst = c < kClasses ? w.list[nbuf][c] : keep;
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const long long idx = wbase + lane * 32 + b;
+        dst[pos++] = dom ? dom[idx] : (int)idx;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <class OffT>
 __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a) {
   __shared__ CtaShared sh;
+  __shared__ int cw[kCoreCats][kWarps];
+  __shared__ int cb[kCoreCats];
   const unsigned grid = gridDim.x;
   Sync* s = a.w.sync;
   const Knobs& k = a.k;
@@ -360,6 +454,7 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
   const long long gthreads = (long long)grid * kThreads;
   int32_t* removed_at = reinterpret_cast<int32_t*>(a.w.state);  // push iteration of the deletion
   uint32_t* cnt = reinterpret_cast<uint32_t*>(removed_at + n);   // residual degree
+  int32_t* doms[2] = {reinterpret_cast<int32_t*>(cnt + n), reinterpret_cast<int32_t*>(cnt + n) + n};
   const OffT* off = a.off;
   auto deg = [off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
   if (threadIdx.x == 0) sh.phase = 0;
@@ -376,6 +471,9 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
   bool lists_ok = true;
   unsigned long long pending = 0;  // vertices deleted by the last push, still to push
   long long K = -1;                // current level
+  const int32_t* dom = nullptr;    // the scans' domain: all vertices, then the remaining ones
+  long long dcount = n;
+  int dsel = 0;
   int it = 0, ballot_it = 0, online_it = 0;
   long long evisit = 0, fsum = 0;
   while (true) {
@@ -389,22 +487,13 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
       for (int attempt = 0; attempt < 2; ++attempt) {
         clear_next_slot(s, sh);
         PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-        unsigned long long nalive = 0, mymin = ~0ull;
-        const unsigned kt = (unsigned)Kt;
-        const int prev = it - 1;  // as if deleted by the push before the next one
-        uint32_t* core = a.core;
-        auto pred = [&](int v) {
-          if (removed_at[v] != INT_MAX) return false;
-          const unsigned c = cnt[v];
-          ++nalive;
-          if (c < mymin) mymin = c;
-          if (c > kt) return false;
-          removed_at[v] = prev;
-          core[v] = kt;
-          return true;
-        };
-        auto none = [](int) {};
-        ballot_filter(n, pred, deg, none, sh, a.w, k, grid, lbuf, slot);
+        unsigned long long nalive = 0, ndel = 0, mymin = ~0ull;
+        int32_t* keep = doms[dsel];
+        // deleted as if by the push before the next one
+        core_scan<OffT>(dcount, dom, keep, (unsigned)Kt, it - 1, removed_at, cnt, a.core, off, a.w, k, grid,
+                        lbuf, slot, cw, cb, nalive, ndel, mymin);
+        const unsigned long long td = cta_sum_u64(ndel, sh);
+        if (threadIdx.x == 0 && td) atomicAdd(&slot.nact, td);
         const unsigned long long ta = cta_sum_u64(nalive, sh);
         {
           unsigned long long m = mymin;
@@ -424,21 +513,24 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
         }
         if (!grid_sync(s, grid, sh, k)) return;
         const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+        dom = doms[dsel];
+        dcount = (long long)p.aux0;
+        dsel ^= 1;
         for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
-        const unsigned total = cnt_l[0] + cnt_l[1] + cnt_l[2] + cnt_l[3];
         if (p.aux1 == 0) {
           done = true;
           break;
         }
-        if (total > 0) {
+        if (p.nact > 0) {
           K = (long long)Kt;
-          pending = total;
+          pending = cnt_l[0] + cnt_l[1] + cnt_l[2] + cnt_l[3];
           break;
         }
         Kt = ~p.aux2;  // no alive vertex has degree K + 1: jump to the smallest
       }
       if (done) break;
       ++ballot_it;
+      if (pending == 0) continue;  // the level deleted isolated vertices only
       filt = 2;
       lists_ok = true;
     } else if (!lists_ok || k.filter == 2) {

@@ -90,8 +90,9 @@ def test_sssp_dense_iterations(delta):
 @pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
 def test_coreness(gi, mode):
     """Coreness equals Batagelj-Zaversnik's; the fixed-k kernel keeps exactly
-    the vertices of coreness >= k; every coreness value is one peeling level
-    of the trace, and the levels only rise."""
+    the vertices of coreness >= k; the coreness of every vertex with edges is
+    a peeling level of the trace (isolated vertices are deleted by a scan,
+    with nothing to push), and the levels only rise."""
     g = GRAPHS[gi]
     G = make(g, bits=32 if gi % 2 else 64, **FORCED[mode])
     core = G.coreness().cpu().numpy().view(np.uint32)
@@ -99,7 +100,8 @@ def test_coreness(gi, mode):
     assert np.array_equal(core, exp), (g.name, mode)
     assert G.last_status() == 0
     lev = [int(x) for x in G.trace()[:, 3]]
-    assert lev == sorted(lev) and set(lev) == set(int(x) for x in exp), (g.name, mode)
+    has_edges = np.diff(g.offsets) > 0
+    assert lev == sorted(lev) and set(lev) == set(int(x) for x in exp[has_edges]), (g.name, mode)
     for k in (1, 3, 16):
         inc, _ = G.kcore(k)
         assert np.array_equal(inc.cpu().numpy() == 1, core >= k), (g.name, mode, k)
