@@ -14,6 +14,8 @@ GPUs"), cited per function in ``oracle.c``:
 * ``sssp_bsp``   -- Sec. 2.1, the per-iteration BSP relaxation narrative.
 * ``kcore``      -- Sec. 6 "k-Core", queue peeling (membership + residual degree).
 * ``coreness``   -- Batagelj-Zaversnik core numbers (cross-check of ``kcore``).
+* ``wcc``        -- Sec. 3.2 (voting algorithms), component labels = the
+                    smallest vertex id of each weakly connected component.
 * ``pagerank``   -- Sec. 6 "PageRank", FP64 Jacobi pull iteration (readings of
                     the unstated teleport, dangling and stop rules: see the
                     function docstring).
@@ -64,6 +66,8 @@ def _load():
         lib.or_kcore.restype = ctypes.c_int
         lib.or_coreness.argtypes = [i64, vp, vp, vp]
         lib.or_coreness.restype = ctypes.c_int
+        lib.or_wcc.argtypes = [i64, vp, vp, vp]
+        lib.or_wcc.restype = ctypes.c_int
         lib.or_pagerank.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, i64, vp, vp]
         lib.or_pagerank.restype = i64
         _lib = lib
@@ -129,6 +133,15 @@ def coreness(off, idx) -> np.ndarray:
     core = np.zeros(n, dtype=np.uint32)
     _load().or_coreness(n, off.ctypes.data, ip, core.ctypes.data)
     return core
+
+
+def wcc(off, idx) -> np.ndarray:
+    """Label of every vertex: the smallest vertex id of its component."""
+    off, idx, ip = _csr(off, idx)
+    n = off.size - 1
+    label = np.empty(n, dtype=np.uint32)
+    _load().or_wcc(n, off.ctypes.data, ip, label.ctypes.data)
+    return label
 
 
 def pagerank(in_off, in_idx, outdeg=None, d: float = 0.85, tol: float = 1e-6,

@@ -212,6 +212,36 @@ OR_EXPORT int or_kcore(int64_t n, const int64_t *off, const int32_t *idx,
     return 0;
 }
 
+/* Weakly connected components (Sec. 3.2 names WCC among the voting
+ * algorithms): label[v] = the smallest vertex id of v's component.  Plain
+ * definition: visit the vertices in increasing order and flood each
+ * unlabelled one's component by a FIFO search, labelling it with that
+ * vertex, which is then the smallest id the component holds.  Edges are
+ * followed in both directions of the CSR as given (a symmetric CSR). */
+OR_EXPORT int or_wcc(int64_t n, const int64_t *off, const int32_t *idx, uint32_t *label)
+{
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t v = 0; v < n; ++v) label[v] = UINT32_MAX;
+    for (int64_t r = 0; r < n; ++r) {
+        if (label[r] != UINT32_MAX) continue;
+        int64_t head = 0, tail = 0;
+        label[r] = (uint32_t)r;
+        queue[tail++] = r;
+        while (head < tail) {
+            int64_t v = queue[head++];
+            for (int64_t p = off[v]; p < off[v + 1]; ++p) {
+                int64_t u = idx[p];
+                if (label[u] == UINT32_MAX) {
+                    label[u] = (uint32_t)r;
+                    queue[tail++] = u;
+                }
+            }
+        }
+    }
+    free(queue);
+    return 0;
+}
+
 /* Core number of every vertex (Batagelj & Zaversnik 2003): bucket the
  * vertices by degree and repeatedly remove a vertex of minimum current
  * degree; its current degree at removal is its core number. */

@@ -317,6 +317,42 @@ def test_coreness_vs_bruteforce():
         assert core[v] == kv
 
 
+# ------------------------------------------------------------------- WCC
+def reach_closure(g):
+    """Boolean reachability matrix (reflexive) by Floyd-Warshall on 0/1."""
+    n = g.n
+    r = np.eye(n, dtype=bool)
+    for u in range(n):
+        r[u, g.indices[g.offsets[u]:g.offsets[u + 1]]] = True
+    for m in range(n):
+        r |= np.outer(r[:, m], r[m, :])
+    return r
+
+
+@pytest.mark.parametrize("gi", range(len(small_graphs())))
+def test_wcc_vs_reachability(gi):
+    g = small_graphs()[gi]
+    lab = oracle.wcc(g.offsets, g.indices)
+    r = reach_closure(g)
+    for v in range(g.n):
+        assert lab[v] == np.nonzero(r[v])[0].min(), (g.name, v)
+
+
+def test_wcc_invariants_and_closed_forms():
+    g = gg.rmat(13)
+    lab = oracle.wcc(g.offsets, g.indices).astype(np.int64)
+    v = np.arange(g.n)
+    assert np.all(lab <= v) and np.array_equal(lab[lab], lab)
+    u = np.repeat(v, g.degrees())
+    assert np.array_equal(lab[u], lab[g.indices])  # both ends of every edge agree
+    for s in (0, 5, int(np.argmax(g.degrees())), g.n - 1):
+        reached = oracle.bfs(g.offsets, g.indices, s) >= 0
+        assert np.array_equal(reached, lab == lab[s])
+    assert np.all(oracle.wcc(gg.grid(7, 9).offsets, gg.grid(7, 9).indices) == 0)
+    e = gg.random_graph(40, 0, seed=1)
+    assert np.array_equal(oracle.wcc(e.offsets, e.indices), np.arange(40, dtype=np.uint32))
+
+
 # ----------------------------------------------------------------- PageRank
 def pagerank_dense(g, d):
     """Fixed point of the PageRank map by a dense FP64 linear solve."""
