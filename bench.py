@@ -8,7 +8,8 @@ step runs, each as one persistent kernel through the C ABI: SSSP from vertex
 0, k-core with k = 16 and PageRank (d = 0.85, FP32, L1 stop 1e-6).
 Other workloads: --workload rmat24-bfs (BFS from vertex 0 on R-MAT scale 24,
 int64 offsets), rmat16-bfs, rmat24-sssp, rmat24-pagerank, rmat24-kcore,
-rmat20-coreness, rmat24-coreness (k-core decomposition),
+rmat20-coreness, rmat24-coreness (k-core decomposition), rmat20-wcc,
+rmat24-wcc (connected components),
 rmat22-bfs, rmat22-sssp (profiling sizes), grid4096-bfs, grid4096-sssp,
 batch22, serve.
 
@@ -59,6 +60,10 @@ WORKLOADS = {
                             desc="R-MAT scale 20, int32 CSR: k-core decomposition (coreness of every vertex)"),
     "rmat24-coreness": dict(kind="rmat", scale=24, bits=64, algs=["coreness"],
                             desc="R-MAT scale 24, int64 offsets: k-core decomposition (coreness of every vertex)"),
+    "rmat20-wcc": dict(kind="rmat", scale=20, bits=32, algs=["wcc"],
+                       desc="R-MAT scale 20, int32 CSR: weakly connected components (min-label propagation)"),
+    "rmat24-wcc": dict(kind="rmat", scale=24, bits=64, algs=["wcc"],
+                       desc="R-MAT scale 24, int64 offsets: weakly connected components"),
     "rmat22-bfs": dict(kind="rmat", scale=22, bits=32, algs=["bfs"],
                        desc="R-MAT scale 22 (n=4,194,304, ef 16), int32 CSR: BFS src 0 (profiling size)"),
     "rmat22-sssp": dict(kind="rmat", scale=22, bits=32, algs=["sssp"],
@@ -199,7 +204,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_FILES = {"coreness_kernel": "kcore.cu"}  # kernels not in <algorithm>.cu
+KERNEL_FILES = {"coreness_kernel": "kcore.cu", "wcc_kernel": "sssp.cu"}  # kernels not in <algorithm>.cu
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -251,6 +256,8 @@ def algorithmic(alg, g, bits, out, iters):
         return e // 2, 4 * e + (2 * so + 1) * n
     if alg == "coreness":
         return e // 2, 4 * e + (2 * so + 8) * n
+    if alg == "wcc":
+        return e // 2, 4 * e + (2 * so + 12) * n
     if alg == "pagerank":
         return (e // 2) * iters, (4 * e + (2 * so + 12) * n) * iters
     raise ValueError(alg)
@@ -277,7 +284,7 @@ def run_simdx(args, rank, world, local):
     algs = wl["algs"]
     graphs = {a: G for a in algs}
     tuned, tuned_full, tune_s = {}, {}, 0.0
-    if args.autotune and "coreness" not in algs:
+    if args.autotune and not {"coreness", "wcc"} & set(algs):
         from paper_1812_04070_gb300 import simdx
         code = {"bfs": simdx.ALGO_BFS, "sssp": simdx.ALGO_SSSP, "kcore": simdx.ALGO_KCORE,
                 "pagerank": simdx.ALGO_PAGERANK}
@@ -297,6 +304,7 @@ def run_simdx(args, rank, world, local):
         "kcore": (torch.empty(g.n, dtype=torch.uint8, device=dev), torch.empty(g.n, dtype=torch.int32, device=dev)),
         "pagerank": torch.empty(g.n, dtype=torch.float32, device=dev),
         "coreness": torch.empty(g.n, dtype=torch.int32, device=dev),
+        "wcc": torch.empty(g.n, dtype=torch.int32, device=dev),
     }
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -310,6 +318,8 @@ def run_simdx(args, rank, world, local):
             Ga.kcore(16, out=outs["kcore"][0], resid=outs["kcore"][1], stats=st)
         elif alg == "coreness":
             Ga.coreness(out=outs["coreness"], stats=st)
+        elif alg == "wcc":
+            Ga.wcc(out=outs["wcc"], stats=st)
         else:
             Ga.pagerank(0.85, 1e-6, 1000, out=outs["pagerank"], stats=st)
 
@@ -348,7 +358,7 @@ def run_simdx(args, rank, world, local):
     work = {}
     for a in algs:
         o = outs[a]
-        if a in ("kcore", "coreness"):
+        if a in ("kcore", "coreness", "wcc"):
             host = None
         elif a == "sssp":
             host = o.cpu().numpy().view(np.uint32)
@@ -425,11 +435,12 @@ def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
                 "kcore": (torch.empty(g.n, dtype=torch.uint8).pin_memory(),
                           torch.empty(g.n, dtype=torch.int32).pin_memory()),
                 "pagerank": torch.empty(g.n, dtype=torch.float32).pin_memory(),
-                "coreness": torch.empty(g.n, dtype=torch.int32).pin_memory()}
+                "coreness": torch.empty(g.n, dtype=torch.int32).pin_memory(),
+                "wcc": torch.empty(g.n, dtype=torch.int32).pin_memory()}
     h2d = p_off.numel() * p_off.element_size() + p_idx.numel() * 4 + (p_w.numel() * 4 if "sssp" in algs else 0)
     d2h = 0
     for a in algs:
-        d2h += g.n * (4 if a in ("bfs", "sssp", "pagerank", "coreness") else 5)
+        d2h += g.n * (4 if a in ("bfs", "sssp", "pagerank", "coreness", "wcc") else 5)
 
     def one():
         G = Graph(p_off.numpy(), p_idx.numpy(), weights=p_w.numpy().view(np.uint32) if "sssp" in algs else None)
@@ -446,6 +457,8 @@ def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
                 host_out[a][1].copy_(rs, non_blocking=True)
             elif a == "coreness":
                 host_out[a].copy_(G.coreness(), non_blocking=True)
+            elif a == "wcc":
+                host_out[a].copy_(G.wcc(), non_blocking=True)
             else:
                 host_out[a].copy_(G.pagerank(0.85, 1e-6, 1000), non_blocking=True)
         torch.cuda.synchronize()
@@ -636,6 +649,10 @@ def cpu_baseline(workload, g, w, budget_s=15.0):
             oracle.coreness(g.offsets, g.indices)
             m = g.e // 2
             parts.append("coreness full")
+        elif a == "wcc":
+            oracle.wcc(g.offsets, g.indices)
+            m = g.e // 2
+            parts.append("wcc full")
         else:
             iters = 5
             oracle.pagerank(g.offsets, g.indices, fixed_iter=iters)

@@ -246,6 +246,16 @@ SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
 SIMDX_API int simdx_kcore_decompose(simdx_graph *g, uint32_t *coreness, simdx_stats *stats,
                                     void *stream);
 
+/* Weakly connected components (Sec. 3.2 lists WCC with the voting
+ * algorithms): label[v] = the smallest vertex id of v's component, so two
+ * vertices share a label exactly when a path joins them.  Min-label
+ * propagation on the SSSP path: every vertex starts active with its own id,
+ * a push offers the label to every neighbour (min combine, dense iterations
+ * as in SSSP), and the run ends when no label changes.  label: device
+ * uint32[n].  Needs a symmetric graph.  Errors: EINVAL (NULL label,
+ * directed graph). */
+SIMDX_API int simdx_wcc(simdx_graph *g, uint32_t *label, simdx_stats *stats, void *stream);
+
 /* PageRank (Sec. 6 "PageRank"; aggregation combine = sum, pull):
  *   x_0 = 1/n;  x_{t+1}(v) = (1-d)/n + d*(sum_{u in N_in(v)} x_t(u)/outdeg(u)
  *                                         + D_t/n),

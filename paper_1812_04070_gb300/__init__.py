@@ -177,6 +177,14 @@ class Graph:
         simdx.simdx_kcore_decompose(self.handle, out.data_ptr(), stats, _stream_handle(stream))
         return out
 
+    def wcc(self, out=None, stats: simdx_stats | None = None, stream=None):
+        """uint32 component label (smallest vertex id of the component) of
+        every vertex in an int32 tensor (simdx_wcc)."""
+        torch = _torch()
+        out = self._out(out, torch.int32)
+        simdx.simdx_wcc(self.handle, out.data_ptr(), stats, _stream_handle(stream))
+        return out
+
     def autotune(self, algo: int, arg: int = 0, reps: int = 5, stream=None) -> tuple[dict, float]:
         """Measure knob settings for `algo` (simdx.ALGO_*; arg = source or
         k) on this graph, install the fastest and return it with its median

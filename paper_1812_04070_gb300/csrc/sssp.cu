@@ -44,7 +44,9 @@ struct SsspArgs {
   Knobs k;
 };
 
-template <class OffT, bool V>
+// With W (connected components) the relaxed value is the neighbour's label
+// itself: no weight is read.
+template <class OffT, bool V, bool W = false>
 struct SsspPush {
   struct Src {
     uint32_t d;
@@ -134,7 +136,7 @@ struct SsspPush {
       cur[q] = 0;
       x[q] = s[q].base + u[q];
       if ((ok >> q) & 1u) {
-        nd[q] = (unsigned long long)s[q].d + gload(wt + p[q]);
+        nd[q] = (unsigned long long)s[q].d + (W ? 0u : gload(wt + p[q]));
         cur[q] = dist[x[q]];
       }
     }
@@ -217,7 +219,13 @@ struct SsspPull {
 // dist < pdist over all vertices costs less than recording them.
 constexpr unsigned long long kDenseDiv = 16;
 
-template <class OffT, bool V, bool PULL>
+// With W the kernel computes weakly connected components by min-label
+// propagation (Sec. 3.2 lists WCC with the voting algorithms; the label
+// that survives a vertex's combine is the smallest it is offered): every
+// vertex starts active with its own id as its label, relaxations add no
+// weight and there are no buckets, so the fixed point labels each
+// component with its smallest id.
+template <class OffT, bool V, bool PULL, bool W = false>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
   __shared__ unsigned red_u[kWarps];
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
   const long long gthreads = (long long)grid * kThreads;
   uint32_t* pdist = reinterpret_cast<uint32_t*>(a.w.state);
   uint8_t* pend = reinterpret_cast<uint8_t*>(pdist + n);
-  const unsigned long long delta = k.delta ? k.delta : 0ull;
+  const unsigned long long delta = (W || !k.delta) ? 0ull : k.delta;
   const unsigned long long kInfT = ~0ull;
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
@@ -246,16 +254,16 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     } else {
       is_src = x == a.src;
     }
-    a.dist[x] = is_src ? 0u : 0xffffffffu;
+    a.dist[x] = W ? (uint32_t)x : (is_src ? 0u : 0xffffffffu);
     pdist[x] = 0xffffffffu;
-    pend[x] = is_src ? 1 : 0;  // the source is the first pending vertex
+    pend[x] = (W || is_src) ? 1 : 0;  // the source (every vertex for W) is pending
   }
   if (PULL)  // pull frontiers (BFS leaves these bitmaps as it likes)
     for (long long q = gtid; q < (((long long)n + 31) >> 5); q += gthreads) {
       a.w.bm_f[0][q] = 0u;
       a.w.bm_f[1][q] = 0u;
     }
-  if (blockIdx.x == 0) {
+  if (!W && blockIdx.x == 0) {
     const int nsrc = V ? a.ninst : 1;
     for (int i = threadIdx.x; i < nsrc; i += kThreads) {
       const int v = V ? (a.ninst <= 64 ? a.src_list[i] : a.srcs[i]) : a.src;
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
   unsigned long long T = delta ? delta : kInfT;  // bucket bound: process dist < T
   int lbuf = 0;
   unsigned cnt[kClasses];
-  bool lists_ok = true;
+  bool lists_ok = !W;  // W: the first filter lists every vertex
   {
     const PhaseSlot& p = s->slot[0];
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
@@ -394,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
         if (total > 0 || delta == 0) break;
         // the guessed bucket was empty: jump to the bucket of the min distance
         const unsigned long long mn = ~p.aux2;
-        Tn = (mn / delta + 1) * delta;
+        Tn = delta ? (mn / delta + 1) * delta : kInfT;  // (delta > 0 here)
       }
       if (done) break;
       filt = 2;
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       online_reset(sh);
       __syncthreads();
       PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-      SsspPush<OffT, V> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
+      SsspPush<OffT, V, W> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
       f.dense = mf * kDenseDiv > m_all;
       scan_all = f.dense;
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
@@ -541,6 +549,29 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
   // push kernel carries none of their registers
   const bool pull = g->symmetric && g->cfg.direction == 2;
   const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true> : (const void*)sssp_kernel<OffT, false, false>;
+  int grid = grid_for(g, kern);
+  int rc = prepare_launch(g, st);
+  if (rc) return rc;
+  void* args[] = {&a};
+  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st);
+}
+
+template <class OffT>
+static int run_wcc(simdx_graph* g, uint32_t* label, simdx_stats* stats, cudaStream_t st) {
+  SsspArgs<OffT> a{};
+  a.n = (int)g->n;
+  a.src = 0;
+  a.nreal = (int)g->n;
+  a.ninst = 1;
+  a.srcs = nullptr;
+  a.off = (const OffT*)g->off;
+  a.idx = g->idx;
+  a.wt = nullptr;  // never read
+  a.dist = label;
+  a.w = make_work(g);
+  a.k = make_knobs(g);
+  const void* kern = (const void*)sssp_kernel<OffT, false, false, true>;
   int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
@@ -661,4 +692,15 @@ extern "C" int simdx_sssp_batch(simdx_graph* g, const int32_t* srcs, int32_t k, 
   if (rc) return rc;
   return g->off_bits == 32 ? run_sssp_batch<int32_t>(g, srcs, k, dist, stats, st)
                            : run_sssp_batch<long long>(g, srcs, k, dist, stats, st);
+}
+
+extern "C" int simdx_wcc(simdx_graph* g, uint32_t* label, simdx_stats* stats, void* stream) {
+  if (!g || !label || !g->symmetric) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g->n == 0) {
+    int rc = prepare_launch(g, st);
+    return rc ? rc : finish_launch(g, stats, st);
+  }
+  return g->off_bits == 32 ? run_wcc<int32_t>(g, label, stats, st) : run_wcc<long long>(g, label, stats, st);
 }

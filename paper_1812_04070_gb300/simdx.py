@@ -81,6 +81,7 @@ SIGNATURES = {
     "simdx_sssp": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_kcore": (ctypes.c_int, [_vp, _u32, _vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_kcore_decompose": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
+    "simdx_wcc": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_pagerank": (ctypes.c_int, [_vp, _f32, _f32, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_bfs_noalloc": (ctypes.c_int, [ctypes.POINTER(simdx_csr), _i32, _vp, _vp]),
     "simdx_bfs_batch": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
@@ -203,6 +204,11 @@ def simdx_kcore(g: int, k: int, in_core_ptr: int, resid_ptr: int | None, stats: 
 def simdx_kcore_decompose(g: int, core_ptr: int, stats: simdx_stats | None, stream: int | None) -> None:
     _check(_lib().simdx_kcore_decompose(g, core_ptr, ctypes.byref(stats) if stats is not None else None, stream),
            "simdx_kcore_decompose")
+
+
+def simdx_wcc(g: int, label_ptr: int, stats: simdx_stats | None, stream: int | None) -> None:
+    _check(_lib().simdx_wcc(g, label_ptr, ctypes.byref(stats) if stats is not None else None, stream),
+           "simdx_wcc")
 
 
 def simdx_pagerank(g: int, damping: float, l1_tol: float, max_iter: int, rank_ptr: int,

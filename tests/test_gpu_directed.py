@@ -71,4 +71,8 @@ def test_directed_kcore_rejected():
     G = _make(off, idx, ioff, iidx, w, bits=64)
     with pytest.raises(SimdxError):
         G.kcore(2)
+    with pytest.raises(SimdxError):
+        G.coreness()
+    with pytest.raises(SimdxError):
+        G.wcc()
     G.close()

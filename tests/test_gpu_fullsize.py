@@ -48,6 +48,7 @@ def test_rmat20_sssp_kcore_pagerank():
         assert np.array_equal(inc.cpu().numpy(), ei)
         assert np.array_equal(resid.cpu().numpy(), er)
     assert np.array_equal(G.coreness().cpu().numpy().view(np.uint32), oracle.coreness(g.offsets, g.indices))
+    assert np.array_equal(G.wcc().cpu().numpy().view(np.uint32), oracle.wcc(g.offsets, g.indices))
     rel, t, t_stop, st = check_pagerank(G, g)
     assert st.status == 0
     assert rel <= 1e-6, rel
@@ -68,6 +69,7 @@ def test_rmat24_bfs_sssp():
     G = make(g, w, bits=64)
     assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
     assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
+    assert np.array_equal(G.wcc().cpu().numpy().view(np.uint32), oracle.wcc(g.offsets, g.indices))
     G.close()
 
 
@@ -79,6 +81,7 @@ def test_grid4096_bfs_sssp():
     assert lev.max() == 8190  # level(r, c) = r + c from the corner
     assert np.array_equal(lev, oracle.bfs(g.offsets, g.indices, 0))
     assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
+    assert not G.wcc().any()  # one component: label 0 everywhere (the label walks 8190 hops)
     G.close()
 
 

@@ -108,6 +108,22 @@ def test_coreness(gi, mode):
     G.close()
 
 
+@pytest.mark.parametrize("mode", ["default", "ballot", "overflow", "tiny_bins", "all_classes", "one_cta_per_sm"])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_wcc(gi, mode):
+    """Component labels equal the oracle's (smallest id per component)."""
+    from paper_1812_04070_gb300 import simdx_stats
+    import torch
+    g = GRAPHS[gi]
+    G = make(g, bits=64 if gi % 2 else 32, **FORCED[mode])
+    st = simdx_stats()
+    lab = G.wcc(stats=st).cpu().numpy().view(np.uint32)
+    torch.cuda.synchronize()
+    assert np.array_equal(lab, oracle.wcc(g.offsets, g.indices)), (g.name, mode)
+    assert st.status == 0 and G.last_status() == 0
+    G.close()
+
+
 @pytest.mark.parametrize("mode", ["default", "push", "pull", "ballot", "overflow", "all_classes",
                                   "all_classes_pull", "one_cta_per_sm"])
 @pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
