@@ -248,12 +248,14 @@ SIMDX_API int simdx_kcore_decompose(simdx_graph *g, uint32_t *coreness, simdx_st
 
 /* Weakly connected components (Sec. 3.2 lists WCC with the voting
  * algorithms): label[v] = the smallest vertex id of v's component, so two
- * vertices share a label exactly when a path joins them.  Min-label
- * propagation on the SSSP path: every vertex starts active with its own id,
- * a push offers the label to every neighbour (min combine, dense iterations
- * as in SSSP), and the run ends when no label changes.  label: device
- * uint32[n].  Needs a symmetric graph.  Errors: EINVAL (NULL label,
- * directed graph). */
+ * vertices share a label exactly when a path joins them.  Two launches on
+ * `stream`: a BFS from a vertex of largest degree (chosen when the graph is
+ * created) labels its component with the component's smallest id; then
+ * min-label propagation on the SSSP path runs over the vertices it did not
+ * reach (each starts with its own id; a push offers the label to every
+ * neighbour, min combine), ending when no label changes.  Stats and trace
+ * records cover both launches.  label: device uint32[n].  Needs a
+ * symmetric graph.  Errors: EINVAL (NULL label, directed graph). */
 SIMDX_API int simdx_wcc(simdx_graph *g, uint32_t *label, simdx_stats *stats, void *stream);
 
 /* PageRank (Sec. 6 "PageRank"; aggregation combine = sum, pull):

@@ -569,6 +569,29 @@ static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* st
   return finish_launch(g, stats, st);
 }
 
+template <class OffT>
+static int launch_bfs_only(simdx_graph* g, int32_t src, int32_t* levels, cudaStream_t st) {
+  BfsArgs<OffT> a{};
+  a.n = (int)g->n;
+  a.src = src;
+  a.off = (const OffT*)g->off;
+  a.idx = g->idx;
+  a.ioff = (const OffT*)g->in_off;
+  a.iidx = g->in_idx;
+  a.level = levels;
+  a.m_total = g->e;
+  a.w = make_work(g);
+  a.k = make_knobs(g);
+  const void* kern = (const void*)bfs_kernel<OffT>;
+  void* args[] = {&a};
+  return launch_coop(kern, grid_for(g, kern), args, st);
+}
+
+int bfs_launch_only(simdx_graph* g, int32_t src, int32_t* levels, cudaStream_t st) {
+  return g->off_bits == 32 ? launch_bfs_only<int32_t>(g, src, levels, st)
+                           : launch_bfs_only<long long>(g, src, levels, st);
+}
+
 // Launch the BFS kernel on caller-provided arrays and workspace views (no
 // graph object): used by entry points whose workspace is not library-owned
 // device memory.

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -158,6 +159,14 @@ int prepare_launch(simdx_graph* g, cudaStream_t st) {
   return SIMDX_OK;
 }
 
+int prepare_next_launch(simdx_graph* g, cudaStream_t st) {
+  char* sy = reinterpret_cast<char*>(g->sync);
+  SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, arrive), 0, sizeof(unsigned long long), st));
+  SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, slot), 0, sizeof(PhaseSlot) * 3, st));
+  SIMDX_CUDA(cudaMemsetAsync(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16), st));
+  return SIMDX_OK;
+}
+
 // A cooperative launch through the extensible launch API, which stream
 // capture records as a cooperative kernel node.
 int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st) {
@@ -246,6 +255,24 @@ __global__ void weight_max_kernel(long long e, const uint32_t* w, unsigned* out)
   unsigned m = 0;
   for (long long p = tid; p < e; p += stride) m = max(m, w[p]);
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// A vertex of largest degree, smallest id among them: (degree << 32 |
+// ~id) maximised.
+template <class OffT>
+__global__ void hub_kernel(long long n, const OffT* off, unsigned long long* out) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long m = 0;
+  for (long long v = tid; v < n; v += stride) {
+    const unsigned long long key = ((unsigned long long)(off[v + 1] - off[v]) << 32) | (0xffffffffull - (unsigned long long)v);
+    m = key > m ? key : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
@@ -415,9 +442,9 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
       return fail(rc);
   }
   // validate on the device (also catches bad host input after the copy)
-  int* d_bad = nullptr;  // [0] validation flags, [1] largest weight
-  if ((e = dev_alloc((void**)&d_bad, 2 * sizeof(int), st)) != cudaSuccess) return fail(cuda_status(e, "dev_alloc"));
-  cudaMemsetAsync(d_bad, 0, 2 * sizeof(int), st);
+  int* d_bad = nullptr;  // [0] validation flags, [1] largest weight, [2..3] hub key
+  if ((e = dev_alloc((void**)&d_bad, 4 * sizeof(int), st)) != cudaSuccess) return fail(cuda_status(e, "dev_alloc"));
+  cudaMemsetAsync(d_bad, 0, 4 * sizeof(int), st);
   int vblocks = std::max(1, std::min(4 * g->num_sms, (int)((g->e + g->n) / 256 + 1)));
   const simdx_csr* parts[2] = {csr, csc};
   for (int pi = 0; pi < 2; ++pi) {
@@ -431,14 +458,25 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
   }
   if (g->w && g->e > 0)
     weight_max_kernel<<<vblocks, 256, 0, st>>>(g->e, g->w, reinterpret_cast<unsigned*>(d_bad + 1));
-  int h_bad[2] = {0, 0};
-  e = cudaMemcpyAsync(h_bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (g->off_bits == 32)
+    hub_kernel<int32_t><<<vblocks, 256, 0, st>>>(g->n, (const int32_t*)g->off,
+                                                 reinterpret_cast<unsigned long long*>(d_bad + 2));
+  else
+    hub_kernel<long long><<<vblocks, 256, 0, st>>>(g->n, (const long long*)g->off,
+                                                   reinterpret_cast<unsigned long long*>(d_bad + 2));
+  int h_bad[4] = {0, 0, 0, 0};
+  e = cudaMemcpyAsync(h_bad, d_bad, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
   dev_free(d_bad, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "graph validation"));
   if (h_bad[0]) return fail(SIMDX_EINVAL);
   // default bucket width: 16 x the largest weight (a few buckets cover the
   // distances of a low-diameter graph; a long path gets wide buckets)
+  {
+    unsigned long long key = 0;
+    std::memcpy(&key, h_bad + 2, sizeof(key));
+    g->hub = key ? (int32_t)(0xffffffffull - (key & 0xffffffffull)) : 0;
+  }
   const unsigned wmax = static_cast<unsigned>(h_bad[1]);
   if (wmax) g->cfg.delta = wmax >= (1u << 26) ? (1u << 30) : 16u * wmax;
   // workspace

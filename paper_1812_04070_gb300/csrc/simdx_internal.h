@@ -34,6 +34,7 @@ struct simdx_graph {
   void* in_off = nullptr;    // CSC offsets (== off when symmetric)
   int32_t* in_idx = nullptr;
   uint32_t* w = nullptr;
+  int32_t hub = 0;           // a vertex of largest degree (smallest id among them)
   // knobs
   simdx_config cfg{};
   // workspace
@@ -87,6 +88,14 @@ int grid_for(const simdx_graph* g, const void* kernel);
 
 // Reset the barrier/slot block and statistics before a launch.
 int prepare_launch(simdx_graph* g, cudaStream_t st);
+// Before a further launch of the same call: a fresh barrier, phase slots and
+// chunk counters; the abort / error words, the edge count and the stats
+// record carry over (a launch after a failed one returns at its first
+// barrier, and the error stays reported).
+int prepare_next_launch(simdx_graph* g, cudaStream_t st);
+// The BFS kernel from src into levels, on the graph's workspace, with no
+// preparation or stats (the caller brackets it).
+int bfs_launch_only(simdx_graph* g, int32_t src, int32_t* levels, cudaStream_t st);
 
 // Launch `kernel` cooperatively with `grid` CTAs of kThreads threads.
 int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st);

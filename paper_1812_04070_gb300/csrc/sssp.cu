@@ -219,12 +219,13 @@ struct SsspPull {
 // dist < pdist over all vertices costs less than recording them.
 constexpr unsigned long long kDenseDiv = 16;
 
-// With W the kernel computes weakly connected components by min-label
-// propagation (Sec. 3.2 lists WCC with the voting algorithms; the label
-// that survives a vertex's combine is the smallest it is offered): every
-// vertex starts active with its own id as its label, relaxations add no
-// weight and there are no buckets, so the fixed point labels each
-// component with its smallest id.
+// With W the kernel computes weakly connected components (Sec. 3.2 lists
+// WCC with the voting algorithms).  A BFS from a highest-degree vertex,
+// launched just before, left its levels in `dist`: the vertices it reached
+// form one component and take its smallest id as their final label (every
+// vote for them is the same).  The other vertices start with their own id
+// and propagate the minimum (relaxations add no weight, no buckets), so the
+// fixed point labels each component with its smallest id.
 template <class OffT, bool V, bool PULL, bool W = false>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
@@ -246,7 +247,37 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
   // state id -> vertex of the one CSR
   auto realv = [nreal](long long x) { return V ? (int)((unsigned long long)x % nreal) : (int)x; };
   // ---- phase 0: reset state, seed the source(s)
-  for (long long x = gtid; x < n; x += gthreads) {
+  if (W) {
+    unsigned long long mn = ~0ull;  // smallest id the BFS reached (this thread's first)
+    for (long long x = gtid; x < n; x += gthreads)
+      if ((int)a.dist[x] >= 0) {
+        mn = (unsigned long long)x;
+        break;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(kFull, mn, o);
+      mn = y < mn ? y : mn;
+    }
+    if (lane_id() == 0) sh.red64[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = ~0ull;
+      for (int q = 0; q < kWarps; ++q) t = sh.red64[q] < t ? sh.red64[q] : t;
+      if (t != ~0ull) atomicMax(&s->slot[slot_of(sh.phase)].aux2, ~t);  // slots start at 0
+    }
+    clear_next_slot(s, sh);
+    if (!grid_sync(s, grid, sh, k)) return;
+    const uint32_t lab0 = (uint32_t)~s->slot[slot_of(sh.phase - 1)].aux2;
+    for (long long x = gtid; x < n; x += gthreads) {
+      const bool reached = (int)a.dist[x] >= 0;
+      const uint32_t l = reached ? lab0 : (uint32_t)x;
+      const bool edges = gload(a.off + x + 1) != gload(a.off + x);
+      a.dist[x] = l;
+      pdist[x] = (reached || !edges) ? l : 0xffffffffu;  // final unless it still has to push
+      pend[x] = (!reached && edges) ? 1 : 0;
+    }
+  }
+  for (long long x = gtid; !W && x < n; x += gthreads) {
     bool is_src;
     if (V) {
       const long long inst = x / nreal;
@@ -254,9 +285,9 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     } else {
       is_src = x == a.src;
     }
-    a.dist[x] = W ? (uint32_t)x : (is_src ? 0u : 0xffffffffu);
+    a.dist[x] = is_src ? 0u : 0xffffffffu;
     pdist[x] = 0xffffffffu;
-    pend[x] = (W || is_src) ? 1 : 0;  // the source (every vertex for W) is pending
+    pend[x] = is_src ? 1 : 0;  // the source is the first pending vertex
   }
   if (PULL)  // pull frontiers (BFS leaves these bitmaps as it likes)
     for (long long q = gtid; q < (((long long)n + 31) >> 5); q += gthreads) {
@@ -280,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
   unsigned long long T = delta ? delta : kInfT;  // bucket bound: process dist < T
   int lbuf = 0;
   unsigned cnt[kClasses];
-  bool lists_ok = !W;  // W: the first filter lists every vertex
+  bool lists_ok = !W;  // W: the first filter lists the pending vertices
   {
     const PhaseSlot& p = s->slot[0];
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
@@ -491,9 +522,9 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      // a batch's later group launches number their records on from the
-      // iterations the launches before them added to the stats
-      const int ti = it + (V ? a.w.stats->iterations : 0);
+      // a batch's later group launches (and WCC after its BFS) number their
+      // records on from the iterations the launches before them recorded
+      const int ti = it + ((V || W) ? a.w.stats->iterations : 0);
       trace_put(a.w, ti, (pull ? 2 : 1) | (filt << 8) | (scan_all ? 1 << 16 : 0), (long long)total, 0,
                 (long long)(T == kInfT ? -1 : (long long)T), t_it);
       trace_classes(a.w, ti, p);
@@ -575,6 +606,10 @@ static int run_wcc(simdx_graph* g, uint32_t* label, simdx_stats* stats, cudaStre
   int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
+  // the hub's component by BFS (levels in `label`), then the rest
+  if ((rc = bfs_launch_only(g, g->hub, reinterpret_cast<int32_t*>(label), st)) != SIMDX_OK) return rc;
+  if ((rc = prepare_next_launch(g, st)) != SIMDX_OK) return rc;
+  a.src = g->hub;
   void* args[] = {&a};
   if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
   return finish_launch(g, stats, st);
@@ -648,14 +683,7 @@ static int run_sssp_batch(simdx_graph* g, const int32_t* srcs, int k, uint32_t* 
   if (rc) return rc;
   for (int g0 = 0; g0 < k; g0 += group) {
     const int gk = std::min(group, k - g0);
-    if (g0 > 0) {
-      // a fresh barrier and phase slots; abort / err / evisit carry over, so
-      // a group after a failed one returns at its first barrier
-      char* sy = reinterpret_cast<char*>(g->sync);
-      SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, arrive), 0, sizeof(unsigned long long), st));
-      SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, slot), 0, sizeof(PhaseSlot) * 3, st));
-      SIMDX_CUDA(cudaMemsetAsync(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16), st));
-    }
+    if (g0 > 0 && (rc = prepare_next_launch(g, st)) != SIMDX_OK) return rc;
     a.n = gk * (int)g->n;
     a.src = srcs[g0];
     a.ninst = gk;
