@@ -157,11 +157,14 @@ __device__ __forceinline__ bool grid_sync(Sync* s, unsigned grid, CtaShared& sh,
     bool skip = (k.skip_cta == (int)blockIdx.x) && ((unsigned long long)k.skip_phase == ph);
     if (!skip) red_release_add_u64(&s->arrive, 1ull);
     const unsigned long long target = ph * (unsigned long long)grid;
+    // polls without sleeping (measured on GB300: 2.3 us per barrier of 608
+    // CTAs, 2.5 us with a 32 ns sleep per poll); every 64 polls it checks
+    // the abort word and the time limit
     unsigned long long t0 = 0;
     unsigned spins = 0;
     while (ld_acquire_u64(&s->arrive) < target) {
-      if (ld_volatile_i32(&s->abort)) { ok = 0; break; }
       if ((++spins & 63u) == 0) {
+        if (ld_volatile_i32(&s->abort)) { ok = 0; break; }
         unsigned long long t = globaltimer();
         if (t0 == 0) t0 = t;
         else if (t - t0 > k.timeout_ns) {
@@ -171,7 +174,6 @@ __device__ __forceinline__ bool grid_sync(Sync* s, unsigned grid, CtaShared& sh,
           break;
         }
       }
-      __nanosleep(32);
     }
     if (ok && ld_volatile_i32(&s->abort)) ok = 0;
     sh.ok = ok;
