@@ -14,9 +14,8 @@
 //          the iteration (removed_at >= i) and is deleted if the count is < k;
 //          the owner writes, no atomics.
 // Pull runs while the deleted vertices carry many edges (the start), push
-// once they become few (Sec. 5: "k-Core conducts pull at the beginning while
-// push in the end"); the switch compares the frontier's edges with the alive
-// vertices' edges.
+// once they become few, the order Sec. 5 gives for k-core; the switch
+// compares the frontier's edges with the alive vertices' edges.
 #include <climits>
 
 #include "simdx_internal.h"
