@@ -305,6 +305,11 @@ __device__ __forceinline__ void pr_tile(const PrArgs<OffT>& a, PrPull<OffT>& f, 
   end_bit = nx;
 }
 
+// Fetch the line holding p into L2 with no register waiting on it.
+__device__ __forceinline__ void pr_prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // One iteration's sums over the in-edges of this warp's tile range
 // [t_beg, t_end).
 template <class OffT>
@@ -315,6 +320,13 @@ __device__ __forceinline__ void pr_walk(const PrArgs<OffT>& a, PrPull<OffT>& f, 
   int trank = rank0;
   unsigned end_bit = 1;
   for (int t = t_beg; t < t_end; t += 2) {
+    {
+      // the next two tiles' in-edge indices (eight 128-byte lines) go to L2
+      // while this step's gathers are in flight
+      const int lane = lane_id();
+      const long long p = (long long)(t + 2) * kTile + 32 * lane;
+      if (lane < 8 && t + 2 + (lane >> 2) < t_end && p < a.e) pr_prefetch_l2(a.iidx + p);
+    }
     const TileIn x = pr_load(a, f.cin, t);
     TileIn y{};
     const bool two = t + 1 < t_end;
