@@ -56,3 +56,21 @@ def test_host_only_calls(lib):
     assert (c.small_max, c.bin_per_thread) == (32, 64)  # Sec. 4: thread/warp separator 32, threshold 64
     assert 128 <= c.med_max <= 2048  # Sec. 4: the warp/CTA separator is insensitive in [128, 2048]
     assert simdx.simdx_version() >= 10000
+
+
+def test_config_layout_matches_header(lib):
+    """The binding's simdx_config mirrors the header field for field (the
+    batch_group knob took one of the reserved words, so the size is
+    unchanged); simdx_config_default writes the whole struct."""
+    import ctypes
+    from paper_1812_04070_gb300 import simdx
+    text = open(os.path.join(ROOT, "include", "simdx.h")).read()
+    end = text.index("} simdx_config;")
+    body = text[text.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(?:int32_t|uint32_t|float)\s+([a-z_0-9]+)(\[(\d+)\])?;", body)
+    assert [f[0] for f in fields] == [f[0] for f in simdx.simdx_config._fields_]
+    words = sum(int(n) if n else 1 for _, _, n in fields)
+    assert ctypes.sizeof(simdx.simdx_config) == 4 * words
+    c = simdx.simdx_config_default()
+    assert c.batch_group == 0 and list(c.reserved) == [0] * 7
