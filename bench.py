@@ -626,44 +626,49 @@ def run_serve(args, rank, world, local):
 # ------------------------------------------------------------ CPU oracle legs
 def cpu_baseline(workload, g, w, budget_s=15.0):
     """The oracle as it stands (single thread), on a bounded sample of the
-    workload; returns GTEPS with the same edge counting."""
+    workload repeated until about budget_s seconds of CPU work; returns GTEPS
+    with the same edge counting."""
     import oracle
     wl = WORKLOADS[workload]
-    t_tot, edges = 0.0, 0
+    t_tot, edges, reps = 0.0, 0, 0
     parts = []
-    for a in wl["algs"]:
-        t0 = time.perf_counter()
-        if a == "bfs":
-            lev = oracle.bfs(g.offsets, g.indices, 0)
-            m = int(g.degrees()[lev >= 0].sum()) // 2
-            parts.append("bfs full")
-        elif a == "sssp":
-            d = oracle.sssp(g.offsets, g.indices, w, 0)
-            m = int(g.degrees()[d != 0xFFFFFFFF].sum()) // 2
-            parts.append("sssp full")
-        elif a == "kcore":
-            oracle.kcore(g.offsets, g.indices, 16)
-            m = g.e // 2
-            parts.append("kcore full")
-        elif a == "coreness":
-            oracle.coreness(g.offsets, g.indices)
-            m = g.e // 2
-            parts.append("coreness full")
-        elif a == "wcc":
-            oracle.wcc(g.offsets, g.indices)
-            m = g.e // 2
-            parts.append("wcc full")
-        else:
-            iters = 5
-            oracle.pagerank(g.offsets, g.indices, fixed_iter=iters)
-            m = (g.e // 2) * iters
-            parts.append(f"pagerank {iters} iterations")
-        t_tot += time.perf_counter() - t0
-        edges += m
-        if t_tot > budget_s:
+    while True:
+        for a in wl["algs"]:
+            t0 = time.perf_counter()
+            if a == "bfs":
+                lev = oracle.bfs(g.offsets, g.indices, 0)
+                m = int(g.degrees()[lev >= 0].sum()) // 2
+                part = "bfs full"
+            elif a == "sssp":
+                d = oracle.sssp(g.offsets, g.indices, w, 0)
+                m = int(g.degrees()[d != 0xFFFFFFFF].sum()) // 2
+                part = "sssp full"
+            elif a == "kcore":
+                oracle.kcore(g.offsets, g.indices, 16)
+                m = g.e // 2
+                part = "kcore full"
+            elif a == "coreness":
+                oracle.coreness(g.offsets, g.indices)
+                m = g.e // 2
+                part = "coreness full"
+            elif a == "wcc":
+                oracle.wcc(g.offsets, g.indices)
+                m = g.e // 2
+                part = "wcc full"
+            else:
+                iters = 5
+                oracle.pagerank(g.offsets, g.indices, fixed_iter=iters)
+                m = (g.e // 2) * iters
+                part = f"pagerank {iters} iterations"
+            t_tot += time.perf_counter() - t0
+            edges += m
+            if reps == 0:
+                parts.append(part)
+        reps += 1
+        if t_tot >= budget_s or reps >= 50:
             break
     return {"value": round(edges / t_tot / 1e9, 4), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{workload}: " + ", ".join(parts) + f" ({t_tot:.1f} s, single thread)"}
+            "sample": f"{workload}: {reps} x (" + ", ".join(parts) + f") ({t_tot:.1f} s, single thread)"}
 
 
 def run_reference(args, rank, world):
