@@ -353,6 +353,22 @@ def test_wcc_invariants_and_closed_forms():
     assert np.array_equal(oracle.wcc(e.offsets, e.indices), np.arange(40, dtype=np.uint32))
 
 
+def test_coreness_invariants_rmat():
+    """At R-MAT scale: the k-core (queue peeling) is exactly {coreness >= k}
+    for every k up to the largest coreness, each vertex of coreness c has at
+    least c neighbours of coreness >= c, and isolated vertices have 0."""
+    g = gg.rmat(12)
+    core = oracle.coreness(g.offsets, g.indices).astype(np.int64)
+    deg = g.degrees()
+    assert np.all(core[deg == 0] == 0) and np.all(core <= deg)
+    for k in range(0, int(core.max()) + 2):
+        inc, _ = oracle.kcore(g.offsets, g.indices, k)
+        assert np.array_equal(inc.astype(bool), core >= k), k
+    u = np.repeat(np.arange(g.n), deg)
+    strong = np.bincount(u, weights=(core[g.indices] >= core[u]), minlength=g.n)
+    assert np.all(strong >= core)
+
+
 # ----------------------------------------------------------------- PageRank
 def pagerank_dense(g, d):
     """Fixed point of the PageRank map by a dense FP64 linear solve."""
