@@ -31,6 +31,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -207,16 +208,25 @@ def measured_peaks():
 KERNEL_FILES = {"coreness_kernel": "kcore.cu", "wcc_kernel": "sssp.cu"}  # kernels not in <algorithm>.cu
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and with whitespace runs collapsed, so
+    that editing a comment does not count as changing a kernel."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(kernel: str) -> str:
-    """Hash of the sources a kernel is built from: its own file
-    (<algorithm>.cu for <algorithm>_kernel) and the shared device headers."""
+    """Hash of the code a kernel is built from (comments and layout
+    ignored): its own file (<algorithm>.cu for <algorithm>_kernel) and the
+    shared device headers."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1812_04070_gb300", "csrc")
     own = KERNEL_FILES.get(kernel, kernel.replace("_kernel", "") + ".cu")
     for fn in [own, "acc_device.cuh", "simdx_internal.h"]:
-        with open(os.path.join(csrc, fn), "rb") as f:
+        with open(os.path.join(csrc, fn), encoding="utf-8") as f:
             h.update(fn.encode())
-            h.update(f.read())
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

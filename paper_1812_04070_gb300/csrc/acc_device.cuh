@@ -36,7 +36,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kClasses = 4;  // 0 thread, 1 warp, 2 CTA, 3 grid
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBallotChunk = kThreads * 32;  // vertices per ballot-filter chunk
+constexpr int kBallotChunk = kThreads * 32;  // largest ballot-filter chunk (vertices)
 constexpr int kTraceWords = 8;                // int64 words per trace record
 constexpr int kChunkBatch = kThreads * 4;     // class-3 tasks per chunk-prefix batch
 

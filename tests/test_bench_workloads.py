@@ -61,3 +61,11 @@ def test_traffic_records_name_existing_summaries():
         assert workload in bench.WORKLOADS, key
         assert os.path.exists(os.path.join(ROOT, rec["summary"])), key
         assert rec["bytes_per_launch"] > 0 and len(rec["source_hash"]) == 16
+
+
+def test_kernel_hash_ignores_comments_only():
+    a = "__global__ void k(int* p) { p[0] = 1; }  // store\n"
+    b = "/* the kernel */\n__global__ void k(int* p) {\n  p[0] = 1;\n}\n"
+    c = "__global__ void k(int* p) { p[0] = 2; }\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
