@@ -384,9 +384,11 @@ SIMDX_API int simdx_autotune(simdx_graph *g, int32_t algo, int64_t arg, int32_t 
  * lists, online-filter bins, bitmaps, barrier words) lives in one fixed
  * device array of about 15 MB that every GPU loading the library holds until
  * the process exits.
- *   csr     device CSR of a symmetric graph (offsets int32/int64, indices
- *           int32), 1 <= n <= 262144 (2^18) vertices; larger graphs fail
- *           with SIMDX_EINVAL.  The CSR is checked first (synchronously).
+ *   csr     device CSR of out-edges (offsets int32/int64, indices int32),
+ *           symmetric or directed, 1 <= n <= 262144 (2^18) vertices; larger
+ *           graphs fail with SIMDX_EINVAL.  Every level is a push level (only
+ *           out-edges are read), so no in-edge array is needed.  The CSR is
+ *           checked first: the call waits on `stream` for that check.
  *   src     source vertex; levels: device int32[n], written as simdx_bfs
  *           writes it (hop distance, -1 if unreachable).
  * The first call on a device looks up the scratch address on that device

@@ -147,7 +147,9 @@ extern "C" int simdx_bfs_noalloc(const simdx_csr* csr, int32_t src, int32_t* lev
   k.med_max = cfg.med_max;
   k.huge_min = cfg.huge_min;
   k.bin_cap = kBinCap;
-  k.direction = 0;
+  // push only: a push level reads out-edges alone, so a directed CSR gives
+  // the same levels as a symmetric one (no in-edge array is passed here)
+  k.direction = 1;
   k.filter = 0;
   k.alpha = cfg.alpha;
   k.beta = cfg.beta;
