@@ -19,6 +19,9 @@ GPUs"), cited per function in ``oracle.c``:
 * ``pagerank``   -- Sec. 6 "PageRank", FP64 Jacobi pull iteration (readings of
                     the unstated teleport, dangling and stop rules: see the
                     function docstring).
+* ``bfs_par``, ``kcore_par``, ``pagerank_par`` -- the same results computed
+                    with OpenMP on every host core, only to time the CPU
+                    baseline; pinned equal to the single-threaded functions.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` against brute force, closed forms or invariants.
@@ -41,11 +44,16 @@ UNREACHED_DIST = 0xFFFFFFFF
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so in place (gcc -O2, single-threaded)."""
+    """Compile liboracle.so in place (gcc -O2).  The definitions are
+    single-threaded; only the ``*_par`` timing variants use OpenMP, and the
+    library is built without it (those variants then run on one thread) if
+    the compiler has no OpenMP runtime."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                               "-fvisibility=hidden", _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=gnu11", "-fvisibility=hidden", _SRC, "-o", tmp]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -70,6 +78,14 @@ def _load():
         lib.or_wcc.restype = ctypes.c_int
         lib.or_pagerank.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, i64, vp, vp]
         lib.or_pagerank.restype = i64
+        lib.or_bfs_par.argtypes = [i64, vp, vp, i32, vp]
+        lib.or_bfs_par.restype = ctypes.c_int
+        lib.or_kcore_par.argtypes = [i64, vp, vp, u32, vp, vp]
+        lib.or_kcore_par.restype = ctypes.c_int
+        lib.or_pagerank_par.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, i64, vp, vp]
+        lib.or_pagerank_par.restype = i64
+        lib.or_threads.argtypes = []
+        lib.or_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -163,4 +179,45 @@ def pagerank(in_off, in_idx, outdeg=None, d: float = 0.85, tol: float = 1e-6,
     l1 = ctypes.c_double(0.0)
     it = _load().or_pagerank(n, off.ctypes.data, ip, od.ctypes.data, float(d), float(tol),
                              int(max_iter), int(fixed_iter), x.ctypes.data, ctypes.byref(l1))
+    return x[:n], int(it), float(l1.value)
+
+
+# ------------------------------------------------ parallel timing variants
+def threads() -> int:
+    """Threads the ``*_par`` variants run on (OpenMP's default team size)."""
+    return int(_load().or_threads())
+
+
+def bfs_par(off, idx, src: int) -> np.ndarray:
+    """``bfs`` computed level-synchronously on all host cores."""
+    off, idx, ip = _csr(off, idx)
+    n = off.size - 1
+    lev = np.empty(n, dtype=np.int32)
+    if _load().or_bfs_par(n, off.ctypes.data, ip, int(src), lev.ctypes.data) != 0:
+        raise ValueError("source out of range")
+    return lev
+
+
+def kcore_par(off, idx, k: int):
+    """``kcore`` computed by level-synchronous peeling on all host cores."""
+    off, idx, ip = _csr(off, idx)
+    n = off.size - 1
+    inc = np.empty(n, dtype=np.uint8)
+    res = np.empty(n, dtype=np.uint32)
+    _load().or_kcore_par(n, off.ctypes.data, ip, int(k), inc.ctypes.data, res.ctypes.data)
+    return inc, res
+
+
+def pagerank_par(in_off, in_idx, outdeg=None, d: float = 0.85, tol: float = 1e-6,
+                 max_iter: int = 1000, fixed_iter: int = -1):
+    """``pagerank`` with each iteration's per-vertex pulls on all host cores
+    (same values bit for bit)."""
+    off, idx, ip = _csr(in_off, in_idx)
+    n = off.size - 1
+    od = np.diff(off) if outdeg is None else np.asarray(outdeg)
+    od = np.ascontiguousarray(od, dtype=np.int64)
+    x = np.empty(max(n, 1), dtype=np.float64)
+    l1 = ctypes.c_double(0.0)
+    it = _load().or_pagerank_par(n, off.ctypes.data, ip, od.ctypes.data, float(d), float(tol),
+                                 int(max_iter), int(fixed_iter), x.ctypes.data, ctypes.byref(l1))
     return x[:n], int(it), float(l1.value)

@@ -343,3 +343,157 @@ OR_EXPORT int64_t or_pagerank(int64_t n, const int64_t *in_off,
     free(y);
     return t;
 }
+
+/* ------------------------------------------- parallel timing variants */
+/* The same results as or_bfs, or_kcore and or_pagerank, computed with
+ * OpenMP on every core the process may use.  They exist only to time the
+ * CPU baseline on all host cores; tests pin each one equal, element for
+ * element, to its single-threaded definition above.  Built without OpenMP
+ * they run on one thread and give the same results. */
+
+/* Level-synchronous BFS: every vertex of level L offers L+1 to its
+ * neighbours; the first offer to an unvisited vertex claims it with a
+ * compare-and-swap and appends it to level L+1.  Levels are unique, so the
+ * result equals or_bfs. */
+OR_EXPORT int or_bfs_par(int64_t n, const int64_t *off, const int32_t *idx,
+                         int32_t src, int32_t *level)
+{
+    if (src < 0 || src >= n) return 1;
+    int32_t *cur = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < n; ++v) level[v] = -1;
+    level[src] = 0;
+    cur[0] = src;
+    int64_t ncur = 1;
+    int32_t L = 0;
+    while (ncur > 0) {
+        int64_t nnext = 0;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < ncur; ++i) {
+            int32_t v = cur[i];
+            for (int64_t p = off[v]; p < off[v + 1]; ++p) {
+                int32_t u = idx[p];
+                int32_t expect = -1;
+                if (__atomic_load_n(&level[u], __ATOMIC_RELAXED) == -1 &&
+                    __atomic_compare_exchange_n(&level[u], &expect, L + 1, 0, __ATOMIC_RELAXED,
+                                                __ATOMIC_RELAXED)) {
+                    int64_t slot = __atomic_fetch_add(&nnext, 1, __ATOMIC_RELAXED);
+                    nxt[slot] = u;
+                }
+            }
+        }
+        int32_t *t = cur; cur = nxt; nxt = t;
+        ncur = nnext;
+        ++L;
+    }
+    free(cur);
+    free(nxt);
+    return 0;
+}
+
+/* k-core by level-synchronous peeling: the degrees are counted in parallel;
+ * each round deletes the vertices that fell below k in the previous round
+ * and decrements their surviving neighbours atomically; the decrement that
+ * takes a neighbour from k to k-1 enqueues it.  The surviving set is the
+ * unique maximal subgraph of minimum degree >= k, so the result equals
+ * or_kcore. */
+OR_EXPORT int or_kcore_par(int64_t n, const int64_t *off, const int32_t *idx,
+                           uint32_t k, uint8_t *in_core, uint32_t *resid)
+{
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *cur = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t ncur = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < n; ++v) {
+        deg[v] = off[v + 1] - off[v];
+        in_core[v] = deg[v] >= (int64_t)k;
+        if (!in_core[v]) {
+            int64_t slot = __atomic_fetch_add(&ncur, 1, __ATOMIC_RELAXED);
+            cur[slot] = (int32_t)v;
+        }
+    }
+    while (ncur > 0) {
+        int64_t nnext = 0;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < ncur; ++i) {
+            int32_t v = cur[i];
+            for (int64_t p = off[v]; p < off[v + 1]; ++p) {
+                int32_t u = idx[p];
+                if (!__atomic_load_n(&in_core[u], __ATOMIC_RELAXED)) continue;
+                if (__atomic_fetch_sub(&deg[u], 1, __ATOMIC_RELAXED) == (int64_t)k) {
+                    __atomic_store_n(&in_core[u], 0, __ATOMIC_RELAXED);
+                    int64_t slot = __atomic_fetch_add(&nnext, 1, __ATOMIC_RELAXED);
+                    nxt[slot] = u;
+                }
+            }
+        }
+        int32_t *t = cur; cur = nxt; nxt = t;
+        ncur = nnext;
+    }
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t v = 0; v < n; ++v) {
+        uint32_t c = 0;
+        if (in_core[v])
+            for (int64_t p = off[v]; p < off[v + 1]; ++p) c += in_core[idx[p]];
+        if (resid) resid[v] = c;
+    }
+    free(deg);
+    free(cur);
+    free(nxt);
+    return 0;
+}
+
+/* PageRank as or_pagerank, with the per-vertex pulls of an iteration run in
+ * parallel (each vertex sums its in-edges in the same order as there); the
+ * dangling mass and the L1 change are summed in vertex order on one thread,
+ * so every value equals or_pagerank's bit for bit. */
+OR_EXPORT int64_t or_pagerank_par(int64_t n, const int64_t *in_off,
+                                  const int32_t *in_idx, const int64_t *outdeg,
+                                  double d, double tol, int64_t max_iter,
+                                  int64_t fixed_iter, double *x_out, double *l1_out)
+{
+    if (n == 0) return 0;
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int64_t v = 0; v < n; ++v) x[v] = 1.0 / (double)n;
+    int64_t t = 0;
+    double l1 = 0.0;
+    int64_t limit = fixed_iter >= 0 ? fixed_iter : max_iter;
+    while (t < limit) {
+        double dangling = 0.0;
+        for (int64_t u = 0; u < n; ++u)
+            if (outdeg[u] == 0) dangling += x[u];
+#pragma omp parallel for schedule(dynamic, 1024)
+        for (int64_t v = 0; v < n; ++v) {
+            double s = 0.0;
+            for (int64_t p = in_off[v]; p < in_off[v + 1]; ++p) {
+                int32_t u = in_idx[p];
+                s += x[u] / (double)outdeg[u];
+            }
+            y[v] = (1.0 - d) / (double)n + d * (s + dangling / (double)n);
+        }
+        l1 = 0.0;
+        for (int64_t v = 0; v < n; ++v) l1 += fabs(y[v] - x[v]);
+        double *tmp = x; x = y; y = tmp;
+        ++t;
+        if (fixed_iter < 0 && l1 < tol) break;
+    }
+    memcpy(x_out, x, sizeof(double) * (size_t)n);
+    if (l1_out) *l1_out = l1;
+    free(x);
+    free(y);
+    return t;
+}
+
+/* Threads the parallel variants use (1 when built without OpenMP). */
+OR_EXPORT int or_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -69,3 +69,32 @@ def test_kernel_hash_ignores_comments_only():
     c = "__global__ void k(int* p) { p[0] = 2; }\n"
     assert bench._code_only(a) == bench._code_only(b)
     assert bench._code_only(a) != bench._code_only(c)
+
+
+def test_inspected_bytes_and_defaults():
+    class St:
+        edges_visited = 1000
+    assert bench.inspected_bytes("bfs", 64, St, 10) == 4 * 1000 + 28 * 10
+    assert bench.inspected_bytes("sssp", 32, St, 10) == 8 * 1000 + 20 * 10
+    assert bench.inspected_bytes("pagerank", 32, St, 10) is None
+    assert set(bench.BYTES_BASIS) >= {"bfs", "sssp", "kcore", "coreness", "wcc", "pagerank"}
+    # the headline configuration is the default line
+    import sys as _s
+    argv, _s.argv = _s.argv, ["bench.py"]
+    try:
+        assert bench.parse().workload == "rmat24-bfs"
+    finally:
+        _s.argv = argv
+
+
+def test_cpu_leg_parallel_and_serial_agree_on_work():
+    g = gg.rmat(10)
+    w = gg.weights(g, 1, 1, 64)
+    bench.WORKLOADS["_tiny"] = dict(kind="rmat", scale=10, bits=32, algs=["bfs", "kcore", "pagerank"], desc="")
+    try:
+        a = bench.cpu_leg("_tiny", g, w, 0.0, parallel=True)
+        b = bench.cpu_leg("_tiny", g, w, 0.0, parallel=False)
+    finally:
+        del bench.WORKLOADS["_tiny"]
+    assert a["cores"] == oracle.threads() and b["cores"] == 1
+    assert a["value"] > 0 and b["value"] > 0 and "OpenMP" in a["sample"]

@@ -429,3 +429,27 @@ def test_pagerank_stop_rule():
     _, _, l1_prev = oracle.pagerank(g.offsets, g.indices, fixed_iter=it - 1)
     assert l1_prev >= 1e-6
     assert abs(x.sum() - 1) < 1e-9
+
+
+# ------------------------------------------------- parallel timing variants
+# The OpenMP variants time the CPU baseline on every host core.  Each must
+# give the single-threaded definition's result element for element (they are
+# pinned through it, not through themselves).
+PAR_GRAPHS = [lambda: gg.path(1), lambda: gg.path(50), lambda: gg.star(40), lambda: gg.complete(9),
+              lambda: gg.grid(37, 23), lambda: gg.from_edges(10, [0, 1, 5, 6], [1, 2, 6, 7]),
+              lambda: gg.random_graph(900, 5000, seed=7), lambda: gg.rmat(13)]
+
+
+@pytest.mark.parametrize("gi", range(len(PAR_GRAPHS)))
+def test_parallel_variants_equal_definitions(gi):
+    g = PAR_GRAPHS[gi]()
+    deg = g.degrees()
+    for s in sorted({0, g.n - 1, int(np.argmax(deg))}):
+        assert np.array_equal(oracle.bfs_par(g.offsets, g.indices, s), oracle.bfs(g.offsets, g.indices, s))
+    for k in (0, 1, 2, 3, 5, 16):
+        a, b = oracle.kcore(g.offsets, g.indices, k), oracle.kcore_par(g.offsets, g.indices, k)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for kw in (dict(fixed_iter=7), dict(tol=1e-9)):
+        a, b = oracle.pagerank(g.offsets, g.indices, **kw), oracle.pagerank_par(g.offsets, g.indices, **kw)
+        assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
+    assert oracle.threads() >= 1
