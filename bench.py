@@ -81,6 +81,13 @@ WORKLOADS = {
                          desc="4096x4096 4-neighbour grid: BFS from corner 0"),
     "grid4096-sssp": dict(kind="grid", rows=4096, bits=64, algs=["sssp"], wmax=1000,
                           desc="4096x4096 4-neighbour grid, w in [1,1000]: SSSP from corner 0"),
+    "grid4096-ablation": dict(kind="ablation", graph="grid", rows=4096, bits=64, algs=["bfs", "sssp"],
+                              wmax=1000,
+                              desc="4096x4096 4-neighbour grid (w in [1,1000]), BFS / SSSP from corner 0: all, "
+                                   "selective and no kernel fusion (Sec. 5, Table 2); JIT vs ballot-only filter"),
+    "rmat24-ablation": dict(kind="ablation", graph="rmat", scale=24, bits=64, algs=["bfs", "sssp", "kcore"],
+                            desc="R-MAT scale 24, int64 offsets: BFS / SSSP src 0 and k-core 16 under all, "
+                                 "selective and no kernel fusion (BFS, SSSP); JIT vs ballot-only filter (Sec. 4)"),
     "batch22": dict(kind="batch", scale=22, bits=32,
                     desc="R-MAT scale 22 (n=4,194,304, ef 16, w in [1,64]): 64 BFS + 64 SSSP sources uniform over "
                          "non-isolated vertices (seed 0xBA7C4), batched vs one call per query; plus 256 R-MAT "
@@ -137,7 +144,7 @@ def job_rate(units_per_rank: float, seconds: float, world: int) -> float:
 
 def make_graph(wl):
     import graphgen as gg
-    if wl["kind"] == "rmat":
+    if wl["kind"] == "rmat" or wl.get("graph") == "rmat":
         g = gg.rmat(wl["scale"])
         w = gg.weights(g, gg.weight_seed(wl["scale"]), 1, wl.get("wmax", 64))
     else:
@@ -697,6 +704,79 @@ def run_serve(args, rank, world, local):
             "per_query_qps": round(per_query, 1), "rates": rates, "server": info}
 
 
+def run_ablation(args, rank, world, local):
+    """Kernel fusion (Sec. 5, Table 2) and task management (Sec. 4) ablations
+    on one graph: every algorithm under all fusion (one persistent launch),
+    selective push-pull fusion (one launch per run of one direction) and no
+    fusion (one launch per iteration), and under the JIT filter (online,
+    ballot on overflow) against the ballot filter alone.  Times are CUDA
+    events around each call (median of the repetitions, L2 flushed before
+    each); every mode's output is checked equal to the all-fusion JIT run."""
+    import torch
+    from paper_1812_04070_gb300 import Graph, build, simdx_stats
+    torch.cuda.set_device(local)
+    build()
+    wl = WORKLOADS[args.workload]
+    g, w = make_graph(wl)
+    bits = wl["bits"]
+    off = g.offsets if bits == 64 else g.offsets.astype(np.int32)
+    G = Graph(off, g.indices, weights=w)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    out8 = torch.empty(g.n, dtype=torch.uint8, device=dev)
+    reps = max(3, min(args.steps, 7))
+    modes = {"bfs": [(0, 0), (1, 0), (2, 0), (0, 2), (2, 2)], "sssp": [(0, 0), (2, 0), (0, 2), (2, 2)],
+             "kcore": [(0, 0), (0, 2)]}
+
+    def call(a, st=None):
+        if a == "bfs":
+            G.bfs(0, out=out, stats=st)
+        elif a == "sssp":
+            G.sssp(0, out=out, stats=st)
+        else:
+            G.kcore(16, out=out8, want_resid=False, stats=st)
+
+    res = {}
+    for a in wl["algs"]:
+        ref = None
+        rows = []
+        for fusion, filt in modes[a]:
+            G.set_config(fusion=fusion, filter=filt)
+            st = simdx_stats()
+            call(a, st)
+            torch.cuda.synchronize()
+            o = (out8 if a == "kcore" else out).clone()
+            if ref is None:
+                ref = o
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call(a)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            rows.append({"fusion": ["all", "selective", "none"][fusion], "filter": "JIT" if filt == 0 else "ballot",
+                         "ms": round(ms, 3), "iterations": st.iterations, "launches": st.launches,
+                         "us_per_iteration": round(ms * 1e3 / max(1, st.iterations), 2),
+                         "pull_iters": st.pull_iters, "ballot_iters": st.ballot_iters,
+                         "identical": bool(torch.equal(o, ref))})
+        res[a] = rows
+    G.set_config(fusion=0, filter=0)
+    G.close()
+    base = res[wl["algs"][0]][0]
+    return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],
+            "unit": "us", "n_gpus": world, "steps": reps, "warmup": 1, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded R-MAT / grid)",
+            "config": {"workload": args.workload, "description": wl["desc"], "n": g.n, "directed_edges": g.e,
+                       "l2": "flushed before every timed call"},
+            "ablation": res}
+
+
 # ------------------------------------------------------------ CPU oracle legs
 def cpu_leg(workload, g, w, budget_s, parallel):
     """The oracle on a bounded sample of the workload, repeated until about
@@ -789,6 +869,8 @@ def main():
         res = run_reference(args, rank, world)
     elif WORKLOADS[args.workload]["kind"] == "batch":
         res = run_batch(args, rank, world, local)
+    elif WORKLOADS[args.workload]["kind"] == "ablation":
+        res = run_ablation(args, rank, world, local)
     elif WORKLOADS[args.workload]["kind"] == "serve":
         res = run_serve(args, rank, world, local)
     else:

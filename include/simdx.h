@@ -103,7 +103,10 @@ typedef struct {
     int64_t edges_visited;   /* edge entries read by compute                */
     int64_t frontier_sum;    /* sum over iterations of active vertices      */
     double last_l1;          /* PageRank: L1 change of the last iteration   */
-    int64_t reserved[4];
+    int32_t launches;        /* kernel launches the call made (fusion knob,
+                                batch groups, WCC's two launches)           */
+    int32_t reserved32;
+    int64_t reserved[3];
 } simdx_stats;
 
 /* Tuning knobs (defaults in brackets).  Every knob changes speed only, never
@@ -133,7 +136,18 @@ typedef struct {
     int32_t debug_skip_phase;
     int32_t batch_group;     /* simdx_sssp_batch: copies per persistent launch; 0 = as many
                                 as keep one launch's distances within 128 MB [0] */
-    int32_t reserved[7];
+    int32_t fusion;          /* simdx_bfs / simdx_sssp kernel fusion (Sec. 5, Table 2) [0]:
+                                0 all fusion: every iteration in one persistent launch;
+                                1 selective (push-pull) fusion: one launch per run of
+                                consecutive iterations in one direction, each from a kernel
+                                compiled for that direction alone (BFS: push, pull, push =
+                                3 launches; SSSP computes in one direction, so 1 launch);
+                                2 no fusion: one launch per iteration.  Modes 1 and 2 wait
+                                on the stream between launches (the host reads whether the
+                                run finished and which direction comes next), so they
+                                cannot be captured (EUNSUPPORTED while capturing).  Results
+                                are identical in every mode. */
+    int32_t reserved[6];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;

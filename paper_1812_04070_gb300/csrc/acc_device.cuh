@@ -53,6 +53,18 @@ struct PhaseSlot {
   unsigned long long tclass[kClasses];  // max over CTAs of each class's duration (ns)
 };
 
+// Loop state a launch leaves for the next launch of the same run when it
+// stops early (selective fusion: at a change of direction; no fusion: after
+// every iteration).  The host reads `done` and `want_dir` between launches.
+constexpr int kResumeWords = 32;
+struct Resume {
+  int active;                   // the words below continue a run
+  int done;                     // the run has finished
+  int want_dir;                 // direction of the next iteration (1 push, 2 pull)
+  int pad;
+  long long v[kResumeWords];    // algorithm loop state
+};
+
 struct Sync {
   unsigned long long arrive;    // monotonic barrier arrival counter
   int abort;                    // a wait ran out somewhere
@@ -60,6 +72,7 @@ struct Sync {
   unsigned long long evisit;    // edges read by compute (statistics)
   unsigned long long pad[13];   // the polled words alone on their 128-byte line
   PhaseSlot slot[3];
+  Resume rs;
 };
 
 struct DevStats {
@@ -77,6 +90,8 @@ struct Knobs {
   unsigned delta;
   unsigned long long timeout_ns;
   int skip_cta, skip_phase;
+  int fusion;           // 0 all iterations in one launch, 1 one launch per run of one
+                        // direction, 2 one launch per iteration (Sec. 5, Table 2)
 };
 
 // Workspace shared by all algorithms of one graph.

@@ -324,8 +324,20 @@ __device__ void bfs_pull_big(const BfsArgs<OffT>& a, int cur, const uint32_t* fb
   }
 }
 
-template <class OffT>
+// Loop state words of the resume record (Resume::v) for a run split over
+// several launches.
+enum { kRsL, kRsLbuf, kRsFb, kRsListsOk, kRsBmOk, kRsPrevDir, kRsCnt0, kRsNf = kRsCnt0 + kClasses, kRsPrevNf,
+       kRsMf, kRsMu, kRsIt, kRsPushIt, kRsPullIt, kRsBallotIt, kRsOnlineIt, kRsFsum, kRsPhases };
+static_assert(kRsPhases < kResumeWords, "resume record too small");
+
+// DIRS: the directions this instantiation computes (kPush | kPull for the
+// all-fusion kernel; kPush or kPull alone for the kernels of selective and
+// no fusion, which stop when the next iteration needs the other direction).
+template <class OffT, int DIRS = kPush | kPull>
 __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
+  constexpr bool kHasPush = (DIRS & kPush) != 0;
+  constexpr bool kHasPull = (DIRS & kPull) != 0;
+  constexpr bool kSplit = DIRS != (kPush | kPull);  // runs may span several launches
   __shared__ CtaShared sh;
   __shared__ PullShared ps;
   const unsigned grid = gridDim.x;
@@ -337,45 +349,49 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   const long long gthreads = (long long)grid * kThreads;
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
+  // a launch that continues a run split over several launches skips the set-up
+  const bool resumed = kSplit && ld_volatile_i32(&s->rs.active) != 0;
 
   // ---- phase 0: reset levels and bitmaps; seed the first task list
   const int src1 = a.nroots > 0 ? -1 : a.src;
-  for (long long v = gtid; v < n; v += gthreads) a.level[v] = (v == src1) ? 0 : -1;
-  for (long long wd = gtid; wd < nwords; wd += gthreads) {
-    unsigned m = (src1 >= 0 && wd == (src1 >> 5)) ? (1u << (src1 & 31)) : 0u;
-    a.w.bm_vis[wd] = m;
-    a.w.bm_f[0][wd] = m;
-  }
-  if (src1 >= 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    long long d = (long long)a.off[src1 + 1] - (long long)a.off[src1];
-    int c = degree_class(d, k);
-    a.w.list[0][c][0] = src1;
-    if (c == 3) a.w.aux3[0][0] = 0xffffffffu;
-    s->slot[0].list_cnt[c] = 1;
-    s->slot[0].nact = 1;
-    s->slot[0].mact = (unsigned long long)d;
-  }
-  clear_next_slot(s, sh);
-  if (!grid_sync(s, grid, sh, k)) return;
-  if (a.nroots > 0) {
-    // several roots at level 0 (e.g. one per graph of a block-diagonal batch)
+  if (!resumed) {
+    for (long long v = gtid; v < n; v += gthreads) a.level[v] = (v == src1) ? 0 : -1;
+    for (long long wd = gtid; wd < nwords; wd += gthreads) {
+      unsigned m = (src1 >= 0 && wd == (src1 >> 5)) ? (1u << (src1 & 31)) : 0u;
+      a.w.bm_vis[wd] = m;
+      a.w.bm_f[0][wd] = m;
+    }
+    if (src1 >= 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+      long long d = (long long)a.off[src1 + 1] - (long long)a.off[src1];
+      int c = degree_class(d, k);
+      a.w.list[0][c][0] = src1;
+      if (c == 3) a.w.aux3[0][0] = 0xffffffffu;
+      s->slot[0].list_cnt[c] = 1;
+      s->slot[0].nact = 1;
+      s->slot[0].mact = (unsigned long long)d;
+    }
     clear_next_slot(s, sh);
-    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-    if (blockIdx.x == 0)
-      for (int i = threadIdx.x; i < a.nroots; i += kThreads) {
-        const int r = a.roots[i];
-        if (atomicExch(&a.level[r], 0) == 0) continue;  // duplicate root
-        atomicOr(&a.w.bm_vis[r >> 5], 1u << (r & 31));
-        atomicOr(&a.w.bm_f[0][r >> 5], 1u << (r & 31));
-        const long long d = (long long)a.off[r + 1] - (long long)a.off[r];
-        const int c = degree_class(d, k);
-        const unsigned pos = atomicAdd(&slot.list_cnt[c], 1u);
-        a.w.list[0][c][pos] = r;
-        if (c == 3) a.w.aux3[0][pos] = 0xffffffffu;
-        atomicAdd(&slot.nact, 1ull);
-        atomicAdd(&slot.mact, (unsigned long long)d);
-      }
     if (!grid_sync(s, grid, sh, k)) return;
+    if (a.nroots > 0) {
+      // several roots at level 0 (e.g. one per graph of a block-diagonal batch)
+      clear_next_slot(s, sh);
+      PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+      if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < a.nroots; i += kThreads) {
+          const int r = a.roots[i];
+          if (atomicExch(&a.level[r], 0) == 0) continue;  // duplicate root
+          atomicOr(&a.w.bm_vis[r >> 5], 1u << (r & 31));
+          atomicOr(&a.w.bm_f[0][r >> 5], 1u << (r & 31));
+          const long long d = (long long)a.off[r + 1] - (long long)a.off[r];
+          const int c = degree_class(d, k);
+          const unsigned pos = atomicAdd(&slot.list_cnt[c], 1u);
+          a.w.list[0][c][pos] = r;
+          if (c == 3) a.w.aux3[0][pos] = 0xffffffffu;
+          atomicAdd(&slot.nact, 1ull);
+          atomicAdd(&slot.mact, (unsigned long long)d);
+        }
+      if (!grid_sync(s, grid, sh, k)) return;
+    }
   }
 
   // uniform loop state (identical in every CTA)
@@ -394,7 +410,19 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   }
   long long m_u = a.m_total - (long long)m_f;
   int it = 0, push_it = 0, pull_it = 0, ballot_it = 0, online_it = 0;
-  long long evisit = 0, fsum = 0;
+  long long evisit = 0, fsum = 0, phases0 = 0;
+  if (resumed) {
+    const volatile long long* r = s->rs.v;
+    L = (int)r[kRsL]; lbuf = (int)r[kRsLbuf]; fb = (int)r[kRsFb];
+    lists_ok = r[kRsListsOk] != 0; bm_ok = r[kRsBmOk] != 0; prev_dir = (int)r[kRsPrevDir];
+    for (int c = 0; c < kClasses; ++c) cnt[c] = (unsigned)r[kRsCnt0 + c];
+    n_f = (unsigned long long)r[kRsNf]; prev_n_f = (unsigned long long)r[kRsPrevNf];
+    m_f = (unsigned long long)r[kRsMf]; m_u = r[kRsMu];
+    it = (int)r[kRsIt]; push_it = (int)r[kRsPushIt]; pull_it = (int)r[kRsPullIt];
+    ballot_it = (int)r[kRsBallotIt]; online_it = (int)r[kRsOnlineIt]; fsum = r[kRsFsum];
+    phases0 = r[kRsPhases];
+  }
+  const int it_launch = it;  // first iteration of this launch
 
   while (true) {
     const unsigned long long t_it = globaltimer();
@@ -406,8 +434,28 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     else dir = ((double)n_f < (double)n / k.beta && n_f <= prev_n_f) ? kPush : kPull;
     int filt = kOnline;
 
+    // -------- selective / no fusion: leave the loop state to the next launch
+    // when this kernel does not compute `dir`, or after one iteration
+    if (kSplit && ((dir == kPush && !kHasPush) || (dir == kPull && !kHasPull) || (k.fusion == 2 && it > it_launch))) {
+      const unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+      if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long* r = s->rs.v;
+        r[kRsL] = L; r[kRsLbuf] = lbuf; r[kRsFb] = fb; r[kRsListsOk] = lists_ok; r[kRsBmOk] = bm_ok;
+        r[kRsPrevDir] = prev_dir;
+        for (int c = 0; c < kClasses; ++c) r[kRsCnt0 + c] = cnt[c];
+        r[kRsNf] = (long long)n_f; r[kRsPrevNf] = (long long)prev_n_f; r[kRsMf] = (long long)m_f;
+        r[kRsMu] = m_u; r[kRsIt] = it; r[kRsPushIt] = push_it; r[kRsPullIt] = pull_it;
+        r[kRsBallotIt] = ballot_it; r[kRsOnlineIt] = online_it; r[kRsFsum] = fsum;
+        r[kRsPhases] = phases0 + (long long)sh.phase;
+        s->rs.want_dir = dir;
+        s->rs.active = 1;
+      }
+      return;
+    }
+
     // -------- make the frontier representation match the direction
-    if (dir == kPull && !bm_ok) {
+    if (kHasPull && dir == kPull && !bm_ok) {
       // ballot scan of the level array: visited and frontier bitmaps
       clear_next_slot(s, sh);
       const int lane = lane_id();
@@ -426,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       bm_ok = true;
       filt = kBallot;
     }
-    if (dir == kPush && (!lists_ok || k.filter == 2)) {
+    if (kHasPush && dir == kPush && (!lists_ok || k.filter == 2)) {
       clear_next_slot(s, sh);
       PhaseSlot& slot = s->slot[slot_of(sh.phase)];
       const OffT* off = a.off;
@@ -453,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     __syncthreads();
     PhaseSlot& slot = s->slot[slot_of(sh.phase)];
     unsigned long long nrec = 0, mrec = 0;
-    if (dir == kPush) {
+    if (kHasPush && (!kHasPull || dir == kPush)) {
       BfsPush<OffT> f(a.level, a.off, L + 1, sh, a.w, k, grid);
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
@@ -461,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       nrec = f.nrec;
       mrec = f.mrec;
       ++push_it;
-    } else {
+    } else if (kHasPull) {
       bfs_pull<OffT>(a, L, a.w.bm_f[fb], a.w.bm_f[fb ^ 1], sh, ps, grid, slot, a.w.list[lbuf][3],
                      a.w.aux3[lbuf], nrec, mrec, evisit);
       ++pull_it;
@@ -481,9 +529,9 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     unsigned long long nn = p.nact, mm = p.mact;
     bool ovf = p.overflow != 0;
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
-    const unsigned nbig = dir == kPull ? (unsigned)p.aux2 : 0u;
+    const unsigned nbig = (kHasPull && dir == kPull) ? (unsigned)p.aux2 : 0u;
     const unsigned long long t_main = globaltimer();
-    if (nbig > 0) {
+    if (kHasPull && nbig > 0) {
       // grid-wide pull of the high in-degree candidates
       clear_next_slot(s, sh);
       PhaseSlot& slot2 = s->slot[slot_of(sh.phase)];
@@ -532,11 +580,12 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     st.pull_iters = pull_it;
     st.ballot_iters = ballot_it;
     st.online_iters = online_it;
-    st.phases = (int)sh.phase;
+    st.phases = (int)(phases0 + (long long)sh.phase);
     st.grid = (int)grid;
     st.edges_visited = (long long)s->evisit;
     st.frontier_sum = fsum;
     st.last_l1 = 0.0;
+    s->rs.done = 1;
   }
 }
 
@@ -560,13 +609,27 @@ static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* st
   a.m_total = g->e;
   a.w = make_work(g);
   a.k = make_knobs(g);
-  const void* kern = (const void*)bfs_kernel<OffT>;
-  int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
   void* args[] = {&a};
-  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
-  return finish_launch(g, stats, st);
+  if (a.k.fusion == 0) {
+    const void* kern = (const void*)bfs_kernel<OffT>;
+    if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
+    return finish_launch(g, stats, st);
+  }
+  // selective fusion (a launch per run of one direction) or no fusion (a
+  // launch per iteration): kernels compiled for one direction each; the host
+  // learns between launches whether the run ended and which direction is next
+  if (capturing(st)) return SIMDX_EUNSUPPORTED;
+  int want = g->cfg.direction == 2 ? kPull : kPush;
+  for (int launch = 0;; ++launch) {
+    const void* kern = want == kPull ? (const void*)bfs_kernel<OffT, kPull> : (const void*)bfs_kernel<OffT, kPush>;
+    if (launch > 0 && (rc = prepare_resume(g, st)) != SIMDX_OK) return rc;
+    if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
+    int done = 0;
+    if ((rc = read_resume(g, st, &done, &want)) != SIMDX_OK) return rc;
+    if (done) return finish_launch(g, stats, st, launch + 1);
+  }
 }
 
 template <class OffT>
@@ -582,6 +645,7 @@ static int launch_bfs_only(simdx_graph* g, int32_t src, int32_t* levels, cudaStr
   a.m_total = g->e;
   a.w = make_work(g);
   a.k = make_knobs(g);
+  a.k.fusion = 0;  // one launch, bracketed by the caller
   const void* kern = (const void*)bfs_kernel<OffT>;
   void* args[] = {&a};
   return launch_coop(kern, grid_for(g, kern), args, st);

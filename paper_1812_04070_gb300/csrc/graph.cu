@@ -103,6 +103,7 @@ Knobs make_knobs(const simdx_graph* g) {
   k.timeout_ns = (unsigned long long)(c.barrier_timeout_ms > 0 ? c.barrier_timeout_ms : 2000) * 1000000ull;
   k.skip_cta = c.debug_skip_cta;
   k.skip_phase = c.debug_skip_phase;
+  k.fusion = c.fusion;
   return k;
 }
 
@@ -162,8 +163,25 @@ int prepare_launch(simdx_graph* g, cudaStream_t st) {
 int prepare_next_launch(simdx_graph* g, cudaStream_t st) {
   char* sy = reinterpret_cast<char*>(g->sync);
   SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, arrive), 0, sizeof(unsigned long long), st));
-  SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, slot), 0, sizeof(PhaseSlot) * 3, st));
+  SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, slot), 0, sizeof(PhaseSlot) * 3 + sizeof(Resume), st));
   SIMDX_CUDA(cudaMemsetAsync(g->chunk_done, 0, sizeof(int) * (size_t)(g->n + 16), st));
+  return SIMDX_OK;
+}
+
+int prepare_resume(simdx_graph* g, cudaStream_t st) {
+  char* sy = reinterpret_cast<char*>(g->sync);
+  SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, arrive), 0, sizeof(unsigned long long), st));
+  SIMDX_CUDA(cudaMemsetAsync(sy + offsetof(Sync, slot), 0, sizeof(PhaseSlot) * 3, st));
+  return SIMDX_OK;
+}
+
+int read_resume(simdx_graph* g, cudaStream_t st, int* done, int* want_dir) {
+  SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->rs_done, &g->sync->rs.done, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                             st));
+  SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->err, &g->sync->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SIMDX_CUDA(cudaStreamSynchronize(st));
+  *done = g->h_stats->rs_done || g->h_stats->err;
+  *want_dir = g->h_stats->rs_want;
   return SIMDX_OK;
 }
 
@@ -193,6 +211,7 @@ bool capturing(cudaStream_t st) {
 struct PendingStats {
   simdx_graph* g;
   simdx_stats* user;
+  int launches;
 };
 
 static void CUDART_CB stats_cb(void* p) {
@@ -211,16 +230,17 @@ static void CUDART_CB stats_cb(void* p) {
   u->edges_visited = d.edges_visited;
   u->frontier_sum = d.frontier_sum;
   u->last_l1 = d.last_l1;
+  u->launches = ps->launches;
   delete ps;
 }
 
-int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st) {
+int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st, int launches) {
   SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->ds, g->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
   SIMDX_CUDA(cudaMemcpyAsync(&g->h_stats->err, &g->sync->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (user) {
     // the host callback owns a one-shot record: a captured graph would replay it
     if (capturing(st)) return SIMDX_EUNSUPPORTED;
-    PendingStats* ps = new (std::nothrow) PendingStats{g, user};
+    PendingStats* ps = new (std::nothrow) PendingStats{g, user, launches};
     if (!ps) return SIMDX_ENOMEM;
     cudaError_t e = cudaLaunchHostFunc(st, stats_cb, ps);
     if (e != cudaSuccess) {
@@ -562,7 +582,8 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
   if (cfg->small_max < 1 || cfg->med_max < cfg->small_max || cfg->huge_min < cfg->med_max ||
       cfg->bin_per_thread < 0 || cfg->bin_per_thread > 4096 || cfg->direction < 0 ||
       cfg->direction > 2 || (cfg->filter != 0 && cfg->filter != 2) || !(cfg->alpha > 0.f) ||
-      !(cfg->beta > 0.f) || !(cfg->kcore_alpha > 0.f) || cfg->ctas_per_sm < 0 || cfg->batch_group < 0)
+      !(cfg->beta > 0.f) || !(cfg->kcore_alpha > 0.f) || cfg->ctas_per_sm < 0 || cfg->batch_group < 0 ||
+      cfg->fusion < 0 || cfg->fusion > 2)
     return SIMDX_EINVAL;
   bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
                     cfg->huge_min != g->cfg.huge_min;

@@ -16,6 +16,7 @@ namespace simdx {
 struct HostStage {
   DevStats ds;
   int err;
+  int rs_done, rs_want;  // Resume::done / want_dir of the last launch (split runs)
   int pad;
   int status() const { return err ? err : ds.status; }
 };
@@ -93,6 +94,12 @@ int prepare_launch(simdx_graph* g, cudaStream_t st);
 // record carry over (a launch after a failed one returns at its first
 // barrier, and the error stays reported).
 int prepare_next_launch(simdx_graph* g, cudaStream_t st);
+// Between the launches of a run split over several launches (fusion knob):
+// a fresh barrier and phase slots, the resume record kept.
+int prepare_resume(simdx_graph* g, cudaStream_t st);
+// Wait for the stream, then report whether the run finished (or failed) and
+// the direction its next launch must compute.
+int read_resume(simdx_graph* g, cudaStream_t st, int* done, int* want_dir);
 // The BFS kernel from src into levels, on the graph's workspace, with no
 // preparation or stats (the caller brackets it).
 int bfs_launch_only(simdx_graph* g, int32_t src, int32_t* levels, cudaStream_t st);
@@ -101,8 +108,9 @@ int bfs_launch_only(simdx_graph* g, int32_t src, int32_t* levels, cudaStream_t s
 int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st);
 
 // Enqueue the copy of device statistics into `user` (may be NULL; must be
-// NULL while `st` is being captured into a CUDA graph).
-int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st);
+// NULL while `st` is being captured into a CUDA graph); `launches` = kernel
+// launches the call made.
+int finish_launch(simdx_graph* g, simdx_stats* user, cudaStream_t st, int launches = 1);
 
 // Whether `st` is being captured into a CUDA graph.
 bool capturing(cudaStream_t st);

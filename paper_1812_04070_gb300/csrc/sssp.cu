@@ -226,7 +226,15 @@ constexpr unsigned long long kDenseDiv = 16;
 // vote for them is the same).  The other vertices start with their own id
 // and propagate the minimum (relaxations add no weight, no buckets), so the
 // fixed point labels each component with its smallest id.
-template <class OffT, bool V, bool PULL, bool W = false>
+// Loop state words of the resume record (Resume::v) for a run with one
+// launch per iteration.
+enum { kRsT, kRsLbuf, kRsCnt0, kRsListsOk = kRsCnt0 + kClasses, kRsMf, kRsScanAll, kRsIt, kRsBallotIt,
+       kRsOnlineIt, kRsPullIt, kRsFsum, kRsPhases };
+static_assert(kRsPhases < kResumeWords, "resume record too small");
+
+// SPLIT: the no-fusion instantiation, which stops after one iteration and
+// leaves its loop state in the resume record for the next launch.
+template <class OffT, bool V, bool PULL, bool W = false, bool SPLIT = false>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
   __shared__ unsigned red_u[kWarps];
@@ -242,6 +250,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
   const unsigned long long kInfT = ~0ull;
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
+  const bool resumed = SPLIT && ld_volatile_i32(&s->rs.active) != 0;
 
   const unsigned nreal = (unsigned)a.nreal;
   // state id -> vertex of the one CSR
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       pend[x] = (!reached && edges) ? 1 : 0;
     }
   }
-  for (long long x = gtid; !W && x < n; x += gthreads) {
+  for (long long x = gtid; !W && !resumed && x < n; x += gthreads) {
     bool is_src;
     if (V) {
       const long long inst = x / nreal;
@@ -289,12 +298,12 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     pdist[x] = 0xffffffffu;
     pend[x] = is_src ? 1 : 0;  // the source is the first pending vertex
   }
-  if (PULL)  // pull frontiers (BFS leaves these bitmaps as it likes)
+  if (PULL && !resumed)  // pull frontiers (BFS leaves these bitmaps as it likes)
     for (long long q = gtid; q < (((long long)n + 31) >> 5); q += gthreads) {
       a.w.bm_f[0][q] = 0u;
       a.w.bm_f[1][q] = 0u;
     }
-  if (!W && blockIdx.x == 0) {
+  if (!W && !resumed && blockIdx.x == 0) {
     const int nsrc = V ? a.ninst : 1;
     for (int i = threadIdx.x; i < nsrc; i += kThreads) {
       const int v = V ? (a.ninst <= 64 ? a.src_list[i] : a.srcs[i]) : a.src;
@@ -305,8 +314,10 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       if (c == 3) a.w.aux3[0][pos] = 0xffffffffu;
     }
   }
-  clear_next_slot(s, sh);
-  if (!grid_sync(s, grid, sh, k)) return;
+  if (!resumed) {
+    clear_next_slot(s, sh);
+    if (!grid_sync(s, grid, sh, k)) return;
+  }
 
   unsigned long long T = delta ? delta : kInfT;  // bucket bound: process dist < T
   int lbuf = 0;
@@ -325,8 +336,34 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       (unsigned long long)(gload(a.off + nreal) - gload(a.off)) * (unsigned long long)(V ? a.ninst : 1);
   unsigned long long mf = 0;  // out-edges of the current task lists
   bool scan_all = false;
+  long long phases0 = 0;
+  if (resumed) {
+    const volatile long long* r = s->rs.v;
+    T = (unsigned long long)r[kRsT]; lbuf = (int)r[kRsLbuf];
+    for (int c = 0; c < kClasses; ++c) cnt[c] = (unsigned)r[kRsCnt0 + c];
+    lists_ok = r[kRsListsOk] != 0; mf = (unsigned long long)r[kRsMf]; scan_all = r[kRsScanAll] != 0;
+    it = (int)r[kRsIt]; ballot_it = (int)r[kRsBallotIt]; online_it = (int)r[kRsOnlineIt];
+    pull_it = (int)r[kRsPullIt]; fsum = r[kRsFsum]; phases0 = r[kRsPhases];
+  }
+  const int it_launch = it;
 
   while (true) {
+    if (SPLIT && it > it_launch) {
+      // no fusion: the next iteration runs in the next launch
+      const unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+      if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long* r = s->rs.v;
+        r[kRsT] = (long long)T; r[kRsLbuf] = lbuf;
+        for (int c = 0; c < kClasses; ++c) r[kRsCnt0 + c] = cnt[c];
+        r[kRsListsOk] = lists_ok; r[kRsMf] = (long long)mf; r[kRsScanAll] = scan_all;
+        r[kRsIt] = it; r[kRsBallotIt] = ballot_it; r[kRsOnlineIt] = online_it; r[kRsPullIt] = pull_it;
+        r[kRsFsum] = fsum; r[kRsPhases] = phases0 + (long long)sh.phase;
+        s->rs.want_dir = PULL ? 2 : 1;
+        s->rs.active = 1;
+      }
+      return;
+    }
     const unsigned long long t_it = globaltimer();
     unsigned total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     filt = 1;
@@ -549,11 +586,12 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
     st.pull_iters += pull_it;
     st.ballot_iters += ballot_it;
     st.online_iters += online_it;
-    st.phases += (int)sh.phase;
+    st.phases += (int)(phases0 + (long long)sh.phase);
     st.grid = (int)grid;
     st.edges_visited = (long long)s->evisit;
     st.frontier_sum += fsum;
     st.last_l1 = 0.0;
+    s->rs.done = 1;
   }
 }
 
@@ -579,13 +617,28 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
   // pull iterations are compiled into their own instantiation, so that the
   // push kernel carries none of their registers
   const bool pull = g->symmetric && g->cfg.direction == 2;
-  const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true> : (const void*)sssp_kernel<OffT, false, false>;
-  int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
   void* args[] = {&a};
-  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
-  return finish_launch(g, stats, st);
+  // all and selective fusion are one launch (an SSSP run computes in one
+  // direction); no fusion runs one launch per iteration until the kernel
+  // reports the run finished
+  if (a.k.fusion != 2) {
+    const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true> : (const void*)sssp_kernel<OffT, false, false>;
+    if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
+    return finish_launch(g, stats, st);
+  }
+  if (capturing(st)) return SIMDX_EUNSUPPORTED;
+  const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true, false, true>
+                          : (const void*)sssp_kernel<OffT, false, false, false, true>;
+  const int grid = grid_for(g, kern);
+  for (int launch = 0;; ++launch) {
+    if (launch > 0 && (rc = prepare_resume(g, st)) != SIMDX_OK) return rc;
+    if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+    int done = 0, want = 0;
+    if ((rc = read_resume(g, st, &done, &want)) != SIMDX_OK) return rc;
+    if (done) return finish_launch(g, stats, st, launch + 1);
+  }
 }
 
 template <class OffT>
@@ -602,6 +655,7 @@ static int run_wcc(simdx_graph* g, uint32_t* label, simdx_stats* stats, cudaStre
   a.dist = label;
   a.w = make_work(g);
   a.k = make_knobs(g);
+  a.k.fusion = 0;
   const void* kern = (const void*)sssp_kernel<OffT, false, false, true>;
   int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
@@ -612,7 +666,7 @@ static int run_wcc(simdx_graph* g, uint32_t* label, simdx_stats* stats, cudaStre
   a.src = g->hub;
   void* args[] = {&a};
   if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
-  return finish_launch(g, stats, st);
+  return finish_launch(g, stats, st, 2);
 }
 
 // The copies of a batch run in groups of equal size whose distances take at
@@ -677,6 +731,7 @@ static int run_sssp_batch(simdx_graph* g, const int32_t* srcs, int k, uint32_t* 
   }
   a.w.state = pdist;  // the kernel finds pend right after the ids processed distances
   a.k = make_knobs(g);
+  a.k.fusion = 0;
   const void* kern = (const void*)sssp_kernel<OffT, true, false>;
   int grid = grid_for(g, kern);
   int rc = prepare_launch(g, st);
@@ -693,7 +748,7 @@ static int run_sssp_batch(simdx_graph* g, const int32_t* srcs, int k, uint32_t* 
     void* args[] = {&a};
     if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
   }
-  return finish_launch(g, stats, st);
+  return finish_launch(g, stats, st, (k + group - 1) / group);
 }
 
 }  // namespace simdx

@@ -40,10 +40,11 @@ class simdx_stats(ctypes.Structure):
                 ("ballot_iters", ctypes.c_int32), ("online_iters", ctypes.c_int32),
                 ("phases", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
                 ("edges_visited", ctypes.c_int64), ("frontier_sum", ctypes.c_int64),
-                ("last_l1", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
+                ("last_l1", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("reserved32", ctypes.c_int32), ("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
 
 
 class simdx_config(ctypes.Structure):
@@ -54,7 +55,8 @@ class simdx_config(ctypes.Structure):
                 ("kcore_alpha", ctypes.c_float), ("delta", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_int32), ("barrier_timeout_ms", ctypes.c_int32),
                 ("debug_skip_cta", ctypes.c_int32), ("debug_skip_phase", ctypes.c_int32),
-                ("batch_group", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("batch_group", ctypes.c_int32), ("fusion", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _LIB = None

@@ -60,7 +60,7 @@ def test_host_only_calls(lib):
 
 def test_config_layout_matches_header(lib):
     """The binding's simdx_config mirrors the header field for field (the
-    batch_group knob took one of the reserved words, so the size is
+    batch_group and fusion knobs took reserved words, so the size is
     unchanged); simdx_config_default writes the whole struct."""
     import ctypes
     from paper_1812_04070_gb300 import simdx
@@ -73,4 +73,18 @@ def test_config_layout_matches_header(lib):
     words = sum(int(n) if n else 1 for _, _, n in fields)
     assert ctypes.sizeof(simdx.simdx_config) == 4 * words
     c = simdx.simdx_config_default()
-    assert c.batch_group == 0 and list(c.reserved) == [0] * 7
+    assert c.batch_group == 0 and c.fusion == 0 and list(c.reserved) == [0] * 6
+
+
+def test_stats_layout_matches_header():
+    """simdx_stats keeps its size: the launch count took reserved words."""
+    import ctypes
+    from paper_1812_04070_gb300 import simdx
+    text = open(os.path.join(ROOT, "include", "simdx.h")).read()
+    end = text.index("} simdx_stats;")
+    body = text[text.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int32_t|int64_t|double)\s+([a-z_0-9]+)(\[(\d+)\])?;", body)
+    assert [f[1] for f in fields] == [f[0] for f in simdx.simdx_stats._fields_]
+    size = sum({"int32_t": 4, "int64_t": 8, "double": 8}[t] * (int(n) if n else 1) for t, _, _, n in fields)
+    assert ctypes.sizeof(simdx.simdx_stats) == size == 88

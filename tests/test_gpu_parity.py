@@ -229,3 +229,65 @@ def test_stats_and_trace():
     assert tr.shape[0] == st.iterations
     assert list(tr[:, 3]) == list(range(st.iterations))
     G.close()
+
+
+# Kernel fusion (Sec. 5, Table 2): all fusion (one launch), selective push-pull
+# fusion (one launch per run of one direction) and no fusion (one launch per
+# iteration) must give identical results.
+FUSION = {"selective": dict(fusion=1), "none": dict(fusion=2), "none_pull": dict(fusion=2, direction=2),
+          "selective_pull": dict(fusion=1, direction=2),
+          "none_all_classes": dict(fusion=2, small_max=2, med_max=4, huge_min=8),
+          "none_ballot": dict(fusion=2, filter=2)}
+
+
+@pytest.mark.parametrize("mode", list(FUSION))
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_bfs_sssp_fusion_modes(gi, mode):
+    g = GRAPHS[gi]
+    w = gg.weights(g, 77 + gi, 1, 64)
+    G = make(g, w, bits=32 if gi % 2 else 64, **FUSION[mode])
+    for s in sources(g):
+        lev = G.bfs(s).cpu().numpy()
+        assert np.array_equal(lev, oracle.bfs(g.offsets, g.indices, s)), (g.name, mode, s)
+        d = G.sssp(s).cpu().numpy().view(np.uint32)
+        assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, s)), (g.name, mode, s)
+    assert G.last_status() == 0
+    G.close()
+
+
+def test_fusion_launch_counts():
+    """Selective fusion launches once per run of consecutive iterations in
+    one direction (push, pull, push on R-MAT: 3, as in Table 2); no fusion
+    once per iteration; all fusion once.  Iterations and edge counts are the
+    same in every mode."""
+    from paper_1812_04070_gb300 import simdx_stats
+    g = gg.rmat(14)
+    w = gg.weights(g, 3, 1, 64)
+    G = make(g, w, bits=32)
+    st0 = simdx_stats()
+    ref = G.bfs(0, stats=st0).cpu().numpy()
+    dirs = [int(r[0]) & 0xff for r in G.trace()]
+    assert st0.launches == 1 and dirs[0] == 1 and 2 in dirs
+    runs = 1 + sum(1 for a, b in zip(dirs, dirs[1:]) if a != b)
+    for fusion, want in [(1, runs), (2, len(dirs))]:
+        G.set_config(fusion=fusion)
+        st = simdx_stats()
+        lev = G.bfs(0, stats=st).cpu().numpy()
+        import torch
+        torch.cuda.synchronize()
+        assert np.array_equal(lev, ref)
+        assert st.launches == want and st.iterations == st0.iterations, (fusion, st.launches, want)
+        assert st.pull_iters == st0.pull_iters and st.edges_visited == st0.edges_visited
+        assert [int(r[0]) & 0xff for r in G.trace()] == dirs
+    G.set_config(fusion=0)
+    sd = simdx_stats()
+    d0 = G.sssp(0, stats=sd).cpu().numpy()
+    G.set_config(fusion=2)
+    sn = simdx_stats()
+    d2 = G.sssp(0, stats=sn).cpu().numpy()
+    import torch
+    torch.cuda.synchronize()
+    # the last launch of an SSSP run only finds that no vertex is pending
+    assert np.array_equal(d0, d2) and sn.iterations == sd.iterations and sd.launches == 1
+    assert sn.launches in (sn.iterations, sn.iterations + 1)
+    G.close()
