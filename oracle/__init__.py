@@ -19,6 +19,9 @@ GPUs"), cited per function in ``oracle.c``:
 * ``pagerank``   -- Sec. 6 "PageRank", FP64 Jacobi pull iteration (readings of
                     the unstated teleport, dangling and stop rules: see the
                     function docstring).
+* ``pagerank_delta`` -- Sec. 6 "PageRank" with its switch to push: FP64 pull
+                    iterations, then pushes of the rank changes still above
+                    a threshold (accumulative delta iteration).
 * ``bfs_par``, ``kcore_par``, ``pagerank_par`` -- the same results computed
                     with OpenMP on every host core, only to time the CPU
                     baseline; pinned equal to the single-threaded functions.
@@ -78,6 +81,9 @@ def _load():
         lib.or_wcc.restype = ctypes.c_int
         lib.or_pagerank.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, i64, vp, vp]
         lib.or_pagerank.restype = i64
+        lib.or_pagerank_delta.argtypes = [i64, vp, vp, vp, vp, dbl, dbl, i64, dbl, dbl, dbl, vp,
+                                          ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+        lib.or_pagerank_delta.restype = i64
         lib.or_bfs_par.argtypes = [i64, vp, vp, i32, vp]
         lib.or_bfs_par.restype = ctypes.c_int
         lib.or_kcore_par.argtypes = [i64, vp, vp, u32, vp, vp]
@@ -180,6 +186,34 @@ def pagerank(in_off, in_idx, outdeg=None, d: float = 0.85, tol: float = 1e-6,
     it = _load().or_pagerank(n, off.ctypes.data, ip, od.ctypes.data, float(d), float(tol),
                              int(max_iter), int(fixed_iter), x.ctypes.data, ctypes.byref(l1))
     return x[:n], int(it), float(l1.value)
+
+
+def pagerank_delta(off, idx, in_off=None, in_idx=None, d: float = 0.85, tol: float = 1e-6,
+                   max_iter: int = 1000, alpha: float = 8.0, theta: float = 2.0, rho_min: float = 0.6):
+    """FP64 PageRank that pulls first and, once the pull contracts slowly
+    (L1 at least rho_min times the previous L1) and the vertices whose
+    change exceeds theta * (previous L1) / n hold fewer than E / alpha
+    out-edges, pushes the remaining rank changes (Sec. 6 "PageRank": pull,
+    then push when most vertices are stable; the switch rule is a reading
+    of the paper's undescribed decision tree).  Out-edges ``off/idx``; in-edges
+    ``in_off/in_idx`` (default: the CSR itself, a symmetric graph).  Stops
+    when the L1 change (pull) or the L1 of the pending changes (push) is
+    below ``tol``; the result is then within d / (1 - d) * tol of the fixed
+    point in L1.  Returns (x float64[n], iterations, pull iterations, last
+    L1)."""
+    off, idx, ip = _csr(off, idx)
+    if in_off is None:
+        ioff, iidx, iip = off, idx, ip
+    else:
+        ioff, iidx, iip = _csr(in_off, in_idx)
+    n = off.size - 1
+    x = np.empty(max(n, 1), dtype=np.float64)
+    pulls = ctypes.c_int64(0)
+    l1 = ctypes.c_double(0.0)
+    it = _load().or_pagerank_delta(n, off.ctypes.data, ip, ioff.ctypes.data, iip, float(d), float(tol),
+                                   int(max_iter), float(alpha), float(theta), float(rho_min), x.ctypes.data,
+                                   ctypes.byref(pulls), ctypes.byref(l1))
+    return x[:n], int(it), int(pulls.value), float(l1.value)
 
 
 # ------------------------------------------------ parallel timing variants

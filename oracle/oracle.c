@@ -497,3 +497,123 @@ OR_EXPORT int or_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------ PageRank, push tail */
+/* Sec. 6 "PageRank": start with pull (the Jacobi iteration of or_pagerank)
+ * and, once most vertices are stable, switch to push, propagating only the
+ * rank changes that are still large (the accumulative delta iteration the
+ * paper cites for this switch).  The paper decides the switch by a decision
+ * tree it does not describe; the rule here is a reading of it, a tree of
+ * two tests made after pull iteration i >= 1 (the run not yet converged):
+ * the pull contracts slowly, L1_i >= rho_min * L1_{i-1} (where it contracts
+ * fast, the signed changes cancel in the pull sums and a selective push
+ * loses that), and few vertices are unstable: those whose change exceeds
+ * eps_i = theta * L1_{i-1} / n have fewer than E / alpha out-edges.  Both
+ * hold: switch to push.  alpha <= 0 never switches.
+ *
+ * With M the iteration matrix of or_pagerank (x_{t+1} = (1-d)/n + M x_t),
+ * the push phase keeps a pair (x, r) with x* = x + (I - M)^-1 r:
+ *   switch after pull iteration i: x = x_i, r = x_{i+1} - x_i;
+ *   each push iteration: L1 = ||r||_1; stop if L1 < tol; otherwise every
+ *   vertex with |r(v)| > eps (eps = theta * L1_prev / n, or 0 when the
+ *   previous iteration selected no vertex) moves r(v) into x(v) and sends
+ *   d * r(v) / outdeg(v) to each out-neighbour (dangling vertices send
+ *   d * r(v) / n to every vertex); L1_prev = L1.
+ * The result is x + r, so ||x_out - x*||_1 <= d / (1 - d) * L1 < d / (1 - d)
+ * * tol, the same guarantee as the pull stop.  off/idx are out-edges,
+ * in_off/in_idx in-edges, outdeg = off[v+1] - off[v].  Returns the number of
+ * iterations (pull + push); *pull_iters gets the pull ones. */
+OR_EXPORT int64_t or_pagerank_delta(int64_t n, const int64_t *off, const int32_t *idx,
+                                    const int64_t *in_off, const int32_t *in_idx,
+                                    double d, double tol, int64_t max_iter, double alpha,
+                                    double theta, double rho_min, double *x_out, int64_t *pull_iters,
+                                    double *l1_out)
+{
+    if (n == 0) { *pull_iters = 0; return 0; }
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *take = (double *)malloc(sizeof(double) * (size_t)n);
+    int64_t e = off[n];
+    for (int64_t v = 0; v < n; ++v) x[v] = 1.0 / (double)n;
+    int64_t t = 0;
+    double l1 = 0.0, l1_prev = 0.0;
+    int push = 0;
+    /* pull phase */
+    while (t < max_iter) {
+        double dangling = 0.0;
+        for (int64_t u = 0; u < n; ++u)
+            if (off[u + 1] == off[u]) dangling += x[u];
+        l1 = 0.0;
+        for (int64_t v = 0; v < n; ++v) {
+            double s = 0.0;
+            for (int64_t p = in_off[v]; p < in_off[v + 1]; ++p) {
+                int32_t u = in_idx[p];
+                s += x[u] / (double)(off[u + 1] - off[u]);
+            }
+            y[v] = (1.0 - d) / (double)n + d * (s + dangling / (double)n);
+            l1 += fabs(y[v] - x[v]);
+        }
+        ++t;
+        if (l1 < tol) {  /* converged by pull alone */
+            double *tmp = x; x = y; y = tmp;
+            break;
+        }
+        if (t >= 2 && alpha > 0.0 && l1 >= rho_min * l1_prev) {
+            double eps = theta * l1_prev / (double)n, m_act = 0.0;
+            for (int64_t v = 0; v < n; ++v)
+                if (fabs(y[v] - x[v]) > eps) m_act += (double)(off[v + 1] - off[v]);
+            if (m_act * alpha < (double)e) {
+                for (int64_t v = 0; v < n; ++v) r[v] = y[v] - x[v];  /* x stays x_i */
+                push = 1;
+                break;
+            }
+        }
+        l1_prev = l1;
+        double *tmp = x; x = y; y = tmp;
+    }
+    *pull_iters = t;
+    if (push) {
+        double unif = 0.0;   /* rank sent to every vertex by dangling vertices */
+        int none = 0;
+        l1_prev = l1;
+        for (;;) {
+            l1 = 0.0;
+            for (int64_t v = 0; v < n; ++v) {
+                r[v] += unif;
+                l1 += fabs(r[v]);
+            }
+            unif = 0.0;
+            if (l1 < tol || t >= max_iter) break;
+            double eps = none ? 0.0 : theta * l1_prev / (double)n, dang = 0.0;
+            int64_t sel = 0;
+            for (int64_t v = 0; v < n; ++v) {
+                take[v] = 0.0;
+                if (fabs(r[v]) > eps) {
+                    take[v] = r[v];
+                    x[v] += r[v];
+                    r[v] = 0.0;
+                    ++sel;
+                    if (off[v + 1] == off[v]) dang += take[v];
+                }
+            }
+            for (int64_t v = 0; v < n; ++v) {
+                if (take[v] == 0.0 || off[v + 1] == off[v]) continue;
+                double c = d * take[v] / (double)(off[v + 1] - off[v]);
+                for (int64_t p = off[v]; p < off[v + 1]; ++p) r[idx[p]] += c;
+            }
+            unif = d * dang / (double)n;
+            none = sel == 0;
+            l1_prev = l1;
+            ++t;
+        }
+        for (int64_t v = 0; v < n; ++v) x[v] += r[v];
+    }
+    memcpy(x_out, x, sizeof(double) * (size_t)n);
+    if (l1_out) *l1_out = l1;
+    free(x);
+    free(y);
+    free(r);
+    free(take);
+    return t;
+}

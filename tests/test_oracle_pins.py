@@ -453,3 +453,61 @@ def test_parallel_variants_equal_definitions(gi):
         a, b = oracle.pagerank(g.offsets, g.indices, **kw), oracle.pagerank_par(g.offsets, g.indices, **kw)
         assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
     assert oracle.threads() >= 1
+
+
+# ------------------------------------------------ PageRank, push tail
+# pagerank_delta pulls, then pushes the rank changes still above a threshold.
+# Pinned by: (a) without a switch it is the pull iteration itself; (b) with
+# every changed vertex pushed (theta = 0) each push iteration is one Jacobi
+# step, so it stops at the same iteration with the same ranks; (c) with any
+# threshold its result is within d / (1 - d) * tol (L1) of the fixed point
+# from a dense FP64 solve, which a dropped dangling share, a wrong
+# out-degree or a lost residual would break.
+def test_pagerank_delta_without_switch_is_pull():
+    for g in [gg.rmat(11), gg.grid(30, 20), gg.star(50)]:
+        a = oracle.pagerank(g.offsets, g.indices)
+        b = oracle.pagerank_delta(g.offsets, g.indices, alpha=0.0)
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1] == b[2]
+
+
+def test_pagerank_delta_full_push_is_jacobi():
+    for g in [gg.rmat(11), gg.grid(30, 20), gg.from_edges(10, [0, 1, 5, 6], [1, 2, 6, 7]), gg.path(40)]:
+        x, it, pulls, _ = oracle.pagerank_delta(g.offsets, g.indices, alpha=1e-30, theta=0.0, rho_min=0.0)
+        j, jt, _ = oracle.pagerank(g.offsets, g.indices)
+        assert pulls == min(2, jt) and it == jt
+        assert np.abs(x - j).sum() < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0, 2.0, 4.0])
+@pytest.mark.parametrize("gi", range(18))
+def test_pagerank_delta_error_bound(gi, theta):
+    g = small_graphs()[gi]
+    if g.n == 0:
+        return
+    d, tol = 0.85, 1e-6
+    exp = pagerank_dense(g, d)
+    x, it, pulls, l1 = oracle.pagerank_delta(g.offsets, g.indices, d=d, tol=tol, alpha=1e-30, theta=theta, rho_min=0.0)
+    assert np.abs(x - exp).sum() <= d / (1 - d) * tol * (1 + 1e-9) + 1e-14
+    assert l1 < tol or it == 1000
+
+
+def test_pagerank_delta_directed_and_grid_bound():
+    from gpu_util import directed_graph
+    off, idx, ioff, iidx, _ = directed_graph(300, 1500, 4)
+    n = off.size - 1
+    deg = np.diff(off)
+    x_ref, _, _ = oracle.pagerank(ioff, iidx, outdeg=deg, tol=1e-14, max_iter=10000)
+    for theta in (1.0, 2.0):
+        x, it, pulls, _ = oracle.pagerank_delta(off, idx, ioff, iidx, alpha=1e-30, theta=theta, rho_min=0.0)
+        assert pulls == 2 and it > 2
+        assert np.abs(x - x_ref).sum() <= 0.85 / 0.15 * 1e-6 + 1e-12
+    # the rule itself: on the grid the pull contracts slowly and few vertices
+    # are unstable, so it switches; on R-MAT the pull contracts fast, so it
+    # keeps pulling
+    g = gg.grid(64, 64)
+    _, it, pulls, _ = oracle.pagerank_delta(g.offsets, g.indices)
+    assert 2 < pulls < it
+    for r in (gg.rmat(12), gg.rmat(14)):
+        _, it, pulls, _ = oracle.pagerank_delta(r.offsets, r.indices)
+        assert pulls == it
+    assert n == 300
