@@ -81,13 +81,19 @@ WORKLOADS = {
                          desc="4096x4096 4-neighbour grid: BFS from corner 0"),
     "grid4096-sssp": dict(kind="grid", rows=4096, bits=64, algs=["sssp"], wmax=1000,
                           desc="4096x4096 4-neighbour grid, w in [1,1000]: SSSP from corner 0"),
+    "grid4096-pagerank": dict(kind="grid", rows=4096, bits=64, algs=["pagerank"],
+                              desc="4096x4096 4-neighbour grid: PageRank d=0.85 tol 1e-6 (pull, then push once "
+                                   "the pull contracts slowly and few vertices are unstable)"),
     "grid4096-ablation": dict(kind="ablation", graph="grid", rows=4096, bits=64, algs=["bfs", "sssp"],
                               wmax=1000,
                               desc="4096x4096 4-neighbour grid (w in [1,1000]), BFS / SSSP from corner 0: all, "
                                    "selective and no kernel fusion (Sec. 5, Table 2); JIT vs ballot-only filter"),
-    "rmat24-ablation": dict(kind="ablation", graph="rmat", scale=24, bits=64, algs=["bfs", "sssp", "kcore"],
-                            desc="R-MAT scale 24, int64 offsets: BFS / SSSP src 0 and k-core 16 under all, "
-                                 "selective and no kernel fusion (BFS, SSSP); JIT vs ballot-only filter (Sec. 4)"),
+    "grid4096-pr-ablation": dict(kind="ablation", graph="grid", rows=4096, bits=64, algs=["pagerank"],
+                                 desc="4096x4096 4-neighbour grid: PageRank pull then push (Sec. 6) vs pull only"),
+    "rmat24-ablation": dict(kind="ablation", graph="rmat", scale=24, bits=64,
+                            algs=["bfs", "sssp", "kcore", "pagerank"],
+                            desc="R-MAT scale 24, int64 offsets: BFS / SSSP src 0, k-core 16 and PageRank under all, "
+                                 "selective and no kernel fusion (BFS, SSSP); JIT vs ballot-only filter (Sec. 4); PageRank switch to push vs pull only"),
     "batch22": dict(kind="batch", scale=22, bits=32,
                     desc="R-MAT scale 22 (n=4,194,304, ef 16, w in [1,64]): 64 BFS + 64 SSSP sources uniform over "
                          "non-isolated vertices (seed 0xBA7C4), batched vs one call per query; plus 256 R-MAT "
@@ -267,8 +273,12 @@ def reached_edges(g, reached_mask):
     return e_c, int(reached_mask.sum())
 
 
-def algorithmic(alg, g, bits, out, iters):
-    """(undirected traversed edges, algorithmic bytes) of one launch."""
+def algorithmic(alg, g, bits, out, iters, st=None):
+    """(undirected traversed edges, algorithmic bytes) of one call.  A
+    PageRank run that switched to push counts its pull iterations as above
+    and each push iteration as a scan of the pending changes (8 bytes per
+    vertex) plus 12 bytes per pushed edge (index, 64-bit add), with the
+    pushed edges from the run's own edge counter."""
     so = s_off(bits)
     n, e = g.n, g.e
     if alg == "bfs":
@@ -284,6 +294,11 @@ def algorithmic(alg, g, bits, out, iters):
     if alg == "wcc":
         return e // 2, 4 * e + (2 * so + 12) * n
     if alg == "pagerank":
+        if st is not None and st.push_iters > 0:
+            pulls = st.pull_iters
+            pushed = max(0, st.edges_visited - pulls * e)
+            return (e // 2) * pulls + pushed // 2, (4 * e + (2 * so + 12) * n) * pulls + \
+                st.push_iters * 8 * n + 12 * pushed
         return (e // 2) * iters, (4 * e + (2 * so + 12) * n) * iters
     raise ValueError(alg)
 
@@ -428,7 +443,7 @@ def run_simdx(args, rank, world, local):
         else:
             host = o.cpu().numpy()
             n_reached[a] = int((host >= 0).sum()) if a == "bfs" else g.n
-        work[a] = algorithmic(a, g, bits, host, stats[a].iterations)
+        work[a] = algorithmic(a, g, bits, host, stats[a].iterations, stats[a])
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -727,14 +742,22 @@ def run_ablation(args, rank, world, local):
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     out8 = torch.empty(g.n, dtype=torch.uint8, device=dev)
     reps = max(3, min(args.steps, 7))
-    modes = {"bfs": [(0, 0), (1, 0), (2, 0), (0, 2), (2, 2)], "sssp": [(0, 0), (2, 0), (0, 2), (2, 2)],
-             "kcore": [(0, 0), (0, 2)]}
+    fl = lambda f, x: (f"fusion={['all', 'selective', 'none'][f]} filter={'JIT' if x == 0 else 'ballot'}",
+                       dict(fusion=f, filter=x))
+    modes = {"bfs": [fl(0, 0), fl(1, 0), fl(2, 0), fl(0, 2), fl(2, 2)],
+             "sssp": [fl(0, 0), fl(2, 0), fl(0, 2), fl(2, 2)], "kcore": [fl(0, 0), fl(0, 2)],
+             "pagerank": [("pull, then push (default switch rule)", dict(pr_alpha=8.0)),
+                          ("pull only", dict(pr_alpha=0.0))]}
+
+    outf = torch.empty(g.n, dtype=torch.float32, device=dev)
 
     def call(a, st=None):
         if a == "bfs":
             G.bfs(0, out=out, stats=st)
         elif a == "sssp":
             G.sssp(0, out=out, stats=st)
+        elif a == "pagerank":
+            G.pagerank(0.85, 1e-6, 1000, out=outf, stats=st)
         else:
             G.kcore(16, out=out8, want_resid=False, stats=st)
 
@@ -742,12 +765,12 @@ def run_ablation(args, rank, world, local):
     for a in wl["algs"]:
         ref = None
         rows = []
-        for fusion, filt in modes[a]:
-            G.set_config(fusion=fusion, filter=filt)
+        for label, knobs in modes[a]:
+            G.set_config(**knobs)
             st = simdx_stats()
             call(a, st)
             torch.cuda.synchronize()
-            o = (out8 if a == "kcore" else out).clone()
+            o = (out8 if a == "kcore" else outf if a == "pagerank" else out).clone()
             if ref is None:
                 ref = o
             ts = []
@@ -760,13 +783,19 @@ def run_ablation(args, rank, world, local):
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1))
             ms = statistics.median(ts)
-            rows.append({"fusion": ["all", "selective", "none"][fusion], "filter": "JIT" if filt == 0 else "ballot",
-                         "ms": round(ms, 3), "iterations": st.iterations, "launches": st.launches,
-                         "us_per_iteration": round(ms * 1e3 / max(1, st.iterations), 2),
-                         "pull_iters": st.pull_iters, "ballot_iters": st.ballot_iters,
-                         "identical": bool(torch.equal(o, ref))})
+            row = {"mode": label, "ms": round(ms, 3), "iterations": st.iterations, "launches": st.launches,
+                   "us_per_iteration": round(ms * 1e3 / max(1, st.iterations), 2),
+                   "pull_iters": st.pull_iters, "push_iters": st.push_iters, "ballot_iters": st.ballot_iters,
+                   "edges_inspected": st.edges_visited}
+            if a == "pagerank":
+                # the two modes reach the fixed point by different paths: both are
+                # within d / (1 - d) * tol of it, so they are compared in L1
+                row["l1_vs_first_mode"] = float((o.double() - ref.double()).abs().sum())
+            else:
+                row["identical"] = bool(torch.equal(o, ref))
+            rows.append(row)
         res[a] = rows
-    G.set_config(fusion=0, filter=0)
+        G.set_config(fusion=0, filter=0, pr_alpha=8.0)
     G.close()
     base = res[wl["algs"][0]][0]
     return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],

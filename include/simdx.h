@@ -147,7 +147,14 @@ typedef struct {
                                 run finished and which direction comes next), so they
                                 cannot be captured (EUNSUPPORTED while capturing).  Results
                                 are identical in every mode. */
-    int32_t reserved[6];
+    float pr_alpha;          /* simdx_pagerank switch from pull to push (Sec. 6 "PageRank"):
+                                after pull iteration t >= 2, push once the L1 change
+                                contracts slowly (L1_t >= pr_rho * L1_{t-1}) and the
+                                vertices whose change exceeds pr_theta * L1_{t-1} / n have
+                                fewer than E / pr_alpha out-edges; 0 = pull only [8] */
+    float pr_theta;          /* push threshold, in units of the mean pending change [2] */
+    float pr_rho;            /* slowest pull contraction that still keeps pulling [0.6] */
+    int32_t reserved[3];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;

@@ -350,6 +350,9 @@ void simdx_config_default(simdx_config* c) {
   c->barrier_timeout_ms = 2000;
   c->debug_skip_cta = -1;
   c->debug_skip_phase = -1;
+  c->pr_alpha = 8.f;
+  c->pr_theta = 2.f;
+  c->pr_rho = 0.6f;
 }
 
 int64_t simdx_eq1_ctas(int64_t regs_per_sm, int64_t regs_per_thread, int64_t threads_per_cta,
@@ -583,7 +586,8 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
       cfg->bin_per_thread < 0 || cfg->bin_per_thread > 4096 || cfg->direction < 0 ||
       cfg->direction > 2 || (cfg->filter != 0 && cfg->filter != 2) || !(cfg->alpha > 0.f) ||
       !(cfg->beta > 0.f) || !(cfg->kcore_alpha > 0.f) || cfg->ctas_per_sm < 0 || cfg->batch_group < 0 ||
-      cfg->fusion < 0 || cfg->fusion > 2)
+      cfg->fusion < 0 || cfg->fusion > 2 || !(cfg->pr_alpha >= 0.f) || !(cfg->pr_theta >= 0.f) ||
+      !(cfg->pr_rho >= 0.f))
     return SIMDX_EINVAL;
   bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
                     cfg->huge_min != g->cfg.huge_min;

@@ -82,11 +82,16 @@ struct PrArgs {
   float d, tol;
   int max_iter;
   const OffT* off;   // out-edges (out-degree)
+  const int32_t* idx;
   const OffT* ioff;  // in-edges
   const int32_t* iidx;
   long long e;       // in-edges
   float* rank;
   float* inv;        // [n] 1 / outdeg (0 for outdeg 0), set once per run
+  // switch from pull to push (the push-tail instantiation only)
+  float alpha, theta, rho;
+  unsigned long long* res;  // [n] pending rank change, signed 2^-60 fixed point
+  long long* push_c;        // [n] what a selected vertex sends along each out-edge (2^-60)
   PrWalk wk;
   Work w;
   Knobs k;
@@ -195,8 +200,8 @@ __device__ __forceinline__ TileIn pr_load(const PrArgs<OffT>& a, const float* ci
 // Sum one tile and finish the rows that end in it.  (ch, cl) (the same in
 // every lane) is the partial of the row open at the tile's start, `trank` the
 // number of row starts before the tile; both advance past the tile.
-template <class OffT>
-__device__ __forceinline__ void pr_tile(const PrArgs<OffT>& a, PrPull<OffT>& f, float base, const int32_t* l0, int c0n,
+template <class OffT, class Pull>
+__device__ __forceinline__ void pr_tile(const PrArgs<OffT>& a, Pull& f, float base, const int32_t* l0, int c0n,
                                         const TileIn& in, float& ch, float& cl, int& trank, const PrCross& cx, int gw,
                                         unsigned& end_bit) {
   const int lane = lane_id();
@@ -312,8 +317,8 @@ __device__ __forceinline__ void pr_prefetch_l2(const void* p) {
 
 // One iteration's sums over the in-edges of this warp's tile range
 // [t_beg, t_end).
-template <class OffT>
-__device__ __forceinline__ void pr_walk(const PrArgs<OffT>& a, PrPull<OffT>& f, float base, const int32_t* l0,
+template <class OffT, class Pull>
+__device__ __forceinline__ void pr_walk(const PrArgs<OffT>& a, Pull& f, float base, const int32_t* l0,
                                         int c0n, int gw, int t_beg, int t_end, int rank0, const PrCross& cx) {
   if (t_beg >= t_end) return;
   float ch = 0.f, cl = 0.f;  // the open row's partial, ch + cl unevaluated
@@ -370,7 +375,174 @@ __device__ __forceinline__ unsigned long long tile_cost(const PrWalk& wk, long l
          (unsigned long long)wk.row_cost * (unsigned)(__popc(h[0]) + __popc(h[1]) + __popc(h[2]) + __popc(h[3]));
 }
 
+// ---------------------------------------------------------- push tail
+// After the switch (Sec. 6 "PageRank": push once most vertices are stable)
+// the run keeps ranks x (FP32, in rank) and pending changes r (signed 2^-60
+// fixed point) with x* = x + (I - M)^-1 r, M the pull iteration's matrix.
+// Each push iteration is two phases: a ballot scan of every vertex (it adds
+// the uniform share of the dangling vertices pushed before, sums |r| for the
+// stop test, and selects the vertices with |r(v)| > eps, moving r(v) into
+// x(v) and fixing what v sends), then a push of the selected vertices along
+// their out-edges by the degree classes, each edge one 64-bit integer add.
+// Integer adds commute, and every selection and claim is made by the owner
+// of the vertex, so the run is bit-identical every time.  It ends when
+// ||r||_1 < tol with x + r as the result: within d / (1 - d) * tol of x*.
+struct PrPush {
+  struct Src {
+    long long c;
+  };
+  unsigned long long* res;
+  const long long* push_c;
+  __device__ __forceinline__ bool src(int v, Src& s, int, unsigned) {
+    s.c = push_c[v];
+    return s.c != 0;
+  }
+  __device__ __forceinline__ int rv(int v) const { return v; }
+  static __device__ __forceinline__ Src shfl(const Src& s, int l) {
+    Src r;
+    r.c = __shfl_sync(kFull, s.c, l);
+    return r;
+  }
+  __device__ __forceinline__ void edges(const Src (&s)[kPushBatch], const int (&)[kPushBatch],
+                                        const int (&u)[kPushBatch], const long long (&)[kPushBatch], unsigned ok) {
+#pragma unroll
+    for (int q = 0; q < kPushBatch; ++q)
+      if ((ok >> q) & 1u) atomicAdd(res + u[q], (unsigned long long)s[q].c);  // no return value: a reduction
+  }
+};
+
+constexpr double kUnfix = 8.67361737988403547e-19;  // 2^-60
+
+// The push iterations.  Launched after the pull kernel of a run with the
+// switch enabled; returns at once when that kernel converged by pulling
+// alone (it then wrote the result and the statistics), else continues after
+// its last pull iteration t, reading x_{t-1} and x_t from rank / x_alt.
 template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) pagerank_push_kernel(const __grid_constant__ PrArgs<OffT> a) {
+  __shared__ CtaShared sh;
+  Sync* s = a.w.sync;
+  if (ld_volatile_i32(&s->rs.active) == 0) return;
+  const unsigned grid = gridDim.x;
+  const Knobs& k = a.k;
+  const int n = a.n;
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long gthreads = (long long)grid * kThreads;
+  unsigned long long* res = a.res;
+  long long* push_c = a.push_c;
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+  const int pulls = (int)s->rs.v[0];
+  int t = pulls;
+  double l1_last = __longlong_as_double(s->rs.v[1]);
+  long long evisit = 0;
+  const float* xalt = reinterpret_cast<const float*>(a.w.state);
+  const float* xo_p = ((t - 1) & 1) ? xalt : a.rank;
+  const float* xn_p = ((t - 1) & 1) ? a.rank : xalt;
+  // x = x_{t-1}, r = x_t - x_{t-1}
+  clear_next_slot(s, sh);
+  for (long long v = gtid; v < n; v += gthreads) {
+    const float xo = xo_p[v], xn = xn_p[v];
+    res[v] = (unsigned long long)((long long)to_fix(xn) - (long long)to_fix(xo));
+    a.rank[v] = xo;
+  }
+  if (!grid_sync(s, grid, sh, k)) return;
+  long long G = 0;          // uniform pending change not yet added to every r(v)
+  double l1p = l1_last;     // L1 of the previous scan
+  bool none = false;        // the previous scan selected no vertex
+  const OffT* off = a.off;
+  while (true) {
+    const unsigned long long t_it = globaltimer();
+    // ---- scan: add G, sum |r|, select |r| > eps and claim
+    clear_next_slot(s, sh);
+    PhaseSlot& slot = s->slot[slot_of(sh.phase)];
+    const unsigned long long eps_fix =
+        none ? 0ull : (unsigned long long)((double)a.theta * l1p / (double)n * kFix);
+    unsigned long long l1acc = 0, dang = 0;
+    const long long GG = G;
+    auto pred = [&](int v) {
+      long long rv = (long long)res[v];
+      if (GG != 0) {
+        rv += GG;
+        res[v] = (unsigned long long)rv;
+      }
+      const unsigned long long av = rv < 0 ? (unsigned long long)(-rv) : (unsigned long long)rv;
+      l1acc += av;
+      return av > eps_fix;
+    };
+    auto deg = [off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+    auto visit = [&](int v) {
+      const long long rv = (long long)res[v];
+      res[v] = 0ull;
+      a.rank[v] += (float)((double)rv * kUnfix);
+      const long long od = (long long)gload(off + v + 1) - (long long)gload(off + v);
+      if (od == 0) {
+        dang += (unsigned long long)rv;
+        push_c[v] = 0;
+      } else {
+        push_c[v] = llrint((double)rv * (double)a.d / (double)od);
+      }
+    };
+    ballot_filter(n, pred, deg, visit, sh, a.w, k, grid, 1, slot);
+    const unsigned long long l1s = cta_sum_u64(l1acc, sh);
+    const unsigned long long ds = cta_sum_u64(dang, sh);
+    if (threadIdx.x == 0) {
+      atomicAdd(&slot.aux1, l1s);
+      atomicAdd(&slot.aux0, ds);
+    }
+    if (!grid_sync(s, grid, sh, k)) return;
+    const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
+    const double l1 = (double)p.aux1 / kFix;
+    unsigned cnt[kClasses];
+    for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
+    const unsigned sel = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    l1_last = l1;
+    if (l1 < (double)a.tol || t >= a.max_iter) {
+      // x + r (claims only moved r into x, so the sum is the state before them)
+      for (long long v = gtid; v < n; v += gthreads)
+        a.rank[v] += (float)((double)(long long)res[v] * kUnfix);
+      trace_put(a.w, t, 1 | (2 << 8), sel, 0, (long long)p.aux1, t_it);
+      break;
+    }
+    const long long Gn = llrint((double)a.d * (double)(long long)p.aux0 / (double)n);
+    // ---- push the selected vertices' changes along their out-edges
+    clear_next_slot(s, sh);
+    {
+      PhaseSlot& slot2 = s->slot[slot_of(sh.phase)];
+      PrPush f{res, push_c};
+      const int32_t* lists[kClasses] = {a.w.list[1][0], a.w.list[1][1], a.w.list[1][2], a.w.list[1][3]};
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot2);
+    }
+    if (!grid_sync(s, grid, sh, k)) return;
+    trace_put(a.w, t, 1 | (2 << 8), sel, 0, (long long)p.aux1, t_it);
+    trace_classes(a.w, t, s->slot[slot_of(sh.phase - 1)]);
+    G = Gn;
+    none = sel == 0;
+    l1p = l1;
+    ++t;
+  }
+  const unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+  if (!grid_sync(s, grid, sh, k)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats& st = *a.w.stats;
+    st.status = 0;
+    st.iterations = t;
+    st.push_iters = t - pulls;
+    st.pull_iters = pulls;
+    st.ballot_iters = 2 + (t - pulls);  // the first pull and every push scan
+    st.online_iters = 0;
+    st.phases = (int)sh.phase;
+    st.grid = (int)grid;
+    st.edges_visited = (long long)s->evisit;
+    st.frontier_sum = (long long)pulls * n;
+    st.last_l1 = l1_last;
+    s->rs.done = 1;
+  }
+}
+
+// TAIL: the instantiation that may switch to push (the pr_alpha knob); the
+// pull-only kernel carries none of its registers.
+template <class OffT, bool TAIL = false>
 __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_constant__ PrArgs<OffT> a) {
   __shared__ CtaShared sh;
   const unsigned grid = gridDim.x;
@@ -527,6 +699,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
   const float base = (1.0f - a.d) / (float)n;
   int t = 0;
   double l1_last = 0.0;
+  bool to_push = false;
   while (true) {
     if (t >= a.max_iter) break;
     const unsigned long long t_it = globaltimer();
@@ -555,20 +728,49 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     Dfix = p.aux0;
+    const double l1_prev = l1_last;
     l1_last = (double)p.aux1 / kFix;
     trace_put(a.w, t, 2 | (2 << 8), n, a.e, (long long)p.aux1, t_it);
     trace_classes(a.w, t, p);
     ++t;
     if (l1_last < (double)a.tol) break;
+    // switch to push (reading of Sec. 6's decision tree): first test, the
+    // pull contracts slowly; only then the second, a scan for the out-edges
+    // of the unstable vertices (change above theta * L1_{t-1} / n)
+    if (TAIL && a.alpha > 0.f && t >= 2 && t < a.max_iter && l1_last >= (double)a.rho * l1_prev) {
+      clear_next_slot(s, sh);
+      PhaseSlot& sl = s->slot[slot_of(sh.phase)];
+      const float eps = (float)((double)a.theta * l1_prev / (double)n);
+      unsigned long long m = 0;
+      for (long long v = gtid; v < n; v += gthreads)
+        if (fabsf(f.xnew[v] - f.xold[v]) > eps) m += (unsigned long long)(gload(off + v + 1) - gload(off + v));
+      m = cta_sum_u64(m, sh);
+      if (threadIdx.x == 0 && m) atomicAdd(&sl.aux2, m);
+      if (!grid_sync(s, grid, sh, k)) return;
+      if ((double)s->slot[slot_of(sh.phase - 1)].aux2 * (double)a.alpha < (double)a.e) {
+        to_push = true;
+        break;
+      }
+    }
   }
-  long long evisit = 0;  // in-edges this warp summed, every iteration
+  long long evisit = 0;  // in-edges this warp summed, every pull iteration
   if (lane_id() == 0 && t_beg < t_end)
     evisit = (long long)t * (min((long long)t_end * kTile, a.e) - (long long)t_beg * kTile);
+  unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+  if (TAIL && to_push) {
+    // the push kernel launched next continues from here (selective fusion:
+    // a pull kernel and a push kernel, Sec. 5)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      s->rs.v[0] = t;
+      s->rs.v[1] = __double_as_longlong(l1_last);
+      s->rs.active = 1;
+    }
+    return;
+  }
   // ---- result: x_t is in rank for even t, in xalt for odd t
   if (t & 1)
     for (long long v = gtid; v < n; v += gthreads) a.rank[v] = xalt[v];
-  unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
-  if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
   if (!grid_sync(s, grid, sh, k)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     DevStats& st = *a.w.stats;
@@ -599,14 +801,26 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   a.tol = tol;
   a.max_iter = max_iter;
   a.off = (const OffT*)g->off;
+  a.idx = g->idx;
   a.ioff = (const OffT*)g->in_off;
   a.iidx = g->in_idx;
   a.e = g->e;
   a.rank = rank;
-  a.inv = static_cast<float*>(g->state) + 3 * (size_t)g->n;
+  a.alpha = g->cfg.pr_alpha;
+  a.theta = g->cfg.pr_theta;
+  a.rho = g->cfg.pr_rho;
+  const bool tail = a.alpha > 0.f;
+  // state (20 bytes per vertex): x_alt | c0 | c1 | 1/outdeg | spare; with the
+  // push tail 1/outdeg moves to the spare slot, the pending changes (8 bytes)
+  // take c1 and the old slot once the pulls end, and what each selected
+  // vertex sends (8 bytes) takes x_alt and c0
+  float* st4 = static_cast<float*>(g->state);
+  a.inv = st4 + (tail ? 4 : 3) * (size_t)g->n;
+  a.push_c = reinterpret_cast<long long*>(st4);
+  a.res = reinterpret_cast<unsigned long long*>(st4 + 2 * (size_t)g->n);
   a.w = make_work(g);
   a.k = make_knobs(g);
-  const void* kern = (const void*)pagerank_kernel<OffT>;
+  const void* kern = tail ? (const void*)pagerank_kernel<OffT, true> : (const void*)pagerank_kernel<OffT>;
   int grid = grid_for(g, kern);
   // walk layout: row-start bits, tile cost prefix and chunk sums, warp
   // ranges, per-warp partials and arrival counters
@@ -642,7 +856,13 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   if (rc) return rc;
   void* args[] = {&a};
   if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
-  return finish_launch(g, stats, st);
+  if (!tail) return finish_launch(g, stats, st);
+  // the push kernel returns at once unless the pull kernel switched; the
+  // decision stays on the device, so the call can still be captured
+  const void* pk = (const void*)pagerank_push_kernel<OffT>;
+  if ((rc = prepare_resume(g, st)) != SIMDX_OK) return rc;
+  if ((rc = launch_coop(pk, grid_for(g, pk), args, st)) != SIMDX_OK) return rc;
+  return finish_launch(g, stats, st, 2);
 }
 
 }  // namespace simdx

@@ -56,7 +56,8 @@ class simdx_config(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("barrier_timeout_ms", ctypes.c_int32),
                 ("debug_skip_cta", ctypes.c_int32), ("debug_skip_phase", ctypes.c_int32),
                 ("batch_group", ctypes.c_int32), ("fusion", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("pr_alpha", ctypes.c_float), ("pr_theta", ctypes.c_float), ("pr_rho", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 _LIB = None

@@ -55,7 +55,44 @@ def make(g, w=None, bits=64, **cfg):
     return G
 
 
+def assert_pagerank(G, g=None, d=0.85, tol=1e-6, max_iter=1000, in_csr=None, outdeg=None):
+    """Run PageRank on the GPU and check it against the FP64 oracle.
+
+    A run that only pulled (the Jacobi iteration) must be within 1e-6
+    relative L1 of the oracle after the same number of iterations and stop
+    within one iteration of the oracle's own stop.  A run that switched to
+    push (Sec. 6 "PageRank") stops when the pending changes sum below tol in
+    L1, which leaves its result within d / (1 - d) * tol of the fixed point;
+    it must be within that bound plus 1e-6 (FP32 rounding) of the oracle's
+    converged fixed point (run to 1e-13).  ``in_csr`` = (in_off, in_idx) of
+    a directed graph (default: g's CSR).  Returns (stats, error)."""
+    from paper_1812_04070_gb300 import simdx_stats
+    import torch
+    ioff, iidx = in_csr if in_csr is not None else (g.offsets, g.indices)
+    st = simdx_stats()
+    x = G.pagerank(d, tol, max_iter, stats=st)
+    torch.cuda.synchronize()
+    x = x.cpu().numpy().astype(np.float64)
+    t = st.iterations
+    assert st.status == 0 and st.pull_iters + st.push_iters == t
+    if st.push_iters == 0:
+        ex, _, _ = oracle.pagerank(ioff, iidx, outdeg=outdeg, d=d, fixed_iter=t)
+        denom = np.abs(ex).sum()
+        rel = np.abs(x - ex).sum() / denom if denom > 0 else 0.0
+        assert rel <= 1e-6, rel
+        _, t_stop, _ = oracle.pagerank(ioff, iidx, outdeg=outdeg, d=d, tol=tol, max_iter=max_iter)
+        assert abs(t - t_stop) <= 1, (t, t_stop)
+        return st, rel
+    xc, _, _ = oracle.pagerank_par(ioff, iidx, outdeg=outdeg, d=d, tol=1e-13, max_iter=100000)
+    err = np.abs(x - xc).sum()
+    bound = d / (1 - d) * tol + 1e-6
+    assert err <= bound, (err, bound, st.pull_iters, st.push_iters)
+    assert st.last_l1 < tol or t == max_iter
+    return st, err
+
+
 def check_pagerank(G, g, d=0.85, tol=1e-6, max_iter=1000):
+    """Jacobi parity of a pull-only run (see assert_pagerank)."""
     from paper_1812_04070_gb300 import simdx_stats
     import torch
     st = simdx_stats()

@@ -60,7 +60,7 @@ def test_host_only_calls(lib):
 
 def test_config_layout_matches_header(lib):
     """The binding's simdx_config mirrors the header field for field (the
-    batch_group and fusion knobs took reserved words, so the size is
+    batch_group, fusion and PageRank switch knobs took reserved words, so the size is
     unchanged); simdx_config_default writes the whole struct."""
     import ctypes
     from paper_1812_04070_gb300 import simdx
@@ -73,7 +73,8 @@ def test_config_layout_matches_header(lib):
     words = sum(int(n) if n else 1 for _, _, n in fields)
     assert ctypes.sizeof(simdx.simdx_config) == 4 * words
     c = simdx.simdx_config_default()
-    assert c.batch_group == 0 and c.fusion == 0 and list(c.reserved) == [0] * 6
+    assert c.batch_group == 0 and c.fusion == 0 and list(c.reserved) == [0] * 3
+    assert (c.pr_alpha, c.pr_theta, c.pr_rho) == (8.0, 2.0, pytest.approx(0.6))
 
 
 def test_stats_layout_matches_header():

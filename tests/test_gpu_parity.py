@@ -12,7 +12,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from gpu_util import FORCED, check_pagerank, make, small_graphs, sources
+from gpu_util import FORCED, assert_pagerank, check_pagerank, make, small_graphs, sources
 
 pytestmark = pytest.mark.gpu
 
@@ -143,10 +143,59 @@ def test_kcore(gi, mode):
 def test_pagerank(gi, mode):
     g = GRAPHS[gi]
     G = make(g, **FORCED[mode])
-    rel, t, t_stop, st = check_pagerank(G, g)
-    assert rel <= 1e-6, (g.name, mode, rel)
-    assert abs(t - t_stop) <= 1, (t, t_stop)
+    assert_pagerank(G, g)
+    G.set_config(pr_alpha=0.0)  # pull only: the Jacobi iteration throughout
+    st, rel = assert_pagerank(G, g)
+    assert st.push_iters == 0 and st.launches == 1
     G.close()
+
+
+# The switch from pull to push (Sec. 6 "PageRank").  Forced early (pr_alpha
+# huge, pr_rho 0: after the second pull) on every graph; with pr_theta = 0
+# every changed vertex pushes, which is the Jacobi step, so the result must
+# match the oracle's Jacobi iterate of the same count.
+@pytest.mark.parametrize("theta", [0.0, 0.5, 2.0, 8.0])
+@pytest.mark.parametrize("mode", ["default", "all_classes"])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_pagerank_push_tail(gi, mode, theta):
+    import torch
+    from paper_1812_04070_gb300 import simdx_stats
+    g = GRAPHS[gi]
+    G = make(g, bits=32 if gi % 2 else 64, pr_alpha=1e30, pr_rho=0.0, pr_theta=theta, **FORCED[mode])
+    st, err = assert_pagerank(G, g)
+    jt = oracle.pagerank(g.offsets, g.indices)[1]
+    if jt > 3 and g.n > 1:
+        assert st.pull_iters == 2 and st.push_iters > 0 and st.launches == 2, (st.pull_iters, st.push_iters)
+    if theta == 0.0 and st.push_iters > 0:
+        ex, _, _ = oracle.pagerank(g.offsets, g.indices, fixed_iter=st.iterations)
+        x = G.pagerank().cpu().numpy().astype(np.float64)
+        assert np.abs(x - ex).sum() / np.abs(ex).sum() <= 1e-6
+        assert abs(st.iterations - jt) <= 1
+    a = G.pagerank().clone()
+    b = G.pagerank().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)  # bit-identical run to run
+    G.close()
+
+
+def test_pagerank_switch_rule():
+    """Default knobs: on a grid the pull contracts slowly and few vertices are
+    unstable, so the run switches after the same pull iterations as the
+    oracle's rule; on R-MAT the pull contracts fast and it never switches."""
+    from paper_1812_04070_gb300 import simdx_stats
+    for g in [gg.grid(64, 64), gg.grid(300, 200)]:
+        G = make(g)
+        st, err = assert_pagerank(G, g)
+        _, it, pulls, _ = oracle.pagerank_delta(g.offsets, g.indices)
+        assert st.push_iters > 0 and st.pull_iters == pulls, (st.pull_iters, pulls)
+        tr = G.trace()
+        assert [int(r[0]) & 0xff for r in tr[:st.iterations]] == [2] * pulls + [1] * st.push_iters
+        G.close()
+    for g in [gg.rmat(12), gg.rmat(14)]:
+        G = make(g)
+        st, _ = assert_pagerank(G, g)
+        assert st.push_iters == 0
+        G.close()
 
 
 def test_pagerank_deterministic_and_max_iter():
