@@ -625,7 +625,23 @@ def run_batch(args, rank, world, local):
     ts = _ev_time(lambda: [Gi.bfs(int(s), out=o) for Gi, s, o in zip(Gs, gsrc, outs)], reps)
     same = all(torch.equal(op[int(bases[i]):int(bases[i + 1])], outs[i]) for i in range(len(graphs)))
     res["multigraph_bfs"] = {"batched_qps": round(256 / tb * 1e3, 1), "per_query_qps": round(256 / ts * 1e3, 1),
-                             "batched_ms": round(tb, 3), "per_query_ms": round(ts, 3), "identical": same}
+                             "batched_ms": round(tb, 3), "per_query_ms": round(ts, 3), "identical": same,
+                             "note": "caller-packed CSR (simdx_bfs_multi)"}
+    # the same 256 graphs as separate objects (simdx_bfs_multigraph: the
+    # library packs them on the device, once per list, and scatters levels)
+    from paper_1812_04070_gb300 import bfs_multigraph
+    outs_m = [torch.empty(x.n, dtype=torch.int32, device="cuda") for x in graphs]
+    t0 = time.perf_counter()
+    bfs_multigraph(Gs, gsrc, outs=outs_m)
+    torch.cuda.synchronize()
+    first_ms = (time.perf_counter() - t0) * 1e3
+    tm = _ev_time(lambda: bfs_multigraph(Gs, gsrc, outs=outs_m), reps)
+    same = all(torch.equal(outs_m[i], outs[i]) for i in range(len(graphs)))
+    res["multigraph_handles_bfs"] = {"batched_qps": round(256 / tm * 1e3, 1), "per_query_qps": round(256 / ts * 1e3, 1),
+                                     "batched_ms": round(tm, 3), "per_query_ms": round(ts, 3), "identical": same,
+                                     "first_call_ms": round(first_ms, 3),
+                                     "note": "separate graph objects (simdx_bfs_multigraph); the first call "
+                                             "builds the pack"}
     for Gi in Gs:
         Gi.close()
     P.close()

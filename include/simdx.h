@@ -333,6 +333,31 @@ SIMDX_API int simdx_sssp_batch(simdx_graph *g, const int32_t *srcs, int32_t k, u
 SIMDX_API int simdx_bfs_multi(simdx_graph *g, const int32_t *roots, int32_t k, int32_t *levels,
                               simdx_stats *stats, void *stream);
 
+/* BFS on k separate graphs in one persistent launch (growth direction (a):
+ * many graphs of uneven size in one launch; Sec. 6 "BFS" per graph).  The
+ * library packs the graphs on the device into one block-diagonal CSR
+ * (graph i's ids offset by the vertices of the graphs before it), runs
+ * simdx_bfs_multi on the pack with root base_i + srcs[i] per block, and
+ * copies block i's levels into levels[i]; no edge joins two blocks, so
+ * levels[i] equals simdx_bfs(gs[i], srcs[i]).
+ *   gs      k graph objects on the current device (any mix of sizes, offset
+ *           widths, symmetric or directed; a graph may appear twice).
+ *   srcs    host int32[k], srcs[i] in [0, n_i).
+ *   levels  host array of k DEVICE pointers, levels[i] int32[n_i].
+ * The pack (a copy of every graph's CSR, 4 bytes per vertex of levels and a
+ * graph object over it) is built by the first call for a list and kept with
+ * gs[0] (freed when gs[0] is destroyed); later calls with the same list in
+ * the same order reuse it, a different list rebuilds it (allocating, and
+ * waiting on `stream` while the pack's graph object is created).  Calls
+ * whose first graph is the same share the pack: like calls on one graph,
+ * they must not overlap in time.  The output pointer table is copied from
+ * the caller's host memory, so the call cannot be captured (EUNSUPPORTED
+ * while capturing).  Errors: EINVAL (k outside [1, 65535], NULL, a source
+ * out of range, a graph on another device, more than 2^31 - 2 vertices in
+ * all), ENOMEM, ECUDA. */
+SIMDX_API int simdx_bfs_multigraph(simdx_graph *const *gs, const int32_t *srcs, int32_t k,
+                                   int32_t *const *levels, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 /* Query server over resident graphs (growth direction (b)): continuous
  * batching.  A dispatcher thread keeps `slots` launches in flight on their

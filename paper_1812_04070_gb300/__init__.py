@@ -16,7 +16,7 @@ import numpy as np
 from . import simdx
 from .simdx import SimdxError, simdx_config, simdx_stats
 
-__all__ = ["Graph", "Server", "simdx", "SimdxError", "simdx_config", "simdx_stats", "build"]
+__all__ = ["Graph", "Server", "bfs_multigraph", "simdx", "SimdxError", "simdx_config", "simdx_stats", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -199,6 +199,19 @@ class Graph:
         simdx.simdx_pagerank(self.handle, float(damping), float(tol), int(max_iter), out.data_ptr(), stats,
                              _stream_handle(stream))
         return out
+
+
+def bfs_multigraph(graphs, srcs, outs=None, stream=None):
+    """BFS of graphs[i] from srcs[i] for every i, all in one persistent launch
+    (simdx_bfs_multigraph).  Returns the list of int32 level tensors."""
+    torch = _torch()
+    if outs is None:
+        outs = [torch.empty(G.n, dtype=torch.int32, device=G.device) for G in graphs]
+    for G, o in zip(graphs, outs):
+        assert o.dtype == torch.int32 and o.is_cuda and o.is_contiguous() and o.numel() >= G.n
+    simdx.simdx_bfs_multigraph([G.handle for G in graphs], [int(s) for s in srcs], [o.data_ptr() for o in outs],
+                               _stream_handle(stream))
+    return outs
 
 
 class Server:

@@ -421,6 +421,7 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
   simdx_graph* g = new (std::nothrow) simdx_graph();
   if (!g) return SIMDX_ENOMEM;
   simdx_config_default(&g->cfg);
+  g->gen = next_graph_gen();
   g->n = csr->n;
   g->e = csr->e;
   g->off_bits = csr->offset_bits;
@@ -538,6 +539,7 @@ int simdx_graph_destroy(simdx_graph* g) {
   if (!g) return SIMDX_EINVAL;
   cudaDeviceSynchronize();  // no call on this graph is in flight past here
   cudaStream_t st = 0;
+  mg_pack_free(g, st);
   if (!g->borrowed) {
     dev_free(g->off, st);
     dev_free(g->idx, st);

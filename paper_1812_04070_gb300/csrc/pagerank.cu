@@ -540,6 +540,27 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_push_kernel(const __grid
   }
 }
 
+// Second test of the switch rule: a scan for the out-edges of the vertices
+// whose change exceeds eps.  Returns 1 to switch, 0 to keep pulling, -1 if
+// the run aborted.  Out of line: the pull walk keeps its registers.
+template <class OffT>
+__device__ __noinline__ int pr_unstable_test(const PrArgs<OffT>& a, const float* xold, const float* xnew, float eps,
+                                             CtaShared& sh) {
+  Sync* s = a.w.sync;
+  const unsigned grid = gridDim.x;
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long gthreads = (long long)grid * kThreads;
+  clear_next_slot(s, sh);
+  PhaseSlot& sl = s->slot[slot_of(sh.phase)];
+  unsigned long long m = 0;
+  for (long long v = gtid; v < a.n; v += gthreads)
+    if (fabsf(xnew[v] - xold[v]) > eps) m += (unsigned long long)(gload(a.off + v + 1) - gload(a.off + v));
+  m = cta_sum_u64(m, sh);
+  if (threadIdx.x == 0 && m) atomicAdd(&sl.aux2, m);
+  if (!grid_sync(s, grid, sh, a.k)) return -1;
+  return (double)s->slot[slot_of(sh.phase - 1)].aux2 * (double)a.alpha < (double)a.e ? 1 : 0;
+}
+
 // TAIL: the instantiation that may switch to push (the pr_alpha knob); the
 // pull-only kernel carries none of its registers.
 template <class OffT, bool TAIL = false>
@@ -738,16 +759,9 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     // pull contracts slowly; only then the second, a scan for the out-edges
     // of the unstable vertices (change above theta * L1_{t-1} / n)
     if (TAIL && a.alpha > 0.f && t >= 2 && t < a.max_iter && l1_last >= (double)a.rho * l1_prev) {
-      clear_next_slot(s, sh);
-      PhaseSlot& sl = s->slot[slot_of(sh.phase)];
-      const float eps = (float)((double)a.theta * l1_prev / (double)n);
-      unsigned long long m = 0;
-      for (long long v = gtid; v < n; v += gthreads)
-        if (fabsf(f.xnew[v] - f.xold[v]) > eps) m += (unsigned long long)(gload(off + v + 1) - gload(off + v));
-      m = cta_sum_u64(m, sh);
-      if (threadIdx.x == 0 && m) atomicAdd(&sl.aux2, m);
-      if (!grid_sync(s, grid, sh, k)) return;
-      if ((double)s->slot[slot_of(sh.phase - 1)].aux2 * (double)a.alpha < (double)a.e) {
+      const int r = pr_unstable_test(a, f.xold, f.xnew, (float)((double)a.theta * l1_prev / (double)n), sh);
+      if (r < 0) return;
+      if (r) {
         to_push = true;
         break;
       }

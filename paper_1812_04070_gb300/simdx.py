@@ -90,6 +90,7 @@ SIGNATURES = {
     "simdx_bfs_batch": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_sssp_batch": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_bfs_multi": (ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
+    "simdx_bfs_multigraph": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "simdx_server_create": (ctypes.c_int, [_vp, _i32, ctypes.c_size_t, _i32, _i32, ctypes.POINTER(_vp)]),
     "simdx_server_submit": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_uint64)]),
     "simdx_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32)]),
@@ -248,6 +249,17 @@ def simdx_bfs_multi(g: int, roots, levels_ptr: int, stats: simdx_stats | None, s
     a = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
     _check(_lib().simdx_bfs_multi(g, a.ctypes.data, int(a.size), levels_ptr,
                                   ctypes.byref(stats) if stats is not None else None, stream), "simdx_bfs_multi")
+
+
+def simdx_bfs_multigraph(graphs, srcs, levels_ptrs, stream: int | None) -> None:
+    """BFS of graph i from srcs[i] into the device array levels_ptrs[i], all
+    graphs in one launch."""
+    import numpy as np
+    k = len(graphs)
+    gs = (ctypes.c_void_p * k)(*graphs)
+    a = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    outs = (ctypes.c_void_p * k)(*levels_ptrs)
+    _check(_lib().simdx_bfs_multigraph(gs, a.ctypes.data, k, outs, stream), "simdx_bfs_multigraph")
 
 
 def simdx_server_create(graphs, mem_budget: int, max_slots: int = 4, max_sssp: int = 8) -> int:

@@ -139,3 +139,51 @@ def test_sssp_batch_directed():
         assert np.array_equal(out[i], oracle.sssp(off, idx, wt, s)), i
         assert torch.equal(torch.from_numpy(out[i].view(np.int32)), G.sssp(s).cpu())
     G.close()
+
+
+def test_bfs_multigraph_separate_handles():
+    """simdx_bfs_multigraph over separate graph objects: 256 R-MAT graphs of
+    uneven size (n log-uniform in [1000, 100000], edge factor 8..32, the
+    batching configuration's recipe), mixed offset widths, through the C ABI;
+    every graph's levels equal the oracle's BFS of that graph.  A second call
+    reuses the pack; a changed list (another order, a directed graph, a
+    graph destroyed and re-created) rebuilds it."""
+    import torch
+    from paper_1812_04070_gb300 import Graph, SimdxError, bfs_multigraph, simdx
+    from gpu_util import directed_graph
+    graphs, srcs = gg.multigraph_batch(count=256)
+    Gs = [Graph(g.offsets if i % 3 == 0 else g.offsets.astype(np.int32), g.indices) for i, g in enumerate(graphs)]
+    outs = bfs_multigraph(Gs, srcs)
+    torch.cuda.synchronize()
+    for i, g in enumerate(graphs):
+        assert np.array_equal(outs[i].cpu().numpy(), oracle.bfs(g.offsets, g.indices, int(srcs[i]))), i
+    srcs2 = [int(gg.pick_sources(g, 1, seed=99 + i)[0]) for i, g in enumerate(graphs)]
+    outs = bfs_multigraph(Gs, srcs2, outs=outs)  # same list: the cached pack
+    torch.cuda.synchronize()
+    for i, g in enumerate(graphs):
+        assert np.array_equal(outs[i].cpu().numpy(), oracle.bfs(g.offsets, g.indices, srcs2[i])), i
+    # another list: reversed order, a directed graph appended, one graph twice
+    off, idx, ioff, iidx, _ = directed_graph(700, 3000, 2)
+    D = Graph(off, idx, csc=(ioff, iidx))
+    sub = list(reversed(Gs[:40])) + [D, Gs[5]]
+    ss = list(reversed([int(s) for s in srcs[:40]])) + [3, int(srcs[5])]
+    res = bfs_multigraph(sub, ss)
+    torch.cuda.synchronize()
+    want = list(reversed(graphs[:40]))
+    for i, g in enumerate(want):
+        assert np.array_equal(res[i].cpu().numpy(), oracle.bfs(g.offsets, g.indices, ss[i])), i
+    assert np.array_equal(res[40].cpu().numpy(), oracle.bfs(off, idx, 3))
+    assert np.array_equal(res[41].cpu().numpy(), oracle.bfs(graphs[5].offsets, graphs[5].indices, int(srcs[5])))
+    # a graph re-created (perhaps at the same address) is a new list entry
+    Gs[1].close()
+    Gs[1] = Graph(graphs[1].offsets, graphs[1].indices)
+    outs = bfs_multigraph(Gs[:8], srcs[:8])
+    torch.cuda.synchronize()
+    for i in range(8):
+        g = graphs[i]
+        assert np.array_equal(outs[i].cpu().numpy(), oracle.bfs(g.offsets, g.indices, int(srcs[i]))), i
+    with pytest.raises(SimdxError) as e:
+        bfs_multigraph(Gs[:2], [0, graphs[1].n])
+    assert e.value.status == simdx.EINVAL
+    for G in Gs + [D]:
+        G.close()

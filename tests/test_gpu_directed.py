@@ -55,7 +55,7 @@ def test_directed_pagerank(case):
     # deterministic
     assert np.array_equal(G.pagerank().cpu().numpy(), G.pagerank().cpu().numpy())
     # the push tail forced after two pulls: pushes run along the out-edges
-    G.set_config(pr_alpha=1e30, pr_rho=0.0)
+    G.set_config(pr_alpha=1e-30, pr_rho=0.0)
     st, _ = assert_pagerank(G, in_csr=(ioff, iidx), outdeg=outdeg)
     assert st.push_iters > 0
     assert np.array_equal(G.pagerank().cpu().numpy(), G.pagerank().cpu().numpy())

@@ -151,7 +151,7 @@ def test_pagerank(gi, mode):
 
 
 # The switch from pull to push (Sec. 6 "PageRank").  Forced early (pr_alpha
-# huge, pr_rho 0: after the second pull) on every graph; with pr_theta = 0
+# tiny, pr_rho 0: after the second pull) on every graph; with pr_theta = 0
 # every changed vertex pushes, which is the Jacobi step, so the result must
 # match the oracle's Jacobi iterate of the same count.
 @pytest.mark.parametrize("theta", [0.0, 0.5, 2.0, 8.0])
@@ -161,7 +161,7 @@ def test_pagerank_push_tail(gi, mode, theta):
     import torch
     from paper_1812_04070_gb300 import simdx_stats
     g = GRAPHS[gi]
-    G = make(g, bits=32 if gi % 2 else 64, pr_alpha=1e30, pr_rho=0.0, pr_theta=theta, **FORCED[mode])
+    G = make(g, bits=32 if gi % 2 else 64, pr_alpha=1e-30, pr_rho=0.0, pr_theta=theta, **FORCED[mode])
     st, err = assert_pagerank(G, g)
     jt = oracle.pagerank(g.offsets, g.indices)[1]
     if jt > 3 and g.n > 1:
