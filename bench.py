@@ -240,11 +240,11 @@ def _code_only(text: str) -> str:
 def kernel_source_hash(kernel: str) -> str:
     """Hash of the code a kernel is built from (comments and layout
     ignored): its own file (<algorithm>.cu for <algorithm>_kernel) and the
-    shared device headers."""
+    shared device header (the host-side header declares no device code)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1812_04070_gb300", "csrc")
     own = KERNEL_FILES.get(kernel, kernel.replace("_kernel", "") + ".cu")
-    for fn in [own, "acc_device.cuh", "simdx_internal.h"]:
+    for fn in [own, "acc_device.cuh"]:
         with open(os.path.join(csrc, fn), encoding="utf-8") as f:
             h.update(fn.encode())
             h.update(_code_only(f.read()).encode())

@@ -419,6 +419,21 @@ SIMDX_API int simdx_server_destroy(simdx_server *s);
 SIMDX_API int simdx_autotune(simdx_graph *g, int32_t algo, int64_t arg, int32_t reps, simdx_config *best,
                              float *best_ms, void *stream);
 
+/* The same tuner for the batched calls (growth direction (a): autotuned bin
+ * thresholds for batches): algo SIMDX_ALGO_BFS times simdx_bfs_batch,
+ * SIMDX_ALGO_SSSP simdx_sssp_batch and SIMDX_ALGO_BFS_MULTI simdx_bfs_multi,
+ * each on the k sources (or roots) `srcs` (host int32[k]).  Knobs tried: the
+ * CTAs per SM and degree-class thresholds; for the SSSP batch also the
+ * overflow threshold, the bucket width and the copies per launch
+ * (batch_group); for the multi-root BFS the BFS knobs.  Blocking; allocates
+ * one scratch output (4 n bytes per source, 4 n for the multi-root BFS) for
+ * its duration.  Results are the same under every setting.  Errors: EINVAL
+ * (bad algo, k, source or reps; k * n >= 2^31 for SSSP), EUNSUPPORTED (SSSP
+ * without weights), or the first error a timed call returns. */
+#define SIMDX_ALGO_BFS_MULTI 5
+SIMDX_API int simdx_autotune_batch(simdx_graph *g, int32_t algo, const int32_t *srcs, int32_t k, int32_t reps,
+                                   simdx_config *best, float *best_ms, void *stream);
+
 /* ------------------------------------------------- no-allocation variant */
 /* BFS for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a deployment convenience).  Some callers cannot call

@@ -192,6 +192,15 @@ class Graph:
         best, ms = simdx.simdx_autotune(self.handle, int(algo), int(arg), int(reps), _stream_handle(stream))
         return {name: getattr(best, name) for name, _ in best._fields_ if name != "reserved"}, ms
 
+    def autotune_batch(self, algo: int, srcs, reps: int = 3, stream=None) -> tuple[dict, float]:
+        """Measure knob settings for a batched call (simdx.ALGO_BFS: bfs_batch,
+        ALGO_SSSP: sssp_batch, ALGO_BFS_MULTI: bfs_multi) on these sources,
+        install the fastest and return it with its median time in ms
+        (simdx_autotune_batch)."""
+        best, ms = simdx.simdx_autotune_batch(self.handle, int(algo), [int(x) for x in srcs], int(reps),
+                                              _stream_handle(stream))
+        return {name: getattr(best, name) for name, _ in best._fields_ if name != "reserved"}, ms
+
     def pagerank(self, damping: float = 0.85, tol: float = 1e-6, max_iter: int = 1000, out=None,
                  stats: simdx_stats | None = None, stream=None):
         torch = _torch()

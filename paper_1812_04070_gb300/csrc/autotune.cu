@@ -6,6 +6,7 @@
 // width and the CTAs per SM of the persistent launch (Eq. 1).  None of them
 // changes a BFS, SSSP or k-core result, so the tuner only compares times.
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "simdx_internal.h"
@@ -46,6 +47,24 @@ std::vector<Knob> knobs_for(int algo) {
   return k;
 }
 
+// Knobs of the batched calls: the bit-parallel BFS batch uses the degree
+// classes and the grid; the SSSP batch adds the bins, the bucket width and
+// the copies per launch; the multi-root BFS is a BFS.
+std::vector<Knob> knobs_for_batch(int algo) {
+  if (algo == SIMDX_ALGO_BFS_MULTI) return knobs_for(SIMDX_ALGO_BFS);
+  std::vector<Knob> k;
+  k.push_back({"ctas_per_sm", {0, 3, 2}, SIMDX_KNOB_I(ctas_per_sm)});
+  k.push_back({"small_max", {8, 16, 32, 64}, SIMDX_KNOB_I(small_max)});
+  k.push_back({"med_max", {128, 256, 512, 1024, 2048}, SIMDX_KNOB_I(med_max)});
+  k.push_back({"huge_min", {1024, 2048, 4096, 8192, 16384}, SIMDX_KNOB_I(huge_min)});
+  if (algo == SIMDX_ALGO_SSSP) {
+    k.push_back({"bin_per_thread", {16, 32, 64, 128}, SIMDX_KNOB_I(bin_per_thread)});
+    k.push_back({"delta", {16, 64, 256, 1024, 4096, 16384, 0}, SIMDX_KNOB_I(delta)});
+    k.push_back({"batch_group", {0, 1, 2, 4, 8, 16, 32, 64}, SIMDX_KNOB_I(batch_group)});
+  }
+  return k;
+}
+
 #undef SIMDX_KNOB_I
 
 bool valid(const simdx_config& c) {
@@ -62,36 +81,13 @@ struct Timer {
 
 }  // namespace
 
-extern "C" int simdx_autotune(simdx_graph* g, int32_t algo, int64_t arg, int32_t reps, simdx_config* best,
-                              float* best_ms, void* stream) {
-  if (!g || !best || reps < 1 || reps > 64) return SIMDX_EINVAL;
-  if (algo < SIMDX_ALGO_BFS || algo > SIMDX_ALGO_PAGERANK) return SIMDX_EINVAL;
-  if ((algo == SIMDX_ALGO_BFS || algo == SIMDX_ALGO_SSSP) && (arg < 0 || arg >= g->n)) return SIMDX_EINVAL;
-  if (algo == SIMDX_ALGO_KCORE && (arg < 0 || arg > 0x7fffffff)) return SIMDX_EINVAL;
-  if (algo == SIMDX_ALGO_SSSP && !g->w) return SIMDX_EUNSUPPORTED;
+// Coordinate descent over `ks` from the graph's current knobs; `run` is one
+// timed call.  Leaves the winner installed.
+static int tune(simdx_graph* g, const std::vector<Knob>& ks, const std::function<int()>& run, int reps,
+                void* stream, simdx_config* best, float* best_ms) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t n = (size_t)std::max<int64_t>(g->n, 1);
-  void* out = nullptr;
-  void* resid = nullptr;
-  SIMDX_CUDA(simdx::dev_alloc(&out, 4 * n, st));
-  if (algo == SIMDX_ALGO_KCORE) {
-    cudaError_t e = simdx::dev_alloc(&resid, 4 * n, st);
-    if (e != cudaSuccess) {
-      simdx::dev_free(out, st);
-      return cuda_status(e, "dev_alloc(autotune resid)");
-    }
-  }
   Timer tm;
   int rc = SIMDX_OK;
-  auto run = [&]() -> int {
-    switch (algo) {
-      case SIMDX_ALGO_BFS: return simdx_bfs(g, (int32_t)arg, (int32_t*)out, nullptr, st);
-      case SIMDX_ALGO_SSSP: return simdx_sssp(g, (int32_t)arg, (uint32_t*)out, nullptr, st);
-      case SIMDX_ALGO_KCORE:
-        return simdx_kcore(g, (uint32_t)arg, (uint8_t*)out, (uint32_t*)resid, nullptr, st);
-      default: return simdx_pagerank(g, 0.85f, 1e-6f, 1000, (float*)out, nullptr, st);
-    }
-  };
   // median time of `reps` runs after one untimed run; the first error otherwise
   auto measure = [&](float& ms) -> int {
     int r = run();
@@ -124,7 +120,6 @@ extern "C" int simdx_autotune(simdx_graph* g, int32_t algo, int64_t arg, int32_t
     }
     if ((rc = simdx_graph_get_config(g, &cur)) != SIMDX_OK) break;
     if ((rc = measure(cur_ms)) != SIMDX_OK) break;
-    const std::vector<Knob> ks = knobs_for(algo);
     for (int pass = 0; pass < 2 && rc == SIMDX_OK; ++pass) {
       bool moved = false;
       for (const Knob& kb : ks) {
@@ -150,11 +145,69 @@ extern "C" int simdx_autotune(simdx_graph* g, int32_t algo, int64_t arg, int32_t
     }
   } while (false);
   if (rc == SIMDX_OK) rc = simdx_graph_set_config(g, &cur);
-  simdx::dev_free(out, st);
-  simdx::dev_free(resid, st);
   cudaStreamSynchronize(st);
   if (rc != SIMDX_OK) return rc;
   *best = cur;
   if (best_ms) *best_ms = cur_ms;
   return SIMDX_OK;
+}
+
+extern "C" int simdx_autotune(simdx_graph* g, int32_t algo, int64_t arg, int32_t reps, simdx_config* best,
+                              float* best_ms, void* stream) {
+  if (!g || !best || reps < 1 || reps > 64) return SIMDX_EINVAL;
+  if (algo < SIMDX_ALGO_BFS || algo > SIMDX_ALGO_PAGERANK) return SIMDX_EINVAL;
+  if ((algo == SIMDX_ALGO_BFS || algo == SIMDX_ALGO_SSSP) && (arg < 0 || arg >= g->n)) return SIMDX_EINVAL;
+  if (algo == SIMDX_ALGO_KCORE && (arg < 0 || arg > 0x7fffffff)) return SIMDX_EINVAL;
+  if (algo == SIMDX_ALGO_SSSP && !g->w) return SIMDX_EUNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)std::max<int64_t>(g->n, 1);
+  void* out = nullptr;
+  void* resid = nullptr;
+  SIMDX_CUDA(simdx::dev_alloc(&out, 4 * n, st));
+  if (algo == SIMDX_ALGO_KCORE) {
+    cudaError_t e = simdx::dev_alloc(&resid, 4 * n, st);
+    if (e != cudaSuccess) {
+      simdx::dev_free(out, st);
+      return cuda_status(e, "dev_alloc(autotune resid)");
+    }
+  }
+  auto run = [&]() -> int {
+    switch (algo) {
+      case SIMDX_ALGO_BFS: return simdx_bfs(g, (int32_t)arg, (int32_t*)out, nullptr, st);
+      case SIMDX_ALGO_SSSP: return simdx_sssp(g, (int32_t)arg, (uint32_t*)out, nullptr, st);
+      case SIMDX_ALGO_KCORE:
+        return simdx_kcore(g, (uint32_t)arg, (uint8_t*)out, (uint32_t*)resid, nullptr, st);
+      default: return simdx_pagerank(g, 0.85f, 1e-6f, 1000, (float*)out, nullptr, st);
+    }
+  };
+  const int rc = tune(g, knobs_for(algo), run, reps, stream, best, best_ms);
+  simdx::dev_free(out, st);
+  simdx::dev_free(resid, st);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
+extern "C" int simdx_autotune_batch(simdx_graph* g, int32_t algo, const int32_t* srcs, int32_t k, int32_t reps,
+                                    simdx_config* best, float* best_ms, void* stream) {
+  if (!g || !best || !srcs || k <= 0 || reps < 1 || reps > 64) return SIMDX_EINVAL;
+  if (algo != SIMDX_ALGO_BFS && algo != SIMDX_ALGO_SSSP && algo != SIMDX_ALGO_BFS_MULTI) return SIMDX_EINVAL;
+  for (int i = 0; i < k; ++i)
+    if (srcs[i] < 0 || srcs[i] >= g->n) return SIMDX_EINVAL;
+  if (algo == SIMDX_ALGO_SSSP && !g->w) return SIMDX_EUNSUPPORTED;
+  if (algo == SIMDX_ALGO_SSSP && (long long)k * g->n >= (1ll << 31) - 64) return SIMDX_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t rows = algo == SIMDX_ALGO_BFS_MULTI ? 1 : (size_t)k;
+  void* out = nullptr;
+  SIMDX_CUDA(simdx::dev_alloc(&out, 4 * rows * (size_t)std::max<int64_t>(g->n, 1), st));
+  auto run = [&]() -> int {
+    switch (algo) {
+      case SIMDX_ALGO_BFS: return simdx_bfs_batch(g, srcs, k, (int32_t*)out, nullptr, st);
+      case SIMDX_ALGO_SSSP: return simdx_sssp_batch(g, srcs, k, (uint32_t*)out, nullptr, st);
+      default: return simdx_bfs_multi(g, srcs, k, (int32_t*)out, nullptr, st);
+    }
+  };
+  const int rc = tune(g, knobs_for_batch(algo), run, reps, stream, best, best_ms);
+  simdx::dev_free(out, st);
+  cudaStreamSynchronize(st);
+  return rc;
 }

@@ -557,6 +557,7 @@ int simdx_graph_destroy(simdx_graph* g) {
   dev_free(g->d_roots, st);
   if (g->h_roots) cudaFreeHost(g->h_roots);
   dev_free(g->sb_state, st);
+  dev_free(g->mss_state, st);
   dev_free(g->pr_ws, st);
   dev_free(g->chunk_cnt, st);
   dev_free(g->dstats, st);

@@ -59,6 +59,8 @@ struct simdx_graph {
   int sb_k = 0;
   void* pr_ws = nullptr;                   // PageRank in-edge walk layout (first use)
   size_t pr_bytes = 0;
+  void* mss_state = nullptr;               // shared-edge batched SSSP state (first use)
+  size_t mss_bytes = 0;
   void* mg_pack = nullptr;                 // simdx_bfs_multigraph pack with this graph first
   unsigned long long gen = 0;              // creation number (distinguishes reused addresses)
   uint32_t* bitmaps = nullptr;  // [4][words]
@@ -125,6 +127,10 @@ int cuda_status(cudaError_t e, const char* what);
 // to the driver each time.  dev_alloc / dev_free are ordered on `st`.
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
 void dev_free(void* p, cudaStream_t st);
+
+// Batched SSSP with the sources sharing each edge read (msssp.cu).
+int sssp_batch_shared(simdx_graph* g, const int32_t* srcs, int k, uint32_t* dist, simdx_stats* stats,
+                      cudaStream_t st);
 
 // Creation numbers of graph objects, and the simdx_bfs_multigraph pack a
 // graph may own (freed with it).

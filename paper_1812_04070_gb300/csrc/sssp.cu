@@ -771,6 +771,9 @@ extern "C" int simdx_sssp_batch(simdx_graph* g, const int32_t* srcs, int32_t k, 
     if (srcs[i] < 0 || srcs[i] >= g->n) return SIMDX_EINVAL;
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // default: every source of a launch shares the edge reads (msssp.cu); the
+  // batch_group knob selects virtual graph copies in groups instead
+  if (g->cfg.batch_group == 0) return sssp_batch_shared(g, srcs, k, dist, stats, st);
   int rc = ensure_sssp_batch_state(g, sssp_group(g, k), k, st);
   if (rc) return rc;
   return g->off_bits == 32 ? run_sssp_batch<int32_t>(g, srcs, k, dist, stats, st)

@@ -17,7 +17,7 @@ import os
 from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, EBARRIER_TIMEOUT, EUNSUPPORTED, EBUSY, ENOTREADY = range(8)
-ALGO_BFS, ALGO_SSSP, ALGO_KCORE, ALGO_PAGERANK = 1, 2, 3, 4
+ALGO_BFS, ALGO_SSSP, ALGO_KCORE, ALGO_PAGERANK, ALGO_BFS_MULTI = 1, 2, 3, 4, 5
 INPUT_HOST = 1
 BORROW = 2
 
@@ -100,6 +100,8 @@ SIGNATURES = {
     "simdx_server_destroy": (ctypes.c_int, [_vp]),
     "simdx_autotune": (ctypes.c_int, [_vp, _i32, _i64, _i32, ctypes.POINTER(simdx_config),
                                       ctypes.POINTER(ctypes.c_float), _vp]),
+    "simdx_autotune_batch": (ctypes.c_int, [_vp, _i32, _vp, _i32, _i32, ctypes.POINTER(simdx_config),
+                                            ctypes.POINTER(ctypes.c_float), _vp]),
 }
 
 
@@ -304,4 +306,13 @@ def simdx_autotune(g: int, algo: int, arg: int, reps: int, stream: int | None) -
     best, ms = simdx_config(), ctypes.c_float()
     _check(_lib().simdx_autotune(g, algo, arg, reps, ctypes.byref(best), ctypes.byref(ms), stream),
            "simdx_autotune")
+    return best, ms.value
+
+
+def simdx_autotune_batch(g: int, algo: int, srcs, reps: int, stream: int | None) -> tuple[simdx_config, float]:
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    best, ms = simdx_config(), ctypes.c_float()
+    _check(_lib().simdx_autotune_batch(g, algo, a.ctypes.data, int(a.size), reps, ctypes.byref(best),
+                                       ctypes.byref(ms), stream), "simdx_autotune_batch")
     return best, ms.value

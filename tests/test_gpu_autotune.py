@@ -56,3 +56,30 @@ def test_autotune_rejects_bad_arguments():
         G.autotune(simdx.ALGO_SSSP, 0)
     assert e.value.status == simdx.EUNSUPPORTED
     G.close()
+
+
+def test_autotune_batch_calls():
+    """simdx_autotune_batch tunes the batched calls (bit-parallel BFS batch,
+    SSSP batch, multi-root BFS); the results stay identical to the oracle."""
+    from paper_1812_04070_gb300 import SimdxError, simdx
+    g = gg.rmat(12)
+    w = gg.weights(g, 4, 1, 64)
+    G = make(g, w, bits=32)
+    srcs = [int(s) for s in gg.pick_sources(g, 12, seed=5)]
+    for algo in (simdx.ALGO_BFS, simdx.ALGO_SSSP, simdx.ALGO_BFS_MULTI):
+        best, ms = G.autotune_batch(algo, srcs, reps=2)
+        assert ms > 0
+        for k, v in best.items():
+            assert getattr(G.config, k) == pytest.approx(v), (algo, k)
+    lb = G.bfs_batch(srcs).cpu().numpy()
+    db = G.sssp_batch(srcs).cpu().numpy().view(np.uint32)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(lb[i], oracle.bfs(g.offsets, g.indices, s))
+        assert np.array_equal(db[i], oracle.sssp(g.offsets, g.indices, w, s))
+    lm = G.bfs_multi(srcs).cpu().numpy()
+    ref = np.min(np.stack([np.where(x < 0, 1 << 30, x) for x in lb]), axis=0)
+    assert np.array_equal(lm, np.where(ref == 1 << 30, -1, ref))
+    with pytest.raises(SimdxError) as e:
+        G.autotune_batch(simdx.ALGO_KCORE, srcs)
+    assert e.value.status == simdx.EINVAL
+    G.close()
