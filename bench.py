@@ -594,7 +594,7 @@ def run_batch(args, rank, world, local):
     (configuration of the batching workload; identical outputs are checked)."""
     import torch
     import graphgen as gg
-    from paper_1812_04070_gb300 import Graph, build
+    from paper_1812_04070_gb300 import Graph, build, simdx_stats
     torch.cuda.set_device(local)
     build()
     wl = WORKLOADS[args.workload]
@@ -606,13 +606,42 @@ def run_batch(args, rank, world, local):
     o1 = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
     reps = max(1, min(args.steps, 5))
     res = {}
+    tuned = {}
+    if args.autotune:
+        from paper_1812_04070_gb300 import simdx
+        default = {k: getattr(G.config, k) for k, _ in G.config._fields_ if k != "reserved"}
+        for name, algo in [("bfs", simdx.ALGO_BFS), ("sssp", simdx.ALGO_SSSP)]:
+            Gt = Graph(g.offsets.astype(np.int32), g.indices, weights=w)
+            best, ms = Gt.autotune_batch(algo, srcs, reps=2)
+            Gt.close()
+            tuned[name] = {k: v for k, v in best.items() if v != default[k]}
+            tuned[name + "_full"] = best
     for name, bat, one in [("bfs", lambda: G.bfs_batch(srcs, out=ob), lambda: [G.bfs(s, out=o1[i]) for i, s in enumerate(srcs)]),
                            ("sssp", lambda: G.sssp_batch(srcs, out=ob), lambda: [G.sssp(s, out=o1[i]) for i, s in enumerate(srcs)])]:
+        ts = _ev_time(one, reps)  # one call per query, default knobs
+        if name + "_full" in tuned:
+            G.set_config(**tuned[name + "_full"])
+        st = simdx_stats()
+        G.bfs_batch(srcs, out=ob, stats=st) if name == "bfs" else G.sssp_batch(srcs, out=ob, stats=st)
+        torch.cuda.synchronize()
         tb = _ev_time(bat, reps)
-        ts = _ev_time(one, reps)
         same = bool(torch.equal(ob, o1))
         res[name] = {"batched_qps": round(64 / tb * 1e3, 1), "per_query_qps": round(64 / ts * 1e3, 1),
-                     "batched_ms": round(tb, 3), "per_query_ms": round(ts, 3), "identical": same}
+                     "batched_ms": round(tb, 3), "per_query_ms": round(ts, 3), "identical": same,
+                     "launches": st.launches, "iterations": st.iterations}
+        if name + "_full" in tuned:
+            res[name]["knobs"] = tuned[name]
+            G.set_config(**{k: v for k, v in default.items()})
+    # the earlier batched SSSP layout for comparison: virtual graph copies in
+    # cache-sized groups, one launch per group (batch_group knob)
+    G.set_config(batch_group=8)
+    st = simdx_stats()
+    G.sssp_batch(srcs, out=ob, stats=st)
+    torch.cuda.synchronize()
+    tg = _ev_time(lambda: G.sssp_batch(srcs, out=ob), reps)
+    res["sssp_virtual_copies"] = {"batched_qps": round(64 / tg * 1e3, 1), "batched_ms": round(tg, 3),
+                                  "launches": st.launches, "identical": bool(torch.equal(ob, o1))}
+    G.set_config(batch_group=0)
     G.close()
     graphs, gsrc = gg.multigraph_batch(count=256)
     packed, bases = gg.pack(graphs)

@@ -26,9 +26,17 @@ def device():
     torch.cuda.set_device(0)
 
 
+_CACHE = {}
+
+
 def _rmat(scale, wmax=64):
-    g = gg.rmat(scale)
-    return g, gg.weights(g, gg.weight_seed(scale), 1, wmax)
+    """The bench's R-MAT graph and weights (generated once per module)."""
+    if (scale, wmax) not in _CACHE:
+        if scale >= 24:
+            _CACHE.clear()  # keep one large graph in host memory
+        g = gg.rmat(scale)
+        _CACHE[(scale, wmax)] = (g, gg.weights(g, gg.weight_seed(scale), 1, wmax))
+    return _CACHE[(scale, wmax)]
 
 
 def test_rmat16_bfs():
@@ -69,6 +77,36 @@ def test_rmat24_bfs_sssp():
     assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
     assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
     assert np.array_equal(G.wcc().cpu().numpy().view(np.uint32), oracle.wcc(g.offsets, g.indices))
+    G.close()
+
+
+def test_rmat24_pagerank_kcore_coreness():
+    """The bench's rmat24-pagerank, rmat24-kcore and rmat24-coreness
+    workloads at full size: PageRank (pull only here: R-MAT's pull contracts
+    fast) within 1e-6 of the FP64 oracle after the same iterations; k-core
+    membership and residual degrees and every core number bit for bit."""
+    g, w = _rmat(24)
+    G = make(g, w, bits=64)
+    st, rel = assert_pagerank(G, g)
+    assert st.push_iters == 0
+    print(f"PageRank R-MAT 24: {st.iterations} iterations, relative L1 {rel:.2e} vs the FP64 oracle")
+    inc, resid = G.kcore(16)
+    ei, er = oracle.kcore_par(g.offsets, g.indices, 16)
+    assert np.array_equal(inc.cpu().numpy(), ei) and np.array_equal(resid.cpu().numpy().view(np.uint32), er)
+    assert np.array_equal(G.coreness().cpu().numpy().view(np.uint32), oracle.coreness(g.offsets, g.indices))
+    G.close()
+
+
+def test_grid4096_pagerank_push_tail():
+    """PageRank on the 4096 x 4096 grid switches to push (the pull contracts
+    slowly and few vertices are unstable); the result is within d / (1 - d) *
+    tol + 1e-6 (L1) of the converged FP64 fixed point."""
+    g = gg.grid(4096, 4096)
+    G = make(g, bits=64)
+    st, err = assert_pagerank(G, g)
+    assert st.push_iters > 0 and st.launches == 2
+    print(f"PageRank grid 4096^2: {st.pull_iters} pull + {st.push_iters} push iterations, L1 error {err:.2e} "
+          f"vs the converged fixed point")
     G.close()
 
 
