@@ -712,6 +712,21 @@ def run_serve(args, rank, world, local):
     qs = make(400)
     o32 = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in raw]
     o8 = [torch.empty(g.n, dtype=torch.uint8, device="cuda") for g in raw]
+    # capacity model: GPU time per query of each (graph, algorithm) when the
+    # server forms full batches (64 BFS, max_sssp SSSP per launch; one k-core
+    # run answers every waiting k-core query, counted here as one run per
+    # query), on the whole GPU; the mix weights them (graph uniform, 50/40/10)
+    max_sssp = 8
+    ob = torch.empty((64, max(g.n for g in raw)), dtype=torch.int32, device="cuda")
+    cost = {}
+    for gi, g in enumerate(raw):
+        s64 = [int(x) for x in srcs[gi][:64]]
+        tb = _ev_time(lambda: Gs[gi].bfs_batch(s64, out=ob), 3) / 64
+        ts = _ev_time(lambda: Gs[gi].sssp_batch(s64[:max_sssp], out=ob), 3) / max_sssp
+        tk = _ev_time(lambda: Gs[gi].kcore(16, out=o8[gi], want_resid=False), 3)
+        cost[scales[gi]] = {"bfs_ms": round(tb, 4), "sssp_ms": round(ts, 4), "kcore_ms": round(tk, 4)}
+    per_q_ms = sum(0.5 * c["bfs_ms"] + 0.4 * c["sssp_ms"] + 0.1 * c["kcore_ms"] for c in cost.values()) / len(raw)
+    ceiling = 1e3 / per_q_ms
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for gi, a, arg in qs:
@@ -723,7 +738,7 @@ def run_serve(args, rank, world, local):
             Gs[gi].kcore(arg, out=o8[gi])
     torch.cuda.synchronize()
     per_query = len(qs) / (time.perf_counter() - t0)
-    srv = Server(Gs, mem_budget=64 << 30, max_slots=4, max_sssp=8)
+    srv = Server(Gs, mem_budget=64 << 30, max_slots=4, max_sssp=max_sssp)
     rates = []
     for rate in [1000, 2000, 5000, 10000, 20000, 50000]:
         m = min(4000, rate * 2)
@@ -732,7 +747,7 @@ def run_serve(args, rank, world, local):
                 for gi, a, _ in q]
         gaps = rng.exponential(1.0 / rate, size=m)
         t_sub, t_done, tk = np.zeros(m), np.zeros(m), [None] * m
-        pending, i = set(), 0
+        pending, i = [], 0  # in submission order
         start = time.perf_counter()
         nxt = start
         while i < m or pending:
@@ -741,13 +756,19 @@ def run_serve(args, rank, world, local):
                 gi, a, arg = q[i]
                 tk[i] = srv.submit(gi, a, arg, bufs[i])
                 t_sub[i] = nxt
-                pending.add(i)
+                pending.append(i)
                 nxt += gaps[i]
                 i += 1
-            for j in list(pending):
-                if srv.poll(tk[j]):
+            # poll the oldest 64 queries only: the client's loop stays O(1) per
+            # query at high rates (a query answered out of order is seen once
+            # it is among the oldest, which adds at most the wait for those)
+            keep = []
+            for idx, j in enumerate(pending):
+                if idx < 64 and srv.poll(tk[j]):
                     t_done[j] = time.perf_counter()
-                    pending.discard(j)
+                else:
+                    keep.append(j)
+            pending = keep
         tot = time.perf_counter() - start
         lat = (t_done - t_sub) * 1e3
         rates.append({"offered_qps": rate, "served_qps": round(job_rate(m, tot, world), 1),
@@ -761,7 +782,10 @@ def run_serve(args, rank, world, local):
     return {"metric": "queries/s (served)", "value": best, "unit": "queries/s", "n_gpus": world, "steps": len(rates),
             "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded R-MAT)", "config": {"workload": args.workload, "description": wl["desc"]},
-            "per_query_qps": round(per_query, 1), "rates": rates, "server": info}
+            "per_query_qps": round(per_query, 1), "rates": rates, "server": info,
+            "capacity_model": {"gpu_ms_per_query_full_batches": round(per_q_ms, 4),
+                               "ceiling_qps": round(ceiling, 1), "served_over_ceiling": round(best / ceiling, 3),
+                               "cost_by_scale": cost}}
 
 
 def run_ablation(args, rank, world, local):
@@ -790,7 +814,9 @@ def run_ablation(args, rank, world, local):
     fl = lambda f, x: (f"fusion={['all', 'selective', 'none'][f]} filter={'JIT' if x == 0 else 'ballot'}",
                        dict(fusion=f, filter=x))
     modes = {"bfs": [fl(0, 0), fl(1, 0), fl(2, 0), fl(0, 2), fl(2, 2)],
-             "sssp": [fl(0, 0), fl(2, 0), fl(0, 2), fl(2, 2)], "kcore": [fl(0, 0), fl(0, 2)],
+             "sssp": [fl(0, 0), fl(2, 0), fl(0, 2), fl(2, 2),
+                      ("combine=plain stores + pull sweeps (no atomics)", dict(fusion=0, filter=0, sssp_combine=1))],
+             "kcore": [fl(0, 0), fl(0, 2)],
              "pagerank": [("pull, then push (default switch rule)", dict(pr_alpha=8.0)),
                           ("pull only", dict(pr_alpha=0.0))]}
 
@@ -840,7 +866,7 @@ def run_ablation(args, rank, world, local):
                 row["identical"] = bool(torch.equal(o, ref))
             rows.append(row)
         res[a] = rows
-        G.set_config(fusion=0, filter=0, pr_alpha=8.0)
+        G.set_config(fusion=0, filter=0, pr_alpha=8.0, sssp_combine=0)
     G.close()
     base = res[wl["algs"][0]][0]
     return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],

@@ -154,7 +154,13 @@ typedef struct {
                                 fewer than E / pr_alpha out-edges; 0 = pull only [8] */
     float pr_theta;          /* push threshold, in units of the mean pending change [2] */
     float pr_rho;            /* slowest pull contraction that still keeps pulling [0.6] */
-    int32_t reserved[3];
+    int32_t sssp_combine;    /* simdx_sssp push combine (Sec. 3.2) [0]: 0 atomicMin; 1 plain
+                                stores (no atomics; a racing smaller value may be overwritten),
+                                then pull sweeps over every vertex until none lowers a distance
+                                (exact; symmetric graphs, all fusion, push; else EUNSUPPORTED).
+                                Trace records mark plain-store iterations with bit 17 and the
+                                sweeps with bit 18. */
+    int32_t reserved[2];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;

@@ -196,7 +196,8 @@ size_t slot_bytes(const simdx_graph* g, int max_sssp) {
   const size_t bins = sizeof(int32_t) * 4 * (size_t)g->grid_max * std::max(1, g->bin_cap);
   const size_t state = 20 * n + 16 * n + 8 * ((size_t)g->e / std::max(1, g->cfg.huge_min) + n);
   const size_t ms = 24 * n;
-  const size_t sb = g->w ? 45 * n * (size_t)max_sssp : 0;
+  // batched SSSP: vertex-major distances (32 or 64 words per vertex) and two masks
+  const size_t sb = g->w ? (4 * (size_t)(max_sssp > 32 ? 64 : 32) + 16) * n : 0;
   return lists + bins + state + ms + sb;
 }
 

@@ -65,6 +65,7 @@ struct SsspPush {
   const Knobs& k;
   unsigned grid;
   bool dense = false;  // land improvements only: no pending flags, no records
+  bool plain = false;  // combine by plain stores (no atomics); sweeps verify the result
   unsigned long long nrec = 0, mrec = 0;
   __device__ SsspPush(const SsspArgs<OffT>& a, uint32_t* pd, uint8_t* pe, uint32_t* ax, unsigned long long t,
                       CtaShared& s, unsigned g)
@@ -145,14 +146,26 @@ struct SsspPush {
       // scanning dist < pdist
 #pragma unroll
       for (int q = 0; q < kPushBatch; ++q)
-        if (nd[q] < cur[q]) atomicMin(&dist[x[q]], (uint32_t)nd[q]);
+        if (nd[q] < cur[q]) {
+          if (plain) dist[x[q]] = (uint32_t)nd[q];
+          else atomicMin(&dist[x[q]], (uint32_t)nd[q]);
+        }
       return;
     }
     uint32_t old[kPushBatch];
 #pragma unroll
     for (int q = 0; q < kPushBatch; ++q) {
       old[q] = 0;
-      if (nd[q] < cur[q]) old[q] = atomicMin(&dist[x[q]], (uint32_t)nd[q]);
+      if (nd[q] < cur[q]) {
+        if (plain) {
+          // a racing smaller store may be overwritten: the sweeps at the end
+          // find every distance left too large
+          dist[x[q]] = (uint32_t)nd[q];
+          old[q] = cur[q];
+        } else {
+          old[q] = atomicMin(&dist[x[q]], (uint32_t)nd[q]);
+        }
+      }
     }
 #pragma unroll
     for (int q = 0; q < kPushBatch; ++q) {
@@ -214,6 +227,38 @@ struct SsspPull {
   }
 };
 
+// Verification sweep of the atomic-free combine (scope reading: plain-store
+// min in push, then pull sweeps until no distance drops): every vertex with
+// an in-edge takes the min of dist[v] + w over all its in-neighbours and, the
+// owner, lowers its own distance (owner writes, no atomics).  A vertex it
+// lowers becomes pending, so its out-edges are pushed again.  When a sweep
+// lowers nothing, dist[u] <= dist[v] + w holds on every edge: the distances
+// are the shortest.  Symmetric graphs (in-edge weight = CSR weight).
+template <class OffT>
+struct SsspVerify {
+  using Acc = unsigned;
+  const uint32_t* wt;
+  uint32_t* dist;
+  uint8_t* pend;
+  unsigned long long changed = 0;
+  __device__ __forceinline__ Acc zero() const { return 0xffffffffu; }
+  __device__ __forceinline__ void combine(Acc& a, Acc b) const { a = b < a ? b : a; }
+  __device__ __forceinline__ void edge(Acc& a, int, int v, long long p) {
+    const uint32_t dv = dist[v];
+    if (dv != 0xffffffffu) {
+      const unsigned long long c = (unsigned long long)dv + gload(wt + p);
+      if (c < a) a = (unsigned)c;
+    }
+  }
+  __device__ __forceinline__ void finish(int u, Acc best) {
+    if (best < dist[u]) {
+      dist[u] = best;
+      pend[u] = 1;
+      ++changed;
+    }
+  }
+};
+
 // A push iteration whose task lists hold more than 1/kDenseDiv of all edges
 // is dense: most of its improvements would be recorded, and one scan of
 // dist < pdist over all vertices costs less than recording them.
@@ -234,7 +279,9 @@ static_assert(kRsPhases < kResumeWords, "resume record too small");
 
 // SPLIT: the no-fusion instantiation, which stops after one iteration and
 // leaves its loop state in the resume record for the next launch.
-template <class OffT, bool V, bool PULL, bool W = false, bool SPLIT = false>
+// VERIFY: the atomic-free combine (plain-store min in push, then pull
+// sweeps until no distance drops).
+template <class OffT, bool V, bool PULL, bool W = false, bool SPLIT = false, bool VERIFY = false>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
   __shared__ unsigned red_u[kWarps];
@@ -472,7 +519,42 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
         const unsigned long long mn = ~p.aux2;
         Tn = delta ? (mn / delta + 1) * delta : kInfT;  // (delta > 0 here)
       }
-      if (done) break;
+      if (done) {
+        if (!VERIFY) break;
+        // atomic-free combine: a pull sweep over every vertex with an
+        // in-edge; done when it lowers no distance
+        clear_next_slot(s, sh);
+        {
+          PhaseSlot& slot_c = s->slot[slot_of(sh.phase)];
+          auto deg = [off = a.off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
+          auto none = [](int) {};
+          bitmap_filter(n, a.w.bm_nz, deg, none, sh, a.w, k, grid, lbuf, slot_c);
+        }
+        if (!grid_sync(s, grid, sh, k)) return;
+        unsigned cc[kClasses];
+        {
+          const PhaseSlot& pc = s->slot[slot_of(sh.phase - 1)];
+          for (int c = 0; c < kClasses; ++c) cc[c] = pc.list_cnt[c];
+        }
+        clear_next_slot(s, sh);
+        PhaseSlot& slot_v = s->slot[slot_of(sh.phase)];
+        SsspVerify<OffT> fv{a.wt, a.dist, pend};
+        const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                          a.w.list[lbuf][3]};
+        pull_classes<OffT>(fv, a.off, a.idx, lists, cc, grid, red_u, k.huge_min, sh, a.w, evisit, &slot_v);
+        const unsigned long long ch = cta_sum_u64(fv.changed, sh);
+        if (threadIdx.x == 0 && ch) atomicAdd(&slot_v.aux0, ch);
+        if (!grid_sync(s, grid, sh, k)) return;
+        const unsigned long long lowered = s->slot[slot_of(sh.phase - 1)].aux0;
+        trace_put(a.w, it, 2 | (2 << 8) | (1 << 18), (long long)(cc[0] + cc[1] + cc[2] + cc[3]),
+                  (long long)lowered, (long long)(T == kInfT ? -1 : (long long)T), t_it);
+        ++it;
+        ++pull_it;
+        ++ballot_it;
+        if (lowered == 0) break;
+        lists_ok = false;  // the lowered vertices are pending: the ballot filter lists them
+        continue;
+      }
       filt = 2;
       if (total == 0) continue;  // (cannot happen: the jump bucket holds the min)
     }
@@ -542,6 +624,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       __syncthreads();
       PhaseSlot& slot = s->slot[slot_of(sh.phase)];
       SsspPush<OffT, V, W> f(a, pdist, pend, a.w.aux3[lbuf], T, sh, grid);
+      f.plain = VERIFY;
       f.dense = mf * kDenseDiv > m_all;
       scan_all = f.dense;
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
@@ -562,7 +645,8 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       // a batch's later group launches (and WCC after its BFS) number their
       // records on from the iterations the launches before them recorded
       const int ti = it + ((V || W) ? a.w.stats->iterations : 0);
-      trace_put(a.w, ti, (pull ? 2 : 1) | (filt << 8) | (scan_all ? 1 << 16 : 0), (long long)total, 0,
+      trace_put(a.w, ti, (pull ? 2 : 1) | (filt << 8) | (scan_all ? 1 << 16 : 0) | ((VERIFY && !pull) ? 1 << 17 : 0),
+                (long long)total, 0,
                 (long long)(T == kInfT ? -1 : (long long)T), t_it);
       trace_classes(a.w, ti, p);
     }
@@ -623,6 +707,14 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
   // all and selective fusion are one launch (an SSSP run computes in one
   // direction); no fusion runs one launch per iteration until the kernel
   // reports the run finished
+  if (g->cfg.sssp_combine == 1) {
+    // the atomic-free combine (measured against atomicMin); its sweeps pull
+    // with the CSR weights, so the graph must be symmetric
+    if (!g->symmetric || pull || a.k.fusion == 2) return SIMDX_EUNSUPPORTED;
+    const void* kern = (const void*)sssp_kernel<OffT, false, false, false, false, true>;
+    if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
+    return finish_launch(g, stats, st);
+  }
   if (a.k.fusion != 2) {
     const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true> : (const void*)sssp_kernel<OffT, false, false>;
     if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;

@@ -340,3 +340,35 @@ def test_fusion_launch_counts():
     assert np.array_equal(d0, d2) and sn.iterations == sd.iterations and sd.launches == 1
     assert sn.launches in (sn.iterations, sn.iterations + 1)
     G.close()
+
+
+@pytest.mark.parametrize("mode", ["default", "all_classes", "overflow", "ballot", "one_cta_per_sm"])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_sssp_atomic_free_combine(gi, mode):
+    """SSSP push with plain-store min (no atomics) and pull sweeps until no
+    distance drops: exact distances; the trace marks the plain-store
+    iterations and ends with a sweep that lowered nothing."""
+    g = GRAPHS[gi]
+    w = gg.weights(g, 77 + gi, 1, 64)
+    G = make(g, w, bits=64 if gi % 2 else 32, sssp_combine=1, **FORCED[mode])
+    for s in sources(g):
+        d = G.sssp(s).cpu().numpy().view(np.uint32)
+        assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, s)), (g.name, mode, s)
+        tr = G.trace()
+        flags = [int(r[0]) for r in tr]
+        assert (flags[-1] >> 18) & 1 and int(tr[-1][2]) == 0
+        assert all(((f >> 17) & 1) for f in flags if (f & 0xff) == 1)
+    G.close()
+
+
+def test_sssp_atomic_free_combine_rejects_directed():
+    from paper_1812_04070_gb300 import SimdxError, simdx
+    from gpu_util import directed_graph
+    from paper_1812_04070_gb300 import Graph
+    off, idx, ioff, iidx, w = directed_graph(300, 1500, 4)
+    G = Graph(off, idx, weights=w, csc=(ioff, iidx))
+    G.set_config(sssp_combine=1)
+    with pytest.raises(SimdxError) as e:
+        G.sssp(0)
+    assert e.value.status == simdx.EUNSUPPORTED
+    G.close()

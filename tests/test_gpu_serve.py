@@ -105,3 +105,68 @@ def test_server_rejects_bad_queries():
     assert np.array_equal(out.cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
     srv.close()
     G.close()
+
+
+def test_server_eight_graphs_config5():
+    """The serving configuration's eight resident graphs (R-MAT scales 14-20
+    and 22, weights [1,64]) and its query mix (50 % BFS, 40 % SSSP, 10 %
+    k-core 16, uniform graph, uniform non-isolated source), submitted in
+    bursts while earlier queries run: every result equals the same query run
+    alone, and a sample equals the oracle."""
+    import torch
+    from paper_1812_04070_gb300 import Graph, Server, build
+    build()
+    torch.cuda.set_device(0)
+    scales = [14, 15, 16, 17, 18, 19, 20, 22]
+    raw = [gg.rmat(sc) for sc in scales]
+    ws = [gg.weights(g, gg.weight_seed(sc), 1, 64) for g, sc in zip(raw, scales)]
+    Gs = [Graph(g.offsets.astype(np.int32), g.indices, weights=w) for g, w in zip(raw, ws)]
+    srcs = [gg.pick_sources(g, 64, 0x5E77E + i) for i, g in enumerate(raw)]
+    rng = np.random.default_rng(0x5E77E)
+    queries = []
+    for _ in range(600):
+        gi = int(rng.integers(0, len(raw)))
+        r = rng.random()
+        algo = Server.BFS if r < 0.5 else Server.SSSP if r < 0.9 else Server.KCORE
+        arg = 16 if algo == Server.KCORE else int(srcs[gi][int(rng.integers(0, len(srcs[gi])))])
+        queries.append((gi, algo, arg))
+    solo = {}
+    for q in set(queries):
+        gi, algo, arg = q
+        if algo == Server.BFS:
+            solo[q] = Gs[gi].bfs(arg).cpu().numpy()
+        elif algo == Server.SSSP:
+            solo[q] = Gs[gi].sssp(arg).cpu().numpy()
+        else:
+            solo[q] = Gs[gi].kcore(arg)[0].cpu().numpy()
+    torch.cuda.synchronize()
+    srv = Server(Gs, mem_budget=64 << 30, max_slots=4, max_sssp=8)
+    outs = [torch.full((raw[gi].n,), 3, dtype=torch.uint8 if a == Server.KCORE else torch.int32, device="cuda")
+            for gi, a, _ in queries]
+    tickets = []
+    for lo in range(0, len(queries), 50):  # bursts of 50 while earlier ones run
+        for i in range(lo, min(lo + 50, len(queries))):
+            gi, algo, arg = queries[i]
+            tickets.append(srv.submit(gi, algo, arg, outs[i]))
+    for tk in tickets:
+        srv.wait(tk)
+    info = srv.info()
+    srv.close()
+    assert info["served"] == len(queries) and info["launches"] < len(queries), info
+    for i, q in enumerate(queries):
+        assert np.array_equal(outs[i].cpu().numpy(), solo[q]), (i, q)
+    seen = set()
+    for i, (gi, algo, arg) in enumerate(queries):
+        if (gi, algo) in seen or scales[gi] > 20:
+            continue
+        seen.add((gi, algo))
+        g = raw[gi]
+        if algo == Server.BFS:
+            exp = oracle.bfs(g.offsets, g.indices, arg)
+        elif algo == Server.SSSP:
+            exp = oracle.sssp(g.offsets, g.indices, ws[gi], arg).view(np.int32)
+        else:
+            exp = oracle.kcore(g.offsets, g.indices, arg)[0]
+        assert np.array_equal(outs[i].cpu().numpy(), exp), (i, gi, algo, arg)
+    for G in Gs:
+        G.close()
