@@ -632,6 +632,15 @@ def run_batch(args, rank, world, local):
         if name + "_full" in tuned:
             res[name]["knobs"] = tuned[name]
             G.set_config(**{k: v for k, v in default.items()})
+    # the shared-edge batch at every group width
+    for width in (8, 16, 32, 64):
+        G.set_config(sssp_batch_width=width)
+        G.sssp_batch(srcs, out=ob)
+        torch.cuda.synchronize()
+        tw = _ev_time(lambda: G.sssp_batch(srcs, out=ob), reps)
+        res[f"sssp_width{width}"] = {"batched_qps": round(64 / tw * 1e3, 1), "batched_ms": round(tw, 3),
+                                     "identical": bool(torch.equal(ob, o1))}
+    G.set_config(sssp_batch_width=0)
     # the earlier batched SSSP layout for comparison: virtual graph copies in
     # cache-sized groups, one launch per group (batch_group knob)
     G.set_config(batch_group=8)

@@ -160,7 +160,10 @@ typedef struct {
                                 (exact; symmetric graphs, all fusion, push; else EUNSUPPORTED).
                                 Trace records mark plain-store iterations with bit 17 and the
                                 sweeps with bit 18. */
-    int32_t reserved[2];
+    int32_t sssp_batch_width;  /* simdx_sssp_batch: sources per group of the shared-edge batch,
+                                8, 16, 32 or 64; 0 = 8 [0] (groups run one after another
+                                inside one launch per 64 sources) */
+    int32_t reserved[1];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;
@@ -313,18 +316,20 @@ SIMDX_API int simdx_bfs_batch(simdx_graph *g, const int32_t *srcs, int32_t k, in
                               simdx_stats *stats, void *stream);
 
 /* Batched SSSP (growth direction (a)): k sources, one persistent launch per
- * group of copies.  The queries of a group run on virtual copies of the
- * graph (state id inst * n + v, one CSR) with delta-stepping buckets shared
- * by the group, so every iteration processes the group's frontiers
- * together.  Groups are of equal size, as large as keeps a group's
- * distances within 128 MB (all k for graphs up to 32M / k vertices), or of
- * at most the batch_group knob, and run one after another on `stream`.  Up
- * to 64 sources per group travel as kernel parameters (the call can then be
- * captured into a CUDA graph); larger groups copy all k to the device first.
- * srcs: host int32[k]; dist: device uint32[k*n], row i = distances from
- * srcs[i], identical to k simdx_sssp calls.  The first call (or a larger
- * group than any before) allocates the batch state (about 45 bytes per
- * vertex per copy of a group); later calls reuse it.  Needs k * n < 2^31.
+ * 64 sources.  Inside a launch the sources run in groups of
+ * sssp_batch_width (default 8): a group keeps its distances vertex-major
+ * (one row of group-width words per vertex) and one task per vertex for all
+ * its sources whose distance there changed, so an edge is read once per
+ * iteration for the whole group and the relaxations of one edge touch one
+ * row (frontier Bellman-Ford per source, min combine by atomicMin).  The 64
+ * sources travel as a kernel parameter (the call can be captured into a
+ * CUDA graph).  srcs: host int32[k]; dist: device uint32[k*n], row i =
+ * distances from srcs[i], identical to k simdx_sssp calls.  The first call
+ * (or a wider group) allocates the batch state (4 x width + 16 bytes per
+ * vertex); later calls reuse it.  With the batch_group knob > 0 the earlier
+ * layout runs instead: virtual graph copies (state id inst * n + v) in groups
+ * of at most batch_group copies sharing delta-stepping buckets, one launch
+ * per group (about 45 bytes per vertex per copy; needs k * n < 2^31).
  * Errors: EINVAL, ENOMEM. */
 SIMDX_API int simdx_sssp_batch(simdx_graph *g, const int32_t *srcs, int32_t k, uint32_t *dist,
                                simdx_stats *stats, void *stream);

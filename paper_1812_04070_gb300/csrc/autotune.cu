@@ -60,7 +60,8 @@ std::vector<Knob> knobs_for_batch(int algo) {
   if (algo == SIMDX_ALGO_SSSP) {
     k.push_back({"bin_per_thread", {16, 32, 64, 128}, SIMDX_KNOB_I(bin_per_thread)});
     k.push_back({"delta", {16, 64, 256, 1024, 4096, 16384, 0}, SIMDX_KNOB_I(delta)});
-    k.push_back({"batch_group", {0, 1, 2, 4, 8, 16, 32, 64}, SIMDX_KNOB_I(batch_group)});
+    k.push_back({"sssp_batch_width", {8, 16, 32, 64}, SIMDX_KNOB_I(sssp_batch_width)});
+    k.push_back({"batch_group", {0, 2, 4, 8, 16}, SIMDX_KNOB_I(batch_group)});
   }
   return k;
 }

@@ -57,7 +57,8 @@ class simdx_config(ctypes.Structure):
                 ("debug_skip_cta", ctypes.c_int32), ("debug_skip_phase", ctypes.c_int32),
                 ("batch_group", ctypes.c_int32), ("fusion", ctypes.c_int32),
                 ("pr_alpha", ctypes.c_float), ("pr_theta", ctypes.c_float), ("pr_rho", ctypes.c_float),
-                ("sssp_combine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("sssp_combine", ctypes.c_int32), ("sssp_batch_width", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 _LIB = None

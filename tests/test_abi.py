@@ -73,7 +73,8 @@ def test_config_layout_matches_header(lib):
     words = sum(int(n) if n else 1 for _, _, n in fields)
     assert ctypes.sizeof(simdx.simdx_config) == 4 * words
     c = simdx.simdx_config_default()
-    assert c.batch_group == 0 and c.fusion == 0 and c.sssp_combine == 0 and list(c.reserved) == [0] * 2
+    assert c.batch_group == 0 and c.fusion == 0 and c.sssp_combine == 0 and c.sssp_batch_width == 0
+    assert list(c.reserved) == [0]
     assert (c.pr_alpha, c.pr_theta, c.pr_rho) == (8.0, 2.0, pytest.approx(0.6))
 
 

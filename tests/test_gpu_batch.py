@@ -38,13 +38,20 @@ def test_bfs_batch(gi, k):
     G.close()
 
 
-@pytest.mark.parametrize("mode", ["default", "ballot", "overflow", "all_classes", "one_cta_per_sm"])
+SSSP_BATCH_MODES = {**{m: FORCED[m] for m in ["default", "ballot", "overflow", "all_classes", "one_cta_per_sm"]},
+                    "width16": dict(sssp_batch_width=16), "width32": dict(sssp_batch_width=32),
+                    "width64": dict(sssp_batch_width=64),
+                    "width64_all_classes": dict(sssp_batch_width=64, small_max=2, med_max=4, huge_min=8),
+                    "virtual_copies": dict(batch_group=4)}
+
+
+@pytest.mark.parametrize("mode", list(SSSP_BATCH_MODES))
 @pytest.mark.parametrize("gi", range(len(BATCH_GRAPHS)))
 def test_sssp_batch(gi, mode):
     g = BATCH_GRAPHS[gi]
     w = gg.weights(g, 5 + gi, 1, 64)
     srcs = list(gg.pick_sources(g, 9, seed=7)) + [0]
-    G = make(g, w, bits=64 if gi % 2 else 32, **FORCED[mode])
+    G = make(g, w, bits=64 if gi % 2 else 32, **SSSP_BATCH_MODES[mode])
     out = G.sssp_batch(srcs).cpu().numpy().view(np.uint32)
     for i, s in enumerate(srcs):
         assert np.array_equal(out[i], oracle.sssp(g.offsets, g.indices, w, int(s))), (g.name, mode, i)
@@ -71,14 +78,21 @@ def test_bfs_multigraph_pack(mode):
     G.close()
 
 
-@pytest.mark.parametrize("k", [1, 33, 64, 70])
-def test_sssp_batch_sizes(k):
-    """Up to 64 sources travel as a kernel parameter, more through device
-    memory."""
+@pytest.mark.parametrize("width", [8, 64])
+@pytest.mark.parametrize("k", [1, 33, 64, 70, 130])
+def test_sssp_batch_sizes(k, width):
+    """Up to 64 sources per launch travel as a kernel parameter, in groups of
+    the batch width; more than 64 take several launches."""
+    import torch
+    from paper_1812_04070_gb300 import simdx_stats
     g = gg.rmat(11)
     w = gg.weights(g, 99, 1, 64)
     srcs = np.resize(gg.pick_sources(g, 50, seed=k), k)
-    G = make(g, w, bits=32)
+    G = make(g, w, bits=32, sssp_batch_width=width)
+    st = simdx_stats()
+    G.sssp_batch([int(s) for s in srcs], stats=st)
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.launches == -(-k // 64)
     out = G.sssp_batch([int(s) for s in srcs]).cpu().numpy().view(np.uint32)
     for i, s in enumerate(srcs):
         assert np.array_equal(out[i], oracle.sssp(g.offsets, g.indices, w, int(s))), (k, i)
