@@ -63,6 +63,12 @@ WORKLOADS = {
                             desc="R-MAT scale 24, int64 offsets: PageRank d=0.85 tol 1e-6"),
     "rmat24-kcore": dict(kind="rmat", scale=24, bits=64, algs=["kcore"],
                          desc="R-MAT scale 24, int64 offsets: k-core k=16"),
+    "rmat20-kcore": dict(kind="rmat", scale=20, bits=32, algs=["kcore"],
+                         desc="R-MAT scale 20, int32 CSR: k-core k=16 (profiling size)"),
+    "rmat20-pagerank": dict(kind="rmat", scale=20, bits=32, algs=["pagerank"],
+                            desc="R-MAT scale 20, int32 CSR: PageRank d=0.85 tol 1e-6 (profiling size)"),
+    "rmat20-sssp": dict(kind="rmat", scale=20, bits=32, algs=["sssp"],
+                        desc="R-MAT scale 20, int32 CSR, w in [1,64]: SSSP src 0 (profiling size)"),
     "rmat20-coreness": dict(kind="rmat", scale=20, bits=32, algs=["coreness"],
                             desc="R-MAT scale 20, int32 CSR: k-core decomposition (coreness of every vertex)"),
     "rmat24-coreness": dict(kind="rmat", scale=24, bits=64, algs=["coreness"],
@@ -90,6 +96,10 @@ WORKLOADS = {
                                    "selective and no kernel fusion (Sec. 5, Table 2); JIT vs ballot-only filter"),
     "grid4096-pr-ablation": dict(kind="ablation", graph="grid", rows=4096, bits=64, algs=["pagerank"],
                                  desc="4096x4096 4-neighbour grid: PageRank pull then push (Sec. 6) vs pull only"),
+    "rmat20-ablation": dict(kind="ablation", graph="rmat", scale=20, bits=32,
+                            algs=["pagerank", "sssp", "kcore", "bfs"],
+                            desc="R-MAT scale 20, int32 CSR: the ablations of rmat24-ablation at the default "
+                                 "workload's size"),
     "rmat24-ablation": dict(kind="ablation", graph="rmat", scale=24, bits=64,
                             algs=["bfs", "sssp", "kcore", "pagerank"],
                             desc="R-MAT scale 24, int64 offsets: BFS / SSSP src 0, k-core 16 and PageRank under all, "
@@ -820,11 +830,15 @@ def run_ablation(args, rank, world, local):
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     out8 = torch.empty(g.n, dtype=torch.uint8, device=dev)
     reps = max(3, min(args.steps, 7))
+    default_delta = G.config.delta
     fl = lambda f, x: (f"fusion={['all', 'selective', 'none'][f]} filter={'JIT' if x == 0 else 'ballot'}",
                        dict(fusion=f, filter=x))
     modes = {"bfs": [fl(0, 0), fl(1, 0), fl(2, 0), fl(0, 2), fl(2, 2)],
              "sssp": [fl(0, 0), fl(2, 0), fl(0, 2), fl(2, 2),
-                      ("combine=plain stores + pull sweeps (no atomics)", dict(fusion=0, filter=0, sssp_combine=1))],
+                      ("combine=plain stores + pull sweeps (no atomics)", dict(fusion=0, filter=0, sssp_combine=1)),
+                      ("delta=64", dict(sssp_combine=0, delta=64)), ("delta=256", dict(delta=256)),
+                      ("delta=unbounded", dict(delta=0)), ("pull every iteration", dict(delta=default_delta,
+                                                                                         direction=2))],
              "kcore": [fl(0, 0), fl(0, 2)],
              "pagerank": [("pull, then push (default switch rule)", dict(pr_alpha=8.0)),
                           ("pull only", dict(pr_alpha=0.0))]}
@@ -845,6 +859,7 @@ def run_ablation(args, rank, world, local):
     for a in wl["algs"]:
         ref = None
         rows = []
+        G.set_config(delta=default_delta, direction=0)
         for label, knobs in modes[a]:
             G.set_config(**knobs)
             st = simdx_stats()
@@ -875,7 +890,7 @@ def run_ablation(args, rank, world, local):
                 row["identical"] = bool(torch.equal(o, ref))
             rows.append(row)
         res[a] = rows
-        G.set_config(fusion=0, filter=0, pr_alpha=8.0, sssp_combine=0)
+        G.set_config(fusion=0, filter=0, pr_alpha=8.0, sssp_combine=0, delta=default_delta, direction=0)
     G.close()
     base = res[wl["algs"][0]][0]
     return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],

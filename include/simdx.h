@@ -161,7 +161,7 @@ typedef struct {
                                 Trace records mark plain-store iterations with bit 17 and the
                                 sweeps with bit 18. */
     int32_t sssp_batch_width;  /* simdx_sssp_batch: sources per group of the shared-edge batch,
-                                8, 16, 32 or 64; 0 = 8 [0] (groups run one after another
+                                8, 16, 32 or 64; 0 = 32 [0] (groups run one after another
                                 inside one launch per 64 sources) */
     int32_t reserved[1];
 } simdx_config;
@@ -317,7 +317,7 @@ SIMDX_API int simdx_bfs_batch(simdx_graph *g, const int32_t *srcs, int32_t k, in
 
 /* Batched SSSP (growth direction (a)): k sources, one persistent launch per
  * 64 sources.  Inside a launch the sources run in groups of
- * sssp_batch_width (default 8): a group keeps its distances vertex-major
+ * sssp_batch_width (default 32): a group keeps its distances vertex-major
  * (one row of group-width words per vertex) and one task per vertex for all
  * its sources whose distance there changed, so an edge is read once per
  * iteration for the whole group and the relaxations of one edge touch one

@@ -3,18 +3,21 @@
 // / Sec. 3.3 per source, aggregation combine = min).
 //
 // The sources run in groups of G (8, 16, 32 or 64; the sssp_batch_width
-// knob), one group after another inside the launch.  A group's distances
-// are kept vertex-major, dvm[v * G + i] for its source i, so the
-// relaxations of one edge for all the group's sources touch one contiguous
-// row of G words (G = 8: one 32-byte sector), and the state of a group of
-// 8 at 4 M vertices (128 MB) stays about the size of L2.  A vertex is active
+// knob, 32 by default), one group after another inside the launch.  A
+// group's distances are kept vertex-major, dvm[v * G + i] for its source i,
+// so the relaxations of one edge for all the group's sources touch one
+// contiguous row of G words (G = 8: one 32-byte sector).  Measured at R-MAT
+// scale 22 with 64 sources: G = 8 / 16 / 32 / 64 run 75 / 61 / 55 / 57 ms
+// (narrow groups keep the state in L2 but repeat every iteration's fixed
+// cost once per group; wide rows stream from DRAM).  A vertex is active
 // for the sources in the mask chg[v] (their distance at v changed since v
 // last relaxed them); one task per active vertex, whatever the number of
-// sources.  A task's edges are walked by a warp whose lanes hold (edge,
-// source) pairs: per edge one index and one weight load, one load of the
-// target's row, and an atomicMin for each source that improves (Combine =
-// min).  The improving sources of an edge are gathered by a ballot and
-// added to chg[u] with one atomicOr; the add that makes chg[u] non-zero
+// sources.  Tasks are walked by the degree-class driver of the single query
+// (lanes over edges, 32 small tasks per warp, chunked hubs); a lane reads
+// an edge's index and weight once and relaxes it for every claimed source
+// of its task from 32-byte pieces of the two rows, with an atomicMin for
+// each source that improves (Combine = min).  The improving sources of an
+// edge are added to chg[u] with one atomicOr; the add that makes chg[u] non-zero
 // records u in the next task lists (online filter, degree-class bins;
 // ballot filter over chg != 0 on overflow), so lists hold no duplicates.
 // Each iteration claims the masks of its tasks first (chg -> cm, a phase of
@@ -25,7 +28,7 @@
 namespace simdx {
 
 constexpr int kMsMaxInst = 64;     // sources per launch
-constexpr int kMsDefaultWidth = 8;  // sources per group (row width of the state)
+constexpr int kMsDefaultWidth = 32;  // sources per group (row width of the state)
 
 template <class OffT>
 struct MsspArgs {
@@ -42,20 +45,31 @@ struct MsspArgs {
   Knobs kn;
 };
 
-// Relaxations of a warp: edges [b, e) of task v for the sources in m, in
-// source rows of G words.  G <= 32: lane l takes source l % G of edge l / G,
-// so a step covers 32 / G edges and each edge's sources read one row of G
-// contiguous words.  G = 64: every lane takes sources l and l + 32 of one
-// edge per step.
+// Push functor for the degree-class driver (push_classes): a lane relaxes
+// one edge (v -> u, weight w) for every source in v's claimed mask, eight
+// sources at a time from 32-byte pieces of the two rows (two 16-byte loads
+// each; the pieces of one row share a sector, so the rest hit L1).
 template <class OffT, int G>
-struct MsRelax {
+struct MsPush {
+  struct Src {
+    unsigned long long m;  // sources claimed by the task
+  };
   const MsspArgs<OffT>& a;
   CtaShared& sh;
   unsigned grid;
   unsigned long long nrec = 0, mrec = 0;
 
-  __device__ MsRelax(const MsspArgs<OffT>& aa, CtaShared& s, unsigned g) : a(aa), sh(s), grid(g) {}
-
+  __device__ MsPush(const MsspArgs<OffT>& aa, CtaShared& s, unsigned g) : a(aa), sh(s), grid(g) {}
+  __device__ __forceinline__ bool src(int v, Src& s, int, unsigned) {
+    s.m = a.cm[v];
+    return s.m != 0ull;
+  }
+  __device__ __forceinline__ int rv(int v) const { return v; }
+  static __device__ __forceinline__ Src shfl(const Src& s, int l) {
+    Src r;
+    r.m = __shfl_sync(kFull, s.m, l);
+    return r;
+  }
   // The improved sources `bits` of target u: add them to chg[u]; the add
   // that makes it non-zero records u for the next iteration.
   __device__ __forceinline__ void mark(int u, unsigned long long bits) {
@@ -66,87 +80,34 @@ struct MsRelax {
       online_record(u, degree_class(d, a.kn), sh, a.w, a.kn, grid);
     }
   }
-
-  __device__ __forceinline__ void run(int v, unsigned long long m, long long b, long long e) {
-    if (b >= e || m == 0) return;
-    const int lane = lane_id();
-    constexpr int kU = 4;
-    if constexpr (G <= 32) {
-      constexpr int EPS = 32 / G;
-      const int eo = lane / G, i = lane % G;
-      const bool act = (m >> i) & 1ull;
-      const uint32_t di = act ? a.dvm[(size_t)v * G + i] : 0u;
-      for (long long p0 = b; p0 < e; p0 += EPS * kU) {
-        int u[kU];
-        uint32_t w[kU], c[kU];
+  __device__ __forceinline__ void edges(const Src (&s)[kPushBatch], const int (&v)[kPushBatch],
+                                        const int (&u)[kPushBatch], const long long (&p)[kPushBatch],
+                                        unsigned ok) {
+    uint32_t w[kPushBatch];
 #pragma unroll
-        for (int q = 0; q < kU; ++q) {
-          const long long p = p0 + q * EPS + eo;
-          u[q] = -1;
-          w[q] = 0u;
-          if (p < e) {
-            u[q] = gload(a.idx + p);
-            w[q] = gload(a.wt + p);
-          }
-        }
+    for (int q = 0; q < kPushBatch; ++q) w[q] = ((ok >> q) & 1u) ? gload(a.wt + p[q]) : 0u;
+#pragma unroll 1
+    for (int q = 0; q < kPushBatch; ++q) {
+      if (!((ok >> q) & 1u)) continue;
+      unsigned long long imp = 0;
+#pragma unroll 1
+      for (int c = 0; c < G / 8; ++c) {
+        const unsigned m8 = (unsigned)(s[q].m >> (8 * c)) & 0xffu;
+        if (!m8) continue;
+        const uint4* dv = reinterpret_cast<const uint4*>(a.dvm + (size_t)v[q] * G + 8 * c);
+        uint4* duv = reinterpret_cast<uint4*>(a.dvm + (size_t)u[q] * G + 8 * c);
+        const uint4 s0 = dv[0], s1 = dv[1], t0 = duv[0], t1 = duv[1];
+        const uint32_t dsv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        const uint32_t dtv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+        uint32_t* du = a.dvm + (size_t)u[q] * G + 8 * c;
 #pragma unroll
-        for (int q = 0; q < kU; ++q) c[q] = (u[q] >= 0 && act) ? a.dvm[(size_t)u[q] * G + i] : 0u;
-#pragma unroll
-        for (int q = 0; q < kU; ++q) {
-          const unsigned long long nd = (unsigned long long)di + w[q];
-          bool got = false;
-          if (u[q] >= 0 && act && nd < c[q]) got = nd < atomicMin(a.dvm + (size_t)u[q] * G + i, (uint32_t)nd);
-          const unsigned bal = __ballot_sync(kFull, got);
-          if (i == 0 && u[q] >= 0) {
-            const unsigned long long bits =
-                G == 32 ? (unsigned long long)bal : (unsigned long long)((bal >> (eo * G)) & ((1u << G) - 1u));
-            if (bits) mark(u[q], bits);
-          }
+        for (int i = 0; i < 8; ++i) {
+          if (!((m8 >> i) & 1u)) continue;
+          const unsigned long long nd = (unsigned long long)dsv[i] + w[q];
+          if (nd < dtv[i] && nd < atomicMin(du + i, (uint32_t)nd)) imp |= 1ull << (8 * c + i);
         }
       }
-    } else {
-      const bool hi = (m >> 32) != 0;  // same in every lane
-      const bool a0 = (m >> lane) & 1ull;
-      const bool a1 = hi && ((m >> (lane + 32)) & 1ull);
-      const uint32_t* dv = a.dvm + (size_t)v * G;
-      const uint32_t d0 = a0 ? dv[lane] : 0u;
-      const uint32_t d1 = a1 ? dv[lane + 32] : 0u;
-      for (long long p = b; p < e; p += kU) {
-        int u[kU];
-        uint32_t w[kU], c0[kU], c1[kU];
-#pragma unroll
-        for (int q = 0; q < kU; ++q) {
-          u[q] = -1;
-          w[q] = 0u;
-          if (p + q < e) {
-            u[q] = gload(a.idx + p + q);
-            w[q] = gload(a.wt + p + q);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kU; ++q) {
-          c0[q] = 0u;
-          c1[q] = 0u;
-          if (u[q] >= 0) {
-            const uint32_t* du = a.dvm + (size_t)u[q] * G;
-            if (a0) c0[q] = du[lane];
-            if (a1) c1[q] = du[lane + 32];
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kU; ++q) {
-          if (u[q] < 0) continue;  // the same in every lane
-          uint32_t* du = a.dvm + (size_t)u[q] * G;
-          const unsigned long long n0 = (unsigned long long)d0 + w[q];
-          const unsigned long long n1 = (unsigned long long)d1 + w[q];
-          bool g0 = false, g1 = false;
-          if (a0 && n0 < c0[q]) g0 = n0 < atomicMin(du + lane, (uint32_t)n0);
-          if (a1 && n1 < c1[q]) g1 = n1 < atomicMin(du + lane + 32, (uint32_t)n1);
-          const unsigned b0 = __ballot_sync(kFull, g0);
-          const unsigned b1 = hi ? __ballot_sync(kFull, g1) : 0u;
-          if ((b0 | b1) && lane == 0) mark(u[q], (unsigned long long)b0 | ((unsigned long long)b1 << 32));
-        }
-      }
+      if (imp) mark(u[q], imp);
     }
   }
 };
@@ -164,8 +125,6 @@ __global__ void __launch_bounds__(kThreads, 4) msssp_kernel(const __grid_constan
   const int n = a.n;
   const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
   const long long gthreads = (long long)grid * kThreads;
-  const int lane = lane_id(), warp = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * kWarps + warp, nw = (long long)grid * kWarps;
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
   int it = 0, ballot_it = 0;
@@ -235,42 +194,11 @@ __global__ void __launch_bounds__(kThreads, 4) msssp_kernel(const __grid_constan
       online_reset(sh);
       __syncthreads();
       PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-      MsRelax<OffT, G> f(a, sh, grid);
+      MsPush<OffT, G> f(a, sh, grid);
       {
-        ClassTimer tm(&slot);
-        // class 3: each task's edges split over every warp of the grid
-        for (unsigned i = 0; i < cnt[3]; ++i) {
-          const int v = a.w.list[lbuf][3][i];
-          const long long vb = gload(a.off + v), ve = gload(a.off + v + 1);
-          const long long ch = ((ve - vb + nw - 1) / nw + 31) & ~31ll;
-          const long long b = vb + gw * ch;
-          const long long e = b + ch < ve ? b + ch : ve;
-          f.run(v, a.cm[v], b, e);
-          if (lane == 0 && b < ve) evisit += e - b;
-        }
-        tm.lap(3);
-        // class 2: one CTA per task, its warps splitting the edges
-        for (unsigned i = blockIdx.x; i < cnt[2]; i += grid) {
-          const int v = a.w.list[lbuf][2][i];
-          const long long vb = gload(a.off + v), ve = gload(a.off + v + 1);
-          const long long ch = ((ve - vb + kWarps - 1) / kWarps + 31) & ~31ll;
-          const long long b = vb + (long long)warp * ch;
-          const long long e = b + ch < ve ? b + ch : ve;
-          f.run(v, a.cm[v], b, e);
-          if (lane == 0 && b < ve) evisit += e - b;
-        }
-        tm.lap(2);
-        // classes 1 and 0: one warp per task
-        for (int c = 1; c >= 0; --c) {
-          const int32_t* list = a.w.list[lbuf][c];
-          for (long long i = gw; i < cnt[c]; i += nw) {
-            const int v = list[i];
-            const long long vb = gload(a.off + v), ve = gload(a.off + v + 1);
-            f.run(v, a.cm[v], vb, ve);
-            if (lane == 0) evisit += ve - vb;
-          }
-          tm.lap(c);
-        }
+        const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
+                                          a.w.list[lbuf][3]};
+        push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
       }
       online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
       const unsigned long long tn = cta_sum_u64(f.nrec, sh);

@@ -197,7 +197,7 @@ size_t slot_bytes(const simdx_graph* g, int max_sssp) {
   const size_t state = 20 * n + 16 * n + 8 * ((size_t)g->e / std::max(1, g->cfg.huge_min) + n);
   const size_t ms = 24 * n;
   // batched SSSP: vertex-major distances (32 or 64 words per vertex) and two masks
-  const size_t sb = g->w ? (4 * (size_t)std::max(8, g->cfg.sssp_batch_width) + 16) * n : 0;
+  const size_t sb = g->w ? (4 * (size_t)(g->cfg.sssp_batch_width ? g->cfg.sssp_batch_width : 32) + 16) * n : 0;
   return lists + bins + state + ms + sb;
 }
 
