@@ -161,8 +161,9 @@ typedef struct {
                                 Trace records mark plain-store iterations with bit 17 and the
                                 sweeps with bit 18. */
     int32_t sssp_batch_width;  /* simdx_sssp_batch: sources per group of the shared-edge batch,
-                                8, 16, 32 or 64; 0 = 32 [0] (groups run one after another
-                                inside one launch per 64 sources) */
+                                8, 16, 32 or 64; 0 = 32 [0]; a smaller batch uses the
+                                narrowest of these that holds it (groups run one after
+                                another inside one launch per 64 sources) */
     int32_t reserved[1];
 } simdx_config;
 

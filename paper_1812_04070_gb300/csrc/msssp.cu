@@ -309,6 +309,8 @@ static int run_msssp_width(simdx_graph* g, const int32_t* srcs, int k, uint32_t*
                            cudaStream_t st) {
   int G = g->cfg.sssp_batch_width;
   if (G == 0) G = kMsDefaultWidth;
+  // no wider rows than the batch needs
+  while (G > 8 && G / 2 >= k) G /= 2;
   switch (G) {
     case 8: return run_msssp<OffT, 8>(g, srcs, k, dist, stats, st);
     case 16: return run_msssp<OffT, 16>(g, srcs, k, dist, stats, st);
