@@ -109,8 +109,10 @@ typedef struct {
     int64_t reserved[3];
 } simdx_stats;
 
-/* Tuning knobs (defaults in brackets).  Every knob changes speed only, never
- * results. */
+/* Tuning knobs (defaults in brackets).  BFS, SSSP, k-core, coreness and
+ * component results are the same under every setting; the PageRank knobs
+ * (pr_*, and the CTAs per SM, which set the summation order) change its
+ * result only within the stated tolerance. */
 typedef struct {
     int32_t small_max;       /* degree < small_max -> thread list [32]   (Sec. 4 "Classification") */
     int32_t med_max;         /* degree < med_max   -> warp list   [512]  (Sec. 4 finds this
@@ -164,7 +166,10 @@ typedef struct {
                                 8, 16, 32 or 64; 0 = 32 [0]; a smaller batch uses the
                                 narrowest of these that holds it (groups run one after
                                 another inside one launch per 64 sources) */
-    int32_t reserved[1];
+    int32_t pr_row_cost;     /* simdx_pagerank: cost of finishing a row, in in-edges, in the
+                                model that cuts the in-edges into equal-cost warp ranges;
+                                0 = 4 [0] (changes the summation order's split, so results
+                                may differ in the last bits; a given setting is deterministic) */
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;

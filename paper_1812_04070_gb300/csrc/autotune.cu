@@ -31,7 +31,10 @@ struct Knob {
 std::vector<Knob> knobs_for(int algo) {
   std::vector<Knob> k;
   k.push_back({"ctas_per_sm", {0, 3, 2}, SIMDX_KNOB_I(ctas_per_sm)});
-  if (algo == SIMDX_ALGO_PAGERANK) return k;  // all vertices active; no task classes
+  if (algo == SIMDX_ALGO_PAGERANK) {  // all vertices active; no task classes
+    k.push_back({"pr_row_cost", {0, 2, 8, 16, 32}, SIMDX_KNOB_I(pr_row_cost)});
+    return k;
+  }
   k.push_back({"small_max", {8, 16, 32, 64}, SIMDX_KNOB_I(small_max)});
   k.push_back({"med_max", {128, 256, 512, 1024, 2048}, SIMDX_KNOB_I(med_max)});
   k.push_back({"huge_min", {1024, 2048, 4096, 8192, 16384}, SIMDX_KNOB_I(huge_min)});

@@ -592,7 +592,8 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
       cfg->fusion < 0 || cfg->fusion > 2 || !(cfg->pr_alpha >= 0.f) || !(cfg->pr_theta >= 0.f) ||
       !(cfg->pr_rho >= 0.f) || cfg->sssp_combine < 0 || cfg->sssp_combine > 1 ||
       (cfg->sssp_batch_width != 0 && cfg->sssp_batch_width != 8 && cfg->sssp_batch_width != 16 &&
-       cfg->sssp_batch_width != 32 && cfg->sssp_batch_width != 64))
+       cfg->sssp_batch_width != 32 && cfg->sssp_batch_width != 64) || cfg->pr_row_cost < 0 ||
+      cfg->pr_row_cost > 4096)
     return SIMDX_EINVAL;
   bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
                     cfg->huge_min != g->cfg.huge_min;

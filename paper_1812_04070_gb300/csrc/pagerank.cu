@@ -864,7 +864,7 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   a.wk.headp = reinterpret_cast<double*>(base + head_b + pre_b + csum_b + ts_b + part_b);
   a.wk.done = reinterpret_cast<int*>(base + head_b + pre_b + csum_b + ts_b + 2 * part_b);
   a.wk.ntiles = ntiles;
-  a.wk.row_cost = kPrRowCost;
+  a.wk.row_cost = g->cfg.pr_row_cost > 0 ? g->cfg.pr_row_cost : kPrRowCost;
   a.wk.vec4 = (reinterpret_cast<uintptr_t>(g->in_idx) & 15) == 0;
   int rc = prepare_launch(g, st);
   if (rc) return rc;
