@@ -836,10 +836,12 @@ def run_ablation(args, rank, world, local):
     default_delta = G.config.delta
     fl = lambda f, x: (f"fusion={['all', 'selective', 'none'][f]} filter={'JIT' if x == 0 else 'ballot'}",
                        dict(fusion=f, filter=x))
-    modes = {"bfs": [fl(0, 0), fl(1, 0), fl(2, 0), fl(0, 2), fl(2, 2)],
+    modes = {"bfs": [fl(0, 0), fl(1, 0), fl(2, 0), fl(0, 2), fl(2, 2),
+                     ("edges staged by bulk copy", dict(fusion=0, filter=0, stage_edges=1))],
              "sssp": [fl(0, 0), fl(2, 0), fl(0, 2), fl(2, 2),
                       ("combine=plain stores + pull sweeps (no atomics)", dict(fusion=0, filter=0, sssp_combine=1)),
-                      ("delta=64", dict(sssp_combine=0, delta=64)), ("delta=256", dict(delta=256)),
+                      ("edges staged by bulk copy", dict(sssp_combine=0, stage_edges=1)),
+                      ("delta=64", dict(stage_edges=0, delta=64)), ("delta=256", dict(delta=256)),
                       ("delta=unbounded", dict(delta=0)), ("pull every iteration", dict(delta=default_delta,
                                                                                          direction=2))],
              "kcore": [fl(0, 0), fl(0, 2)],
@@ -863,7 +865,7 @@ def run_ablation(args, rank, world, local):
     for a in wl["algs"]:
         ref = None
         rows = []
-        G.set_config(delta=default_delta, direction=0)
+        G.set_config(delta=default_delta, direction=0, stage_edges=0)
         for label, knobs in modes[a]:
             G.set_config(**knobs)
             st = simdx_stats()
@@ -895,7 +897,7 @@ def run_ablation(args, rank, world, local):
             rows.append(row)
         res[a] = rows
         G.set_config(fusion=0, filter=0, pr_alpha=8.0, sssp_combine=0, delta=default_delta, direction=0,
-                     pr_row_cost=0)
+                     pr_row_cost=0, stage_edges=0)
     G.close()
     base = res[wl["algs"][0]][0]
     return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],

@@ -170,6 +170,12 @@ typedef struct {
                                 model that cuts the in-edges into equal-cost warp ranges;
                                 0 = 4 [0] (changes the summation order's split, so results
                                 may differ in the last bits; a given setting is deterministic) */
+    int32_t stage_edges;     /* simdx_bfs / simdx_sssp (all fusion, push): 1 = the edge ranges
+                                of CTA-class tasks and grid chunks are staged in shared memory
+                                by the bulk copy engine (cp.async.bulk into two 8 KB buffers,
+                                completion on an mbarrier), the next buffer's copy in flight
+                                while the CTA relaxes the current one; 0 = plain loads [0] */
+    int32_t reserved[7];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;

@@ -92,6 +92,7 @@ struct Knobs {
   int skip_cta, skip_phase;
   int fusion;           // 0 all iterations in one launch, 1 one launch per run of one
                         // direction, 2 one launch per iteration (Sec. 5, Table 2)
+  int stage;            // stage CTA-class edge ranges in shared memory by bulk copy
 };
 
 // Workspace shared by all algorithms of one graph.
@@ -612,10 +613,135 @@ __device__ __forceinline__ void push_strided(F& f, const typename F::Src& s, int
   }
 }
 
+// ------------------------------------------- bulk-copy staging of edges
+// A CTA that walks one contiguous edge range (CTA-class tasks and grid
+// chunks) can stage the neighbour indices in shared memory with the bulk
+// copy engine (cp.async.bulk, completion counted on an mbarrier), two
+// buffers deep: while the CTA relaxes one buffer's edges the next buffer's
+// copy is in flight.  Copies are 16-byte aligned and stay inside the index
+// array; the unaligned head and the tail past the last whole 16 bytes are
+// read from global memory directly.  Every wait is bounded: a copy that
+// never completes aborts the run (the barrier then reports it) instead of
+// hanging.
+constexpr int kStageEdges = 2048;  // indices per buffer (8 KB)
+
+struct __align__(128) StageShared {
+  int32_t buf[2][kStageEdges];
+  unsigned long long bar[2];  // mbarriers, one per buffer
+  unsigned par[2];            // phase parity each buffer's next wait expects
+};
+
+struct Stager {
+  StageShared* sm;      // nullptr: no staging
+  Sync* sync;
+  long long e_total;    // entries of the index array
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Thread 0 of the CTA, once per kernel.
+__device__ __forceinline__ void stage_init(StageShared& sm) {
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar[b])) : "memory");
+      sm.par[b] = 0u;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// Thread 0: copy indices [cs, ce) (cs, ce multiples of 4) into buffer b.
+__device__ __forceinline__ void stage_issue(StageShared& sm, int b, const int32_t* idx, long long cs, long long ce) {
+  const unsigned bar = smem_addr(&sm.bar[b]);
+  const unsigned bytes = (unsigned)((ce - cs) * 4);
+  if (bytes == 0) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    return;
+  }
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(sm.buf[b])), "l"(idx + cs), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Every thread: wait for buffer b's copy (bounded), then flip its parity.
+__device__ __forceinline__ void stage_wait(StageShared& sm, int b, Sync* sync) {
+  const unsigned bar = smem_addr(&sm.bar[b]);
+  const unsigned par = sm.par[b];
+  for (int round = 0; round < 2; ++round) {
+    unsigned done = 0, spins = 0;
+    while (!done) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(bar), "r"(par)
+          : "memory");
+      if (!done && ++spins > (1u << 20)) break;
+    }
+    if (done) break;
+    // the copy did not complete: abort the run, then wait once more (bounded)
+    // for the copy in flight before the buffer is touched again
+    if (threadIdx.x == 0 && round == 0) {
+      atomicExch(&sync->abort, 1);
+      atomicCAS(&sync->err, 0, 4 /* SIMDX_EBARRIER_TIMEOUT */);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sm.par[b] = par ^ 1u;
+}
+
+// Every thread of the CTA: the edges [beg, end) of task v (row rv), their
+// indices staged through shared memory, kPushBatch per thread at a time.
+template <class F>
+__device__ void push_staged(F& f, const typename F::Src& s, int v, const int32_t* idx, long long beg, long long end,
+                            const Stager& st) {
+  StageShared& sm = *st.sm;
+  const long long lim = st.e_total & ~3ll;  // copies stay inside the array
+  const long long a0 = beg & ~3ll;
+  const int tid = threadIdx.x;
+  typename F::Src ss[kPushBatch];
+  int vv[kPushBatch];
+#pragma unroll
+  for (int q = 0; q < kPushBatch; ++q) {
+    ss[q] = s;
+    vv[q] = v;
+  }
+  int b = 0;
+  if (tid == 0) stage_issue(sm, 0, idx, a0 < lim ? a0 : lim, a0 + kStageEdges < lim ? a0 + kStageEdges : lim);
+  for (long long cs = a0; cs < end; cs += kStageEdges, b ^= 1) {
+    const long long nx = cs + kStageEdges;
+    if (tid == 0 && nx < end)
+      stage_issue(sm, b ^ 1, idx, nx < lim ? nx : lim, nx + kStageEdges < lim ? nx + kStageEdges : lim);
+    stage_wait(sm, b, st.sync);
+    const long long ce = cs + kStageEdges < lim ? cs + kStageEdges : (cs < lim ? lim : cs);  // staged: [cs, ce)
+    const long long lo = cs < beg ? beg : cs, hi = nx < end ? nx : end;
+    for (long long p0 = lo; p0 < hi; p0 += (long long)kThreads * kPushBatch) {
+      int u[kPushBatch];
+      long long pp[kPushBatch];
+      unsigned ok = 0;
+#pragma unroll
+      for (int q = 0; q < kPushBatch; ++q) {
+        pp[q] = p0 + tid + (long long)q * kThreads;
+        u[q] = 0;
+        if (pp[q] < hi) {
+          u[q] = pp[q] < ce ? sm.buf[b][pp[q] - cs] : gload(idx + pp[q]);
+          ok |= 1u << q;
+        }
+      }
+      f.edges(ss, vv, u, pp, ok);
+    }
+    __syncthreads();  // buffer b is free for the copy issued next round
+  }
+}
+
 template <class OffT, class F>
 __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
                              const int32_t* const* lists, const unsigned* cnt, unsigned grid,
-                             long long ch, CtaShared& sh, long long& evisit, PhaseSlot* slot = nullptr) {
+                             long long ch, CtaShared& sh, long long& evisit, PhaseSlot* slot = nullptr,
+                             const Stager* stg = nullptr) {
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   ClassTimer tm(slot);
   // class 3: every task is cut into chunks of `ch` edges (fewer when the batch
@@ -636,7 +762,8 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
       const long long end = beg + cb < ve ? beg + cb : ve;
       typename F::Src s;
       if (!f.src(v, s, 3, b0 + item)) continue;
-      push_strided(f, s, v, idx, beg, end, tid, kThreads);
+      if (stg && stg->sm) push_staged(f, s, v, idx, beg, end, *stg);
+      else push_strided(f, s, v, idx, beg, end, tid, kThreads);
       if (tid == 0) evisit += end - beg;
     }
   }
@@ -648,7 +775,8 @@ __device__ void push_classes(F& f, const OffT* off, const int32_t* idx,
     if (!f.src(v, s, 2, i)) continue;
     const int rv = f.rv(v);
     long long beg = gload(off + rv), end = gload(off + rv + 1);
-    push_strided(f, s, v, idx, beg, end, tid, kThreads);
+    if (stg && stg->sm) push_staged(f, s, v, idx, beg, end, *stg);
+    else push_strided(f, s, v, idx, beg, end, tid, kThreads);
     if (tid == 0) evisit += end - beg;
   }
   tm.lap(2);

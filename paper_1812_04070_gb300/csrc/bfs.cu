@@ -333,7 +333,10 @@ static_assert(kRsPhases < kResumeWords, "resume record too small");
 // DIRS: the directions this instantiation computes (kPush | kPull for the
 // all-fusion kernel; kPush or kPull alone for the kernels of selective and
 // no fusion, which stop when the next iteration needs the other direction).
-template <class OffT, int DIRS = kPush | kPull>
+// STAGE: CTA-class push ranges staged in shared memory by bulk copy (the
+// `stage` knob; a separate instantiation, so the default kernel keeps its
+// shared-memory footprint and L1 share).
+template <class OffT, int DIRS = kPush | kPull, bool STAGE = false>
 __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   constexpr bool kHasPush = (DIRS & kPush) != 0;
   constexpr bool kHasPull = (DIRS & kPull) != 0;
@@ -349,6 +352,12 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   const long long gthreads = (long long)grid * kThreads;
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
+  Stager stg{nullptr, s, a.m_total};
+  if constexpr (STAGE) {
+    __shared__ StageShared stage_sm;
+    stage_init(stage_sm);
+    if ((reinterpret_cast<uintptr_t>(a.idx) & 15) == 0) stg.sm = &stage_sm;
+  }
   // a launch that continues a run split over several launches skips the set-up
   const bool resumed = kSplit && ld_volatile_i32(&s->rs.active) != 0;
 
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       BfsPush<OffT> f(a.level, a.off, L + 1, sh, a.w, k, grid);
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, nullptr);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, nullptr, &stg);
       nrec = f.nrec;
       mrec = f.mrec;
       ++push_it;
@@ -613,7 +622,7 @@ static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* st
   if (rc) return rc;
   void* args[] = {&a};
   if (a.k.fusion == 0) {
-    const void* kern = (const void*)bfs_kernel<OffT>;
+    const void* kern = a.k.stage ? (const void*)bfs_kernel<OffT, kPush | kPull, true> : (const void*)bfs_kernel<OffT>;
     if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
     return finish_launch(g, stats, st);
   }

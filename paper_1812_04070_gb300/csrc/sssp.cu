@@ -281,7 +281,8 @@ static_assert(kRsPhases < kResumeWords, "resume record too small");
 // leaves its loop state in the resume record for the next launch.
 // VERIFY: the atomic-free combine (plain-store min in push, then pull
 // sweeps until no distance drops).
-template <class OffT, bool V, bool PULL, bool W = false, bool SPLIT = false, bool VERIFY = false>
+// STAGE: CTA-class push ranges staged in shared memory by bulk copy.
+template <class OffT, bool V, bool PULL, bool W = false, bool SPLIT = false, bool VERIFY = false, bool STAGE = false>
 __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant__ SsspArgs<OffT> a) {
   __shared__ CtaShared sh;
   __shared__ unsigned red_u[kWarps];
@@ -298,6 +299,12 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
   const bool resumed = SPLIT && ld_volatile_i32(&s->rs.active) != 0;
+  Stager stg{nullptr, s, (long long)(gload(a.off + a.nreal) - gload(a.off))};
+  if constexpr (STAGE) {
+    __shared__ StageShared stage_sm;
+    stage_init(stage_sm);
+    if ((reinterpret_cast<uintptr_t>(a.idx) & 15) == 0) stg.sm = &stage_sm;
+  }
 
   const unsigned nreal = (unsigned)a.nreal;
   // state id -> vertex of the one CSR
@@ -629,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       scan_all = f.dense;
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot, &stg);
       online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
       tn = cta_sum_u64(f.nrec, sh);
       tm = cta_sum_u64(f.mrec, sh);
@@ -716,7 +723,9 @@ static int run_sssp(simdx_graph* g, int32_t src, uint32_t* dist, simdx_stats* st
     return finish_launch(g, stats, st);
   }
   if (a.k.fusion != 2) {
-    const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true> : (const void*)sssp_kernel<OffT, false, false>;
+    const void* kern = pull ? (const void*)sssp_kernel<OffT, false, true>
+                       : a.k.stage ? (const void*)sssp_kernel<OffT, false, false, false, false, false, true>
+                                   : (const void*)sssp_kernel<OffT, false, false>;
     if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
     return finish_launch(g, stats, st);
   }

@@ -372,3 +372,44 @@ def test_sssp_atomic_free_combine_rejects_directed():
         G.sssp(0)
     assert e.value.status == simdx.EUNSUPPORTED
     G.close()
+
+
+# Bulk-copy staging of CTA-class edge ranges in shared memory (stage_edges):
+# the same levels and distances as plain loads, also with tiny class
+# thresholds (every task of degree >= 8 walks staged chunks).
+STAGED = {"staged": dict(stage_edges=1), "staged_all_classes": dict(stage_edges=1, small_max=2, med_max=4, huge_min=8),
+          "staged_one_cta_per_sm": dict(stage_edges=1, ctas_per_sm=1)}
+
+
+@pytest.mark.parametrize("mode", list(STAGED))
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_bfs_sssp_staged_edges(gi, mode):
+    g = GRAPHS[gi]
+    w = gg.weights(g, 77 + gi, 1, 64)
+    G = make(g, w, bits=32 if gi % 2 else 64, **STAGED[mode])
+    for s in sources(g):
+        assert np.array_equal(G.bfs(s).cpu().numpy(), oracle.bfs(g.offsets, g.indices, s)), (g.name, mode, s)
+        d = G.sssp(s).cpu().numpy().view(np.uint32)
+        assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, s)), (g.name, mode, s)
+    assert G.last_status() == 0
+    G.close()
+
+
+def test_staged_edges_unaligned_index_array():
+    """A borrowed index array that is not 16-byte aligned takes the plain
+    loads (bulk copies need 16-byte aligned addresses)."""
+    import torch
+    from paper_1812_04070_gb300 import Graph
+    g = gg.rmat(12)
+    w = gg.weights(g, 5, 1, 64)
+    off = torch.from_numpy(g.offsets).cuda()
+    buf = torch.zeros(g.e + 4, dtype=torch.int32, device="cuda")
+    buf[1:g.e + 1] = torch.from_numpy(g.indices).cuda()
+    idx = buf[1:g.e + 1]
+    assert idx.data_ptr() % 16 != 0
+    wt = torch.from_numpy(w.view(np.int32)).cuda()
+    G = Graph(off, idx, weights=wt, borrow=True)
+    G.set_config(stage_edges=1, huge_min=64)
+    assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
+    assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
+    G.close()
