@@ -79,6 +79,7 @@ def test_sssp_dense_iterations(delta):
     assert any((int(r[0]) >> 16) & 1 for r in tr), "no dense iteration"
     assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, 0))
     srcs = [0, 1, 2, 3]
+    G.set_config(batch_group=4)  # the virtual-copy batch shares the dense iterations
     db = G.sssp_batch(srcs).cpu().numpy().view(np.uint32)
     assert any((int(r[0]) >> 16) & 1 for r in G.trace()), "no dense iteration in the batch"
     for i, s in enumerate(srcs):
