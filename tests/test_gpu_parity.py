@@ -410,7 +410,7 @@ def test_staged_edges_unaligned_index_array():
     assert idx.data_ptr() % 16 != 0
     wt = torch.from_numpy(w.view(np.int32)).cuda()
     G = Graph(off, idx, weights=wt, borrow=True)
-    G.set_config(stage_edges=1, huge_min=64)
+    G.set_config(stage_edges=1, small_max=2, med_max=4, huge_min=64)
     assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
     assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
     G.close()
