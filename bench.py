@@ -16,8 +16,8 @@ BFS / SSSP count the edges of the component reached from the source, k-core
 counts every edge once, PageRank counts every edge once per iteration).
 
 Timing: W untimed warm-up steps, then K timed steps.  A step is a batch of
-R queries of the workload (R chosen so that a step holds about 0.1 s of
-kernel time, or --queries); before every query the L2 is flushed (a 512 MB
+R queries of the workload (R chosen so that a step holds about 0.125 s of
+GPU time, or --queries); before every query the L2 is flushed (a 512 MB
 write) outside the timed brackets, and every kernel launch is bracketed by
 CUDA events on the launching stream.  `value` = edges of all timed queries
 over the sum of their kernel times.  The roofline object reports the
@@ -124,7 +124,7 @@ def parse():
     p.add_argument("--impl", default="simdx", choices=["simdx", "reference"])
     p.add_argument("--workload", default="rmat24-bfs", choices=list(WORKLOADS))
     p.add_argument("--queries", type=int, default=0,
-                   help="queries per step (0: as many as make about 0.1 s of kernel time)")
+                   help="queries per step (0: as many as make about 0.125 s of GPU time)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--autotune", action="store_true",
@@ -417,8 +417,8 @@ def run_simdx(args, rank, world, local):
     for _ in range(max(args.warmup, 3)):
         query(False)
     torch.cuda.synchronize()
-    # queries per step: about 0.1 s of kernel time, so that K steps span
-    # seconds of clock samples
+    # queries per step: about 0.125 s of GPU time, so that K steps span
+    # seconds of clock samples (20 steps: about 2.5 s)
     if args.queries > 0:
         R = args.queries
     else:
@@ -428,7 +428,7 @@ def run_simdx(args, rank, world, local):
             query(False)
         q1.record(stream)
         torch.cuda.synchronize()
-        R = int(min(4096, max(1, round(0.1 / (q0.elapsed_time(q1) / 3 / 1e3)))))
+        R = int(min(4096, max(1, round(0.125 / (q0.elapsed_time(q1) / 3 / 1e3)))))
     for _ in range(args.warmup):
         for _ in range(R):
             query(False)
