@@ -847,7 +847,11 @@ def run_ablation(args, rank, world, local):
              "kcore": [fl(0, 0), fl(0, 2)],
              "pagerank": [("pull, then push (default switch rule)", dict(pr_alpha=8.0)),
                           ("pull only", dict(pr_alpha=0.0))] +
-                         [(f"pull only, row cost {rc}", dict(pr_alpha=0.0, pr_row_cost=rc)) for rc in (1, 2, 8, 16, 32)]}
+                         [(f"pull only, row cost {rc}", dict(pr_alpha=0.0, pr_row_cost=rc)) for rc in (1, 2, 8, 16, 32)] +
+                         [(f"pull only, ranges re-cut by measured time after {r}", dict(pr_alpha=0.0, pr_row_cost=0,
+                                                                                          pr_recut=r))
+                          for r in (1, 2)] +
+                         [("pull then push, re-cut after 2", dict(pr_alpha=8.0, pr_recut=2))]}
 
     outf = torch.empty(g.n, dtype=torch.float32, device=dev)
 
@@ -897,7 +901,7 @@ def run_ablation(args, rank, world, local):
             rows.append(row)
         res[a] = rows
         G.set_config(fusion=0, filter=0, pr_alpha=8.0, sssp_combine=0, delta=default_delta, direction=0,
-                     pr_row_cost=0, stage_edges=0)
+                     pr_row_cost=0, stage_edges=0, pr_recut=0)
     G.close()
     base = res[wl["algs"][0]][0]
     return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],

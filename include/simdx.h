@@ -175,7 +175,13 @@ typedef struct {
                                 by the bulk copy engine (cp.async.bulk into two 8 KB buffers,
                                 completion on an mbarrier), the next buffer's copy in flight
                                 while the CTA relaxes the current one; 0 = plain loads [0] */
-    int32_t reserved[7];
+    int32_t pr_recut;        /* simdx_pagerank: after this many iterations, re-cut the warp
+                                ranges of the in-edge walk so that every warp's share of the
+                                walk time measured in the last iteration is equal; 0 = keep the
+                                cost-model cut [0].  The summation order then follows a
+                                measured cut: results stay within tolerance but may differ in
+                                the last bits from run to run. */
+    int32_t reserved[6];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;

@@ -594,7 +594,7 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
       !(cfg->pr_rho >= 0.f) || cfg->sssp_combine < 0 || cfg->sssp_combine > 1 ||
       (cfg->sssp_batch_width != 0 && cfg->sssp_batch_width != 8 && cfg->sssp_batch_width != 16 &&
        cfg->sssp_batch_width != 32 && cfg->sssp_batch_width != 64) || cfg->pr_row_cost < 0 ||
-      cfg->pr_row_cost > 4096 || cfg->stage_edges < 0 || cfg->stage_edges > 1)
+      cfg->pr_row_cost > 4096 || cfg->stage_edges < 0 || cfg->stage_edges > 1 || cfg->pr_recut < 0)
     return SIMDX_EINVAL;
   bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
                     cfg->huge_min != g->cfg.huge_min;

@@ -71,6 +71,9 @@ struct PrWalk {
   double* tailp;             // [warps] partial of the row left open at the end of a warp's range
   double* headp;             // [warps] partial of the row that continues into a warp's range
   int* done;                 // [warps] arrivals for the cross-warp row ending in that warp
+  unsigned long long* wtime; // [warps] SM cycles each warp's walk took (re-cut iteration)
+  unsigned long long* wpre;  // [warps + 1] exclusive prefix of wtime
+  int* tstart2;              // [warps + 1] the ranges cut by measured time
   long long ntiles;          // ceil(E / kTile)
   int row_cost;              // cost of finishing a row, in in-edges
   int vec4;                  // in-edge array is 16-byte aligned
@@ -90,6 +93,7 @@ struct PrArgs {
   float* inv;        // [n] 1 / outdeg (0 for outdeg 0), set once per run
   // switch from pull to push (the push-tail instantiation only)
   float alpha, theta, rho;
+  int recut;                // re-cut the warp ranges by measured time after this iteration (0: never)
   unsigned long long* res;  // [n] pending rank change, signed 2^-60 fixed point
   long long* push_c;        // [n] what a selected vertex sends along each out-edge (2^-60)
   PrWalk wk;
@@ -561,9 +565,117 @@ __device__ __noinline__ int pr_unstable_test(const PrArgs<OffT>& a, const float*
   return (double)s->slot[slot_of(sh.phase - 1)].aux2 * (double)a.alpha < (double)a.e ? 1 : 0;
 }
 
+// The walk state of warp gw under the warp ranges ts (first tile of each
+// warp, nwarps + 1 entries): its tile range, the rank among the rows of the
+// first row starting in it, and the rows it shares with other warps.  An
+// empty range writes a zero head partial (it adds nothing to a row crossing
+// it).
+template <class OffT>
+__device__ void pr_warp_setup(const PrArgs<OffT>& a, const int* ts, long long nwarps, long long gw,
+                              const int32_t* l0, int c0n, int& t_beg, int& t_end, int& rank0, PrCross& cx) {
+  const PrWalk& wk = a.wk;
+  const OffT* ioff = a.ioff;
+  t_beg = ts[gw];
+  t_end = ts[gw + 1];
+  rank0 = 0;
+  cx = PrCross{};
+  if (t_beg >= t_end) {
+    if (lane_id() == 0) wk.headp[gw] = 0.0;
+    return;
+  }
+  auto warp_of = [ts, nwarps](long long tile) {
+    return (int)warp_partition_point(nwarps, [ts, tile](long long w) { return ts[w] <= tile; }) - 1;
+  };
+  auto nonempty = [ts](int w0, int w1) {  // warps in [w0, w1] with a nonempty range
+    int c = 0;
+    for (int w = w0 + lane_id(); w <= w1; w += 32) c += ts[w] < ts[w + 1];
+    return (int)warp_sum_u64((unsigned long long)c);
+  };
+  auto rows_before = [ioff, l0, c0n](long long x) {
+    return (int)warp_partition_point(c0n, [ioff, l0, x](long long q) { return (long long)gload(ioff + l0[q]) < x; });
+  };
+  const long long x = (long long)t_beg * kTile;
+  rank0 = rows_before(x);
+  if (!((wk.head[x >> 5] >> (x & 31)) & 1u)) {
+    cx.head_rank = rank0 - 1;
+    const int u = l0[cx.head_rank];
+    cx.hw0 = warp_of((long long)gload(ioff + u) / kTile);
+    cx.hw1 = warp_of(((long long)gload(ioff + u + 1) - 1) / kTile);
+    cx.hn = nonempty(cx.hw0, cx.hw1);
+  }
+  const long long xe = (long long)t_end * kTile;
+  if (xe < a.e && !((wk.head[xe >> 5] >> (xe & 31)) & 1u)) {
+    const int u = l0[rows_before(xe) - 1];
+    cx.tail_w1 = warp_of(((long long)gload(ioff + u + 1) - 1) / kTile);
+    cx.tn = nonempty((int)gw, cx.tail_w1);
+  }
+}
+
+// Re-cut the warp ranges so that each warp's share of the measured walk
+// time is equal: warp w's old range [ts[w], ts[w+1]) took wtime[w] cycles,
+// spread evenly over its tiles; warp k's new range starts where the
+// cumulative time reaches k / warps of the total.  Writes wk.tstart2; false
+// if the run aborted.  (The summation order then follows the measured cut,
+// so results may differ in the last bits from run to run.)
+template <class OffT>
+__device__ __noinline__ bool pr_recut_ranges(const PrArgs<OffT>& a, const int* ts, long long nwarps, CtaShared& sh) {
+  const PrWalk& wk = a.wk;
+  Sync* s = a.w.sync;
+  const unsigned grid = gridDim.x;
+  const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  // the exclusive prefix of the warp times, by CTA 0
+  clear_next_slot(s, sh);
+  if (blockIdx.x == 0) {
+    const long long per = (nwarps + kThreads - 1) / kThreads;
+    const long long i0 = (long long)threadIdx.x * per;
+    unsigned long long mine = 0;
+    for (long long i = i0; i < i0 + per && i < nwarps; ++i) mine += wk.wtime[i];
+    unsigned long long incl = mine;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh.red64[warp] = incl;
+    __syncthreads();
+    unsigned long long run = incl - mine;
+    for (int q = 0; q < warp; ++q) run += sh.red64[q];
+    for (long long i = i0; i < i0 + per && i < nwarps; ++i) {
+      wk.wpre[i] = run;
+      run += wk.wtime[i];
+    }
+    if (threadIdx.x == kThreads - 1) wk.wpre[nwarps] = run;
+  }
+  if (!grid_sync(s, grid, sh, a.k)) return false;
+  clear_next_slot(s, sh);
+  {
+    const unsigned long long* pre = wk.wpre;
+    const unsigned long long total = pre[nwarps];
+    const unsigned long long target = total / (unsigned long long)nwarps * (unsigned long long)gw +
+                                      total % (unsigned long long)nwarps * (unsigned long long)gw /
+                                          (unsigned long long)nwarps;
+    const long long w = warp_partition_point(nwarps, [pre, target](long long q) { return pre[q + 1] <= target; });
+    int start = (int)wk.ntiles;
+    if (w < nwarps) {
+      const unsigned long long tw = pre[w + 1] - pre[w];  // > 0: pre[w] <= target < pre[w + 1]
+      const long long ob = ts[w], oe = ts[w + 1];
+      start = (int)(ob + (long long)((unsigned long long)(oe - ob) * (target - pre[w]) / tw));
+    }
+    if (gw == 0) start = 0;
+    if (lane_id() == 0) {
+      wk.tstart2[gw] = start;
+      if (gw == nwarps - 1) wk.tstart2[nwarps] = (int)wk.ntiles;
+    }
+  }
+  return grid_sync(s, grid, sh, a.k);
+}
+
 // TAIL: the instantiation that may switch to push (the pr_alpha knob); the
 // pull-only kernel carries none of its registers.
-template <class OffT, bool TAIL = false>
+// RECUT: the instantiation that re-cuts the warp ranges by measured time
+// (the pr_recut knob); the default kernels carry none of its state.
+template <class OffT, bool TAIL = false, bool RECUT = false>
 __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_constant__ PrArgs<OffT> a) {
   __shared__ CtaShared sh;
   const unsigned grid = gridDim.x;
@@ -682,40 +794,11 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
   const int32_t* l0 = a.w.list[0][0];
   const int32_t* l1 = a.w.list[0][1];
   const int c0n = (int)cnt[0];
-  const int t_beg = wk.tstart[gw], t_end = wk.tstart[gw + 1];
-  int rank0 = 0;
+  int t_beg = 0, t_end = 0, rank0 = 0;
   PrCross cx;
-  if (t_beg >= t_end) {
-    if (lane_id() == 0) wk.headp[gw] = 0.0;  // an empty range adds nothing to a row crossing it
-  } else {
-    const int* ts = wk.tstart;
-    auto warp_of = [ts, nwarps](long long tile) {
-      return (int)warp_partition_point(nwarps, [ts, tile](long long w) { return ts[w] <= tile; }) - 1;
-    };
-    auto nonempty = [ts](int w0, int w1) {  // warps in [w0, w1] with a nonempty range
-      int c = 0;
-      for (int w = w0 + lane_id(); w <= w1; w += 32) c += ts[w] < ts[w + 1];
-      return (int)warp_sum_u64((unsigned long long)c);
-    };
-    auto rows_before = [ioff, l0, c0n](long long x) {
-      return (int)warp_partition_point(c0n, [ioff, l0, x](long long q) { return (long long)gload(ioff + l0[q]) < x; });
-    };
-    const long long x = (long long)t_beg * kTile;
-    rank0 = rows_before(x);
-    if (!((wk.head[x >> 5] >> (x & 31)) & 1u)) {
-      cx.head_rank = rank0 - 1;
-      const int u = l0[cx.head_rank];
-      cx.hw0 = warp_of((long long)gload(ioff + u) / kTile);
-      cx.hw1 = warp_of(((long long)gload(ioff + u + 1) - 1) / kTile);
-      cx.hn = nonempty(cx.hw0, cx.hw1);
-    }
-    const long long xe = (long long)t_end * kTile;
-    if (xe < a.e && !((wk.head[xe >> 5] >> (xe & 31)) & 1u)) {
-      const int u = l0[rows_before(xe) - 1];
-      cx.tail_w1 = warp_of(((long long)gload(ioff + u + 1) - 1) / kTile);
-      cx.tn = nonempty((int)gw, cx.tail_w1);
-    }
-  }
+  pr_warp_setup(a, wk.tstart, nwarps, gw, l0, c0n, t_beg, t_end, rank0, cx);
+  // the zero partials of empty ranges are in place before any row sums them
+  if (!grid_sync(s, grid, sh, k)) return;
 
   const float base = (1.0f - a.d) / (float)n;
   int t = 0;
@@ -735,7 +818,10 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     f.dn = __ull2float_rn(Dfix) * 8.67361737988403547e-19f / (float)n;  // D_t / n (2^-60 units)
     {
       ClassTimer tm(&slot);
+      const bool timed = RECUT && a.recut > 0 && t == a.recut - 1;
+      const long long c0 = timed ? clock64() : 0;
       pr_walk<OffT>(a, f, base, l0, c0n, (int)gw, t_beg, t_end, rank0, cx);
+      if (timed && lane_id() == 0) wk.wtime[gw] = (unsigned long long)(clock64() - c0);
       tm.lap(0);
       for (unsigned i = (unsigned)gtid; i < cnt[1]; i += (unsigned)gthreads) f.finish(a, base, l1[i], 0.f);
       tm.lap(1);
@@ -755,6 +841,12 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     trace_classes(a.w, t, p);
     ++t;
     if (l1_last < (double)a.tol) break;
+    if (RECUT && a.recut > 0 && t == a.recut && t < a.max_iter) {
+      // ranges cut by the measured time of the last walk (the `pr_recut` knob)
+      if (!pr_recut_ranges(a, wk.tstart, nwarps, sh)) return;
+      pr_warp_setup(a, wk.tstart2, nwarps, gw, l0, c0n, t_beg, t_end, rank0, cx);
+      if (!grid_sync(s, grid, sh, k)) return;
+    }
     // switch to push (reading of Sec. 6's decision tree): first test, the
     // pull contracts slowly; only then the second, a scan for the out-edges
     // of the unstable vertices (change above theta * L1_{t-1} / n)
@@ -823,6 +915,7 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   a.alpha = g->cfg.pr_alpha;
   a.theta = g->cfg.pr_theta;
   a.rho = g->cfg.pr_rho;
+  a.recut = g->cfg.pr_recut;
   const bool tail = a.alpha > 0.f;
   // state (20 bytes per vertex): x_alt | c0 | c1 | 1/outdeg | spare; with the
   // push tail 1/outdeg moves to the spare slot, the pending changes (8 bytes)
@@ -834,7 +927,9 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   a.res = reinterpret_cast<unsigned long long*>(st4 + 2 * (size_t)g->n);
   a.w = make_work(g);
   a.k = make_knobs(g);
-  const void* kern = tail ? (const void*)pagerank_kernel<OffT, true> : (const void*)pagerank_kernel<OffT>;
+  const void* kern = a.recut > 0 ? (tail ? (const void*)pagerank_kernel<OffT, true, true>
+                                         : (const void*)pagerank_kernel<OffT, false, true>)
+                                  : (tail ? (const void*)pagerank_kernel<OffT, true> : (const void*)pagerank_kernel<OffT>);
   int grid = grid_for(g, kern);
   // walk layout: row-start bits, tile cost prefix and chunk sums, warp
   // ranges, per-warp partials and arrival counters
@@ -847,7 +942,8 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   const size_t csum_b = up(sizeof(unsigned long long) * (size_t)(nch + 1));
   const size_t ts_b = up(sizeof(int) * (size_t)(nw + 1));
   const size_t part_b = up(sizeof(double) * (size_t)nw);
-  const size_t bytes = head_b + pre_b + csum_b + ts_b + 2 * part_b + up(sizeof(int) * (size_t)nw);
+  const size_t wt_b = up(sizeof(unsigned long long) * (size_t)(nw + 1));
+  const size_t bytes = head_b + pre_b + csum_b + ts_b + 2 * part_b + up(sizeof(int) * (size_t)nw) + 2 * wt_b + ts_b;
   if (!g->pr_ws || g->pr_bytes < bytes) {
     dev_free(g->pr_ws, st);
     g->pr_ws = nullptr;
@@ -863,6 +959,12 @@ static int run_pr(simdx_graph* g, float d, float tol, int max_iter, float* rank,
   a.wk.tailp = reinterpret_cast<double*>(base + head_b + pre_b + csum_b + ts_b);
   a.wk.headp = reinterpret_cast<double*>(base + head_b + pre_b + csum_b + ts_b + part_b);
   a.wk.done = reinterpret_cast<int*>(base + head_b + pre_b + csum_b + ts_b + 2 * part_b);
+  {
+    char* q = base + head_b + pre_b + csum_b + ts_b + 2 * part_b + up(sizeof(int) * (size_t)nw);
+    a.wk.wtime = reinterpret_cast<unsigned long long*>(q);
+    a.wk.wpre = reinterpret_cast<unsigned long long*>(q + wt_b);
+    a.wk.tstart2 = reinterpret_cast<int*>(q + 2 * wt_b);
+  }
   a.wk.ntiles = ntiles;
   a.wk.row_cost = g->cfg.pr_row_cost > 0 ? g->cfg.pr_row_cost : kPrRowCost;
   a.wk.vec4 = (reinterpret_cast<uintptr_t>(g->in_idx) & 15) == 0;

@@ -414,3 +414,19 @@ def test_staged_edges_unaligned_index_array():
     assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0))
     assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
     G.close()
+
+
+@pytest.mark.parametrize("recut", [1, 2, 5])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_pagerank_recut_ranges(gi, recut):
+    """Warp ranges re-cut by the measured walk time after `recut` iterations:
+    the same parity as the cost-model cut (pull runs within 1e-6 of the FP64
+    oracle at the same iteration count; runs that switch to push within their
+    bound)."""
+    g = GRAPHS[gi]
+    G = make(g, bits=32 if gi % 2 else 64, pr_recut=recut)
+    assert_pagerank(G, g)
+    G.set_config(pr_alpha=0.0)
+    st, _ = assert_pagerank(G, g)
+    assert st.push_iters == 0
+    G.close()
