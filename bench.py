@@ -837,7 +837,8 @@ def run_ablation(args, rank, world, local):
     fl = lambda f, x: (f"fusion={['all', 'selective', 'none'][f]} filter={'JIT' if x == 0 else 'ballot'}",
                        dict(fusion=f, filter=x))
     modes = {"bfs": [fl(0, 0), fl(1, 0), fl(2, 0), fl(0, 2), fl(2, 2),
-                     ("edges staged by bulk copy", dict(fusion=0, filter=0, stage_edges=1))],
+                     ("edges staged by bulk copy", dict(fusion=0, filter=0, stage_edges=1)),
+                     ("small frontiers on one cluster", dict(stage_edges=0, small_frontier=1))],
              "sssp": [fl(0, 0), fl(2, 0), fl(0, 2), fl(2, 2),
                       ("combine=plain stores + pull sweeps (no atomics)", dict(fusion=0, filter=0, sssp_combine=1)),
                       ("edges staged by bulk copy", dict(sssp_combine=0, stage_edges=1)),
@@ -869,7 +870,7 @@ def run_ablation(args, rank, world, local):
     for a in wl["algs"]:
         ref = None
         rows = []
-        G.set_config(delta=default_delta, direction=0, stage_edges=0)
+        G.set_config(delta=default_delta, direction=0, stage_edges=0, small_frontier=0)
         for label, knobs in modes[a]:
             G.set_config(**knobs)
             st = simdx_stats()
@@ -901,7 +902,7 @@ def run_ablation(args, rank, world, local):
             rows.append(row)
         res[a] = rows
         G.set_config(fusion=0, filter=0, pr_alpha=8.0, sssp_combine=0, delta=default_delta, direction=0,
-                     pr_row_cost=0, stage_edges=0, pr_recut=0)
+                     pr_row_cost=0, stage_edges=0, pr_recut=0, small_frontier=0)
     G.close()
     base = res[wl["algs"][0]][0]
     return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],

@@ -181,7 +181,13 @@ typedef struct {
                                 cost-model cut [0].  The summation order then follows a
                                 measured cut: results stay within tolerance but may differ in
                                 the last bits from run to run. */
-    int32_t reserved[6];
+    int32_t small_frontier;  /* simdx_bfs (all fusion): 1 = while a push frontier holds at most
+                                4096 vertices and 65536 edges, its levels run on the first
+                                thread-block cluster (8 CTAs, the frontier in distributed shared
+                                memory, a cluster barrier per level) while the other CTAs wait;
+                                0 = every level on the whole grid.  Trace records of such levels
+                                carry bit 19. */
+    int32_t reserved[5];
 } simdx_config;
 
 typedef struct simdx_graph simdx_graph;

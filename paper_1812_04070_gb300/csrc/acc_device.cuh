@@ -73,6 +73,8 @@ struct Sync {
   unsigned long long pad[13];   // the polled words alone on their 128-byte line
   PhaseSlot slot[3];
   Resume rs;
+  unsigned long long loc_epoch;  // small-frontier episodes handed back to the grid
+  long long loc[16];             // the loop state an episode hands back
 };
 
 struct DevStats {
@@ -93,6 +95,7 @@ struct Knobs {
   int fusion;           // 0 all iterations in one launch, 1 one launch per run of one
                         // direction, 2 one launch per iteration (Sec. 5, Table 2)
   int stage;            // stage CTA-class edge ranges in shared memory by bulk copy
+  int small;            // small frontiers run on one thread-block cluster
 };
 
 // Workspace shared by all algorithms of one graph.

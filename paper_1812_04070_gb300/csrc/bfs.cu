@@ -21,9 +21,14 @@
 //               on overflow (or when forced) the ballot filter rebuilds
 //               sorted, unique lists from the level array or the frontier
 //               bitmap (Sec. 4, JIT control).
+#include <cooperative_groups.h>
+
 #include <cstring>
+#include <type_traits>
 
 #include "simdx_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace simdx {
 
@@ -324,6 +329,206 @@ __device__ void bfs_pull_big(const BfsArgs<OffT>& a, int cur, const uint32_t* fb
   }
 }
 
+// ------------------------------------------------ small frontiers
+// A push level with a small frontier costs a grid barrier and a chain of
+// dependent global round trips whatever its size (about 10 us on GB300).
+// While the frontier stays small, the levels run on the first thread-block
+// cluster alone: the frontier lives in the distributed shared memory of its
+// kCluster CTAs (a vertex goes to the CTA u % kCluster), each level ends with
+// a cluster barrier, and every CTA of the cluster takes the same decision
+// from the counters in rank 0's shared memory.  The other CTAs wait on a
+// flag (bounded like the grid barrier).  The episode hands the loop state
+// back through the barrier block; levels are in the level array, so the grid
+// rebuilds its lists by the ballot filter.
+constexpr int kCluster = 8;                         // CTAs of the cluster
+constexpr int kLocCap = 1024;                       // frontier entries per CTA buffer
+constexpr unsigned kLocEnterN = 4096;               // enter at most this many frontier vertices
+constexpr unsigned long long kLocEnterM = 65536;    // ... and frontier edges
+constexpr unsigned kLocExitN = 6144;                // leave when the next frontier holds more
+
+struct LocalShared {
+  int32_t f[3][kLocCap];          // this CTA's share of three consecutive frontiers
+  unsigned cnt[3];
+  unsigned ntot[3];               // rank 0: vertices of a frontier over the cluster
+  unsigned ovf[3];                // rank 0: a buffer of that frontier overflowed
+  unsigned stop[3];               // rank 0: the run aborted (read before the barrier)
+  unsigned long long medges[3];   // rank 0: out-edges of the frontier
+};
+
+enum { kLcL, kLcNf, kLcMf, kLcPrevNf, kLcMu, kLcIt, kLcPushIt, kLcOnlineIt, kLcFsum, kLcDone };
+
+// One episode of small-frontier levels (every CTA calls it; cluster 0 works,
+// the rest wait).  The current frontier is the class lists (at most
+// kLocEnterN entries, so a CTA's share fits its buffer).  Returns false if
+// the run aborted.
+template <class OffT>
+__device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh, const unsigned* cnt, int lbuf,
+                          int& L, unsigned long long& n_f, unsigned long long& prev_n_f, unsigned long long& m_f,
+                          long long& m_u, int& it, int& push_it, int& online_it, long long& fsum, long long& evisit,
+                          unsigned long long& episodes, bool& done) {
+  Sync* s = a.w.sync;
+  const Knobs& k = a.k;
+  if (blockIdx.x < kCluster) {
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned r = cl.block_rank();
+    LocalShared* L0 = cl.map_shared_rank(&ls, 0u);
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    if (threadIdx.x < 3) {
+      ls.cnt[threadIdx.x] = 0;
+      ls.ntot[threadIdx.x] = 0;
+      ls.ovf[threadIdx.x] = 0;
+      ls.stop[threadIdx.x] = 0;
+      ls.medges[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    // this CTA's share of the current frontier: the entries j of the class
+    // lists (in class order) with j % kCluster == r
+    unsigned base = 0;
+    for (int c = 0; c < kClasses; ++c) {
+      const int32_t* list = a.w.list[lbuf][c];
+      for (unsigned i = threadIdx.x; i < cnt[c]; i += kThreads)
+        if ((base + i) % kCluster == r) ls.f[0][atomicAdd(&ls.cnt[0], 1u)] = list[i];
+      base += cnt[c];
+    }
+    cl.sync();
+    int cur = 0;
+    while (true) {
+      const int nx = cur == 2 ? 0 : cur + 1, nn = nx == 2 ? 0 : nx + 1;
+      const unsigned long long t_it = globaltimer();
+      if (threadIdx.x == 0) {
+        ls.cnt[nn] = 0;  // the frontier after next: nobody touches it in this level
+        if (r == 0) {
+          ls.ntot[nn] = 0;
+          ls.ovf[nn] = 0;
+          ls.stop[nn] = 0;
+          ls.medges[nn] = 0;
+          ls.stop[nx] = (unsigned)ld_volatile_i32(&s->abort);
+        }
+      }
+      const unsigned myc = ls.cnt[cur] < (unsigned)kLocCap ? ls.cnt[cur] : (unsigned)kLocCap;
+      const int next = L + 1;
+      unsigned long long nrec = 0, mrec = 0;
+      // groups of up to 32 consecutive tasks per warp; the warp walks their
+      // concatenated edges, kPushBatch rounds of 32 edge slots at a time
+      unsigned gs = (myc + kWarps - 1) / kWarps;
+      gs = gs < 1 ? 1 : (gs > 32 ? 32 : gs);
+      for (unsigned b = (unsigned)warp * gs; b < myc; b += (unsigned)kWarps * gs) {
+        const unsigned lim = b + gs < myc ? b + gs : myc;
+        const unsigned i = b + lane;
+        long long beg = 0;
+        int deg = 0;
+        if (i < lim) {
+          const int v = ls.f[cur][i];
+          beg = gload(a.off + v);
+          deg = (int)(gload(a.off + v + 1) - beg);
+        }
+        int incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - deg;
+        for (int e0 = 0; e0 < total; e0 += 32 * kPushBatch) {
+          int u[kPushBatch], lv[kPushBatch];
+#pragma unroll
+          for (int q = 0; q < kPushBatch; ++q) {
+            const int e = e0 + 32 * q + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              const int t = __shfl_sync(kFull, incl, j + step - 1);
+              if (t <= e) j += step;
+            }
+            const long long bj = __shfl_sync(kFull, beg, j);
+            const int xj = __shfl_sync(kFull, excl, j);
+            u[q] = e < total ? gload(a.idx + bj + (e - xj)) : -1;
+          }
+#pragma unroll
+          for (int q = 0; q < kPushBatch; ++q) lv[q] = u[q] >= 0 ? a.level[u[q]] : 0;
+#pragma unroll
+          for (int q = 0; q < kPushBatch; ++q) {
+            if (u[q] >= 0 && lv[q] == -1 && atomicCAS(&a.level[u[q]], -1, next) == -1) {
+              const long long d = (long long)gload(a.off + u[q] + 1) - (long long)gload(a.off + u[q]);
+              ++nrec;
+              mrec += (unsigned long long)d;
+              LocalShared* Ld = cl.map_shared_rank(&ls, (unsigned)u[q] % kCluster);
+              const unsigned pos = atomicAdd(&Ld->cnt[nx], 1u);
+              if (pos < (unsigned)kLocCap) Ld->f[nx][pos] = u[q];
+              else atomicOr(&L0->ovf[nx], 1u);
+            }
+          }
+        }
+        evisit += deg;
+      }
+      nrec = cta_sum_u64(nrec, sh);
+      mrec = cta_sum_u64(mrec, sh);
+      if (threadIdx.x == 0 && nrec) {
+        atomicAdd(&L0->ntot[nx], (unsigned)nrec);
+        atomicAdd(&L0->medges[nx], mrec);
+      }
+      cl.sync();
+      // the same values, so the same decisions, in every CTA of the cluster
+      const unsigned N = L0->ntot[nx], O = L0->ovf[nx], X = L0->stop[nx];
+      const unsigned long long M = L0->medges[nx];
+      trace_put(a.w, it, kPush | (kOnline << 8) | (1 << 19), (long long)n_f, (long long)m_f, L, t_it);
+      fsum += (long long)n_f;
+      ++it;
+      ++push_it;
+      ++online_it;
+      prev_n_f = n_f;
+      n_f = N;
+      m_f = M;
+      m_u -= (long long)M;
+      ++L;
+      if (N == 0) {
+        done = true;
+        break;
+      }
+      const bool to_pull = k.direction != 1 && (double)M > (double)m_u / k.alpha;
+      if (O || X || N > kLocExitN || M > kLocEnterM || to_pull) break;
+      cur = nx;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      long long* w = s->loc;
+      w[kLcL] = L; w[kLcNf] = (long long)n_f; w[kLcMf] = (long long)m_f; w[kLcPrevNf] = (long long)prev_n_f;
+      w[kLcMu] = m_u; w[kLcIt] = it; w[kLcPushIt] = push_it; w[kLcOnlineIt] = online_it; w[kLcFsum] = fsum;
+      w[kLcDone] = done;
+      red_release_add_u64(&s->loc_epoch, 1ull);
+    }
+  }
+  // every CTA: wait for the episode's hand-back (bounded), then take its state
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    while (ld_acquire_u64(&s->loc_epoch) < episodes + 1) {
+      __nanosleep(64);
+      if ((++spins & 63u) == 0) {
+        if (ld_volatile_i32(&s->abort)) { ok = 0; break; }
+        const unsigned long long t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > k.timeout_ns) {
+          atomicExch(&s->abort, 1);
+          atomicCAS(&s->err, 0, 4 /* SIMDX_EBARRIER_TIMEOUT */);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    sh.ok = ok;
+  }
+  __syncthreads();
+  if (!sh.ok) return false;
+  ++episodes;
+  const volatile long long* w = s->loc;
+  L = (int)w[kLcL]; n_f = (unsigned long long)w[kLcNf]; m_f = (unsigned long long)w[kLcMf];
+  prev_n_f = (unsigned long long)w[kLcPrevNf]; m_u = w[kLcMu]; it = (int)w[kLcIt]; push_it = (int)w[kLcPushIt];
+  online_it = (int)w[kLcOnlineIt]; fsum = w[kLcFsum]; done = w[kLcDone] != 0;
+  return true;
+}
+
 // Loop state words of the resume record (Resume::v) for a run split over
 // several launches.
 enum { kRsL, kRsLbuf, kRsFb, kRsListsOk, kRsBmOk, kRsPrevDir, kRsCnt0, kRsNf = kRsCnt0 + kClasses, kRsPrevNf,
@@ -336,13 +541,16 @@ static_assert(kRsPhases < kResumeWords, "resume record too small");
 // STAGE: CTA-class push ranges staged in shared memory by bulk copy (the
 // `stage` knob; a separate instantiation, so the default kernel keeps its
 // shared-memory footprint and L1 share).
-template <class OffT, int DIRS = kPush | kPull, bool STAGE = false>
+// CLU: small frontiers run on the first thread-block cluster (the
+// small_frontier knob; launched with a cluster dimension of kCluster).
+template <class OffT, int DIRS = kPush | kPull, bool STAGE = false, bool CLU = false>
 __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   constexpr bool kHasPush = (DIRS & kPush) != 0;
   constexpr bool kHasPull = (DIRS & kPull) != 0;
   constexpr bool kSplit = DIRS != (kPush | kPull);  // runs may span several launches
   __shared__ CtaShared sh;
   __shared__ PullShared ps;
+  __shared__ typename std::conditional<CLU, LocalShared, char>::type loc_sm;
   const unsigned grid = gridDim.x;
   Sync* s = a.w.sync;
   const Knobs& k = a.k;
@@ -432,6 +640,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     phases0 = r[kRsPhases];
   }
   const int it_launch = it;  // first iteration of this launch
+  unsigned long long episodes = 0;  // small-frontier episodes so far
 
   while (true) {
     const unsigned long long t_it = globaltimer();
@@ -502,6 +711,22 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
       lists_ok = true;
       filt = kBallot;
+    }
+
+    // -------- a small push frontier: levels on one cluster until it grows
+    if constexpr (CLU) {
+      if (k.small && dir == kPush && k.direction != 2 && cnt[0] + cnt[1] + cnt[2] + cnt[3] <= kLocEnterN &&
+          m_f <= kLocEnterM) {
+        bool done = false;
+        if (!bfs_local(a, loc_sm, sh, cnt, lbuf, L, n_f, prev_n_f, m_f, m_u, it, push_it, online_it, fsum, evisit,
+                       episodes, done))
+          return;
+        lists_ok = false;  // levels are in the level array: the ballot filter lists the frontier
+        bm_ok = false;
+        prev_dir = kPush;
+        if (done) break;
+        continue;
+      }
     }
 
     // -------- compute (push or pull) with the online filter recording
@@ -621,6 +846,16 @@ static int run_bfs(simdx_graph* g, int32_t src, int32_t* levels, simdx_stats* st
   int rc = prepare_launch(g, st);
   if (rc) return rc;
   void* args[] = {&a};
+  if (a.k.fusion == 0 && a.k.small && !a.k.stage) {
+    // small frontiers on the first cluster: a cooperative launch in clusters
+    const void* kern = (const void*)bfs_kernel<OffT, kPush | kPull, false, true>;
+    const int grid = grid_for_cluster(g, kern, kCluster);
+    if (grid >= kCluster) {
+      if ((rc = launch_coop(kern, grid, args, st, kCluster)) != SIMDX_OK) return rc;
+      return finish_launch(g, stats, st);
+    }
+    a.k.small = 0;  // no cluster fits: the grid runs every level
+  }
   if (a.k.fusion == 0) {
     const void* kern = a.k.stage ? (const void*)bfs_kernel<OffT, kPush | kPull, true> : (const void*)bfs_kernel<OffT>;
     if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;

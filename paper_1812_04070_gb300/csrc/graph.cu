@@ -105,6 +105,7 @@ Knobs make_knobs(const simdx_graph* g) {
   k.skip_phase = c.debug_skip_phase;
   k.fusion = c.fusion;
   k.stage = c.stage_edges;
+  k.small = c.small_frontier;
   return k;
 }
 
@@ -188,20 +189,58 @@ int read_resume(simdx_graph* g, cudaStream_t st, int* done, int* want_dir) {
 
 // A cooperative launch through the extensible launch API, which stream
 // capture records as a cooperative kernel node.
-int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st) {
-  if (grid <= 0) return SIMDX_EUNSUPPORTED;
+int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st, int cluster) {
+  if (grid <= 0 || (cluster > 1 && grid % cluster)) return SIMDX_EUNSUPPORTED;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (cluster > 1) {
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = (unsigned)cluster;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.numAttrs = 2;
+  }
   SIMDX_CUDA(cudaLaunchKernelExC(&cfg, kernel, args));
   return SIMDX_OK;
+}
+
+// Co-resident grid in clusters of `cluster` CTAs: the occupancy grid, at
+// most the clusters that fit at once, a multiple of the cluster size (0 if
+// none fits).
+int grid_for_cluster(const simdx_graph* g, const void* kernel, int cluster) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> max_clusters;
+  int mc = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = max_clusters.find(kernel);
+    if (it != max_clusters.end()) {
+      mc = it->second;
+    } else {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(cluster * 64);
+      cfg.blockDim = dim3(kThreads);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)cluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&mc, kernel, &cfg) != cudaSuccess) mc = 0;
+      max_clusters[kernel] = mc;
+    }
+  }
+  int grid = std::min(grid_for(g, kernel), mc * cluster);
+  return grid - grid % cluster;
 }
 
 bool capturing(cudaStream_t st) {
@@ -594,7 +633,8 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
       !(cfg->pr_rho >= 0.f) || cfg->sssp_combine < 0 || cfg->sssp_combine > 1 ||
       (cfg->sssp_batch_width != 0 && cfg->sssp_batch_width != 8 && cfg->sssp_batch_width != 16 &&
        cfg->sssp_batch_width != 32 && cfg->sssp_batch_width != 64) || cfg->pr_row_cost < 0 ||
-      cfg->pr_row_cost > 4096 || cfg->stage_edges < 0 || cfg->stage_edges > 1 || cfg->pr_recut < 0)
+      cfg->pr_row_cost > 4096 || cfg->stage_edges < 0 || cfg->stage_edges > 1 || cfg->pr_recut < 0 ||
+      cfg->small_frontier < 0 || cfg->small_frontier > 1)
     return SIMDX_EINVAL;
   bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
                     cfg->huge_min != g->cfg.huge_min;

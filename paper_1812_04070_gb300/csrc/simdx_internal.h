@@ -108,8 +108,11 @@ int read_resume(simdx_graph* g, cudaStream_t st, int* done, int* want_dir);
 // preparation or stats (the caller brackets it).
 int bfs_launch_only(simdx_graph* g, int32_t src, int32_t* levels, cudaStream_t st);
 
-// Launch `kernel` cooperatively with `grid` CTAs of kThreads threads.
-int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st);
+// Launch `kernel` cooperatively with `grid` CTAs of kThreads threads (in
+// clusters of `cluster` CTAs when cluster > 1).
+int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st, int cluster = 1);
+// The co-resident grid of `kernel` in clusters of `cluster` CTAs (0: none fits).
+int grid_for_cluster(const simdx_graph* g, const void* kernel, int cluster);
 
 // Enqueue the copy of device statistics into `user` (may be NULL; must be
 // NULL while `st` is being captured into a CUDA graph); `launches` = kernel

@@ -59,7 +59,8 @@ class simdx_config(ctypes.Structure):
                 ("pr_alpha", ctypes.c_float), ("pr_theta", ctypes.c_float), ("pr_rho", ctypes.c_float),
                 ("sssp_combine", ctypes.c_int32), ("sssp_batch_width", ctypes.c_int32),
                 ("pr_row_cost", ctypes.c_int32), ("stage_edges", ctypes.c_int32),
-                ("pr_recut", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("pr_recut", ctypes.c_int32), ("small_frontier", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _LIB = None

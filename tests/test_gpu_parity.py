@@ -430,3 +430,47 @@ def test_pagerank_recut_ranges(gi, recut):
     st, _ = assert_pagerank(G, g)
     assert st.push_iters == 0
     G.close()
+
+
+# Small frontiers on one thread-block cluster (small_frontier): the same
+# levels as the grid, with the frontier in distributed shared memory.
+SMALL = {"small": dict(small_frontier=1), "small_push": dict(small_frontier=1, direction=1),
+         "small_all_classes": dict(small_frontier=1, small_max=2, med_max=4, huge_min=8),
+         "small_ballot": dict(small_frontier=1, filter=2)}
+
+
+@pytest.mark.parametrize("mode", list(SMALL))
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_bfs_small_frontier_cluster(gi, mode):
+    g = GRAPHS[gi]
+    G = make(g, bits=32 if gi % 2 else 64, **SMALL[mode])
+    for s in sources(g):
+        assert np.array_equal(G.bfs(s).cpu().numpy(), oracle.bfs(g.offsets, g.indices, s)), (g.name, mode, s)
+    assert G.last_status() == 0
+    G.close()
+
+
+def test_bfs_small_frontier_levels_and_multi_root():
+    """On a grid every level is small: the trace marks the cluster levels
+    (bit 19), and the statistics count every level; a multi-root BFS over a
+    block-diagonal pack gives each graph's levels."""
+    import torch
+    from paper_1812_04070_gb300 import simdx_stats
+    g = gg.grid(120, 90)
+    G = make(g, bits=64, small_frontier=1)
+    st = simdx_stats()
+    lev = G.bfs(0, stats=st).cpu().numpy()
+    torch.cuda.synchronize()
+    assert np.array_equal(lev, oracle.bfs(g.offsets, g.indices, 0))
+    assert st.iterations == 120 + 90 - 1 and st.status == 0
+    tr = G.trace()
+    assert sum((int(r[0]) >> 19) & 1 for r in tr) >= st.iterations - 2
+    G.close()
+    graphs, srcs = gg.multigraph_batch(count=12, n_lo=50, n_hi=2000, seed=9)
+    packed, bases = gg.pack(graphs)
+    roots = [int(x) for x in (srcs.astype(np.int64) + bases[:-1])]
+    P = make(packed, bits=32, small_frontier=1)
+    lv = P.bfs_multi(roots).cpu().numpy()
+    for i, x in enumerate(graphs):
+        assert np.array_equal(lv[bases[i]:bases[i + 1]], oracle.bfs(x.offsets, x.indices, int(srcs[i]))), i
+    P.close()
