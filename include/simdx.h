@@ -183,10 +183,12 @@ typedef struct {
                                 the last bits from run to run. */
     int32_t small_frontier;  /* simdx_bfs (all fusion): 1 = while a push frontier holds at most
                                 4096 vertices and 65536 edges, its levels run on the first
-                                thread-block cluster (8 CTAs, the frontier in distributed shared
+                                thread-block cluster (16 CTAs, the frontier in distributed shared
                                 memory, a cluster barrier per level) while the other CTAs wait;
+                                the launch is then in clusters of 16 (a few CTAs fewer fit).
                                 0 = every level on the whole grid.  Trace records of such levels
-                                carry bit 19. */
+                                carry bit 19, with words 6 and 7 the times (ns) at which CTA 0
+                                finished its walk and passed the cluster barrier. */
     int32_t reserved[5];
 } simdx_config;
 

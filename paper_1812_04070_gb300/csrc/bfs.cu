@@ -333,34 +333,141 @@ __device__ void bfs_pull_big(const BfsArgs<OffT>& a, int cur, const uint32_t* fb
 // A push level with a small frontier costs a grid barrier and a chain of
 // dependent global round trips whatever its size (about 10 us on GB300).
 // While the frontier stays small, the levels run on the first thread-block
-// cluster alone: the frontier lives in the distributed shared memory of its
-// kCluster CTAs (a vertex goes to the CTA u % kCluster), each level ends with
-// a cluster barrier, and every CTA of the cluster takes the same decision
-// from the counters in rank 0's shared memory.  The other CTAs wait on a
-// flag (bounded like the grid barrier).  The episode hands the loop state
-// back through the barrier block; levels are in the level array, so the grid
-// rebuilds its lists by the ballot filter.
-constexpr int kCluster = 8;                         // CTAs of the cluster
-constexpr int kLocCap = 1024;                       // frontier entries per CTA buffer
+// cluster alone, with a cluster barrier per level; the other CTAs wait on a
+// flag (bounded like the grid barrier).  Each CTA of the cluster appends the
+// vertices it claims to its own shared memory (one shared atomic per warp
+// and batch slot); before the barrier it stores its counters into every
+// CTA's shared memory, so after it all CTAs read the same totals locally and
+// take the same decisions.  CTA r walks the r-th sixteenth of the
+// concatenated buffers, reading the entries from distributed shared memory.
+// No remote atomics, no contended counters.  The episode hands the loop
+// state back through the barrier block; levels are in the level array, so
+// the grid rebuilds its lists by the ballot filter.
+//
+// A frontier entry is the vertex's edge range, packed as (beg << 24) | deg:
+// the claim of a vertex loads its offsets together with the compare-and-swap
+// on its level, so a level is two dependent global round trips (edge
+// targets; claim + offsets) plus the cluster barrier.  Degrees of a walked
+// frontier are at most kLocEnterM (a larger one ends the episode before its
+// level), and beg < 2^39 for any graph that fits in device memory (bit 63
+// marks a claim while the entry is in registers).
+constexpr int kCluster = 16;                        // CTAs of the cluster (a non-portable size)
+constexpr int kLocCap = 512;                        // entries a CTA can claim in one level
 constexpr unsigned kLocEnterN = 4096;               // enter at most this many frontier vertices
 constexpr unsigned long long kLocEnterM = 65536;    // ... and frontier edges
 constexpr unsigned kLocExitN = 6144;                // leave when the next frontier holds more
+constexpr int kLocBatch = 4;                        // edges per lane in flight
+constexpr unsigned long long kLocDegMask = (1ull << 24) - 1;
+static_assert(kCluster <= 32 && (kCluster & (kCluster - 1)) == 0, "one lane per CTA of the cluster");
 
-struct LocalShared {
-  int32_t f[3][kLocCap];          // this CTA's share of three consecutive frontiers
-  unsigned cnt[3];
-  unsigned ntot[3];               // rank 0: vertices of a frontier over the cluster
-  unsigned ovf[3];                // rank 0: a buffer of that frontier overflowed
-  unsigned stop[3];               // rank 0: the run aborted (read before the barrier)
-  unsigned long long medges[3];   // rank 0: out-edges of the frontier
+struct LocCounters {
+  unsigned long long medges;  // out-edges of the CTA's claims
+  unsigned cnt;               // the CTA's claims
+  unsigned flags;             // bit 0: it claimed more than kLocCap; bit 1 (rank 0): the run aborted
 };
 
-enum { kLcL, kLcNf, kLcMf, kLcPrevNf, kLcMu, kLcIt, kLcPushIt, kLcOnlineIt, kLcFsum, kLcDone };
+struct LocalShared {
+  unsigned long long f[2][kLocCap];  // entries this CTA claimed: the current and the next frontier
+  unsigned cnt[3];                   // claims of this CTA in a level (counter slots rotate over three)
+  unsigned ovf[3];                   // this CTA claimed more than kLocCap
+  unsigned stop;                     // rank 0: the run aborted (read before the barrier)
+  unsigned long long medges[3];      // out-edges of this CTA's claims
+  LocCounters all[3][kCluster];      // every CTA's counters of a level, stored here by that CTA
+};
+
+// The pull levels' and the cluster levels' shared memory never live at once
+// (a grid barrier or the episode's closing cluster barrier lies between).
+union PullLocalShared {
+  PullShared ps;
+  LocalShared loc;
+};
+__device__ __forceinline__ PullShared& pull_part(PullShared& x) { return x; }
+__device__ __forceinline__ PullShared& pull_part(PullLocalShared& x) { return x.ps; }
+
+enum { kLcL, kLcNf, kLcMf, kLcPrevNf, kLcMu, kLcIt, kLcPushIt, kLcOnlineIt, kLcFsum, kLcDone, kLcBeat = 15 };
+
+__device__ __forceinline__ unsigned long long loc_pack(long long beg, long long deg) {
+  return ((unsigned long long)beg << 24) | (unsigned long long)(deg < (long long)kLocDegMask ? deg : kLocDegMask);
+}
+
+// The edge j (0 <= j < total) of a warp's group of up to 64 tasks: lane t
+// holds tasks t and t + 32 with inclusive edge prefixes ia, ib (ib counts on
+// from the first half's total ta).  Returns the task's lane and half.  Every
+// lane reads both prefixes of the lane it probes and keeps the one of its
+// own half (a lane's half depends on its own j).
+__device__ __forceinline__ int loc_find(int ia, int ib, int ta, int j, bool& hi) {
+  hi = j >= ta;
+  int t = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int xa = __shfl_sync(kFull, ia, t + step - 1);
+    const int xb = __shfl_sync(kFull, ib, t + step - 1);
+    if ((hi ? xb : xa) <= j) t += step;
+  }
+  return t;
+}
+
+// The CTA (lane of the warp) that holds entry g of the concatenated buffers:
+// lanes 0..kCluster-1 hold the exclusive prefix p of the CTAs' counts (lanes
+// beyond hold ~0u).
+__device__ __forceinline__ int loc_owner(unsigned p, unsigned g) {
+  int t = 0;
+#pragma unroll
+  for (int step = kCluster / 2; step >= 1; step >>= 1) {
+    const unsigned x = __shfl_sync(kFull, p, t + step);
+    if (x <= g) t += step;
+  }
+  return t;
+}
+
+// Before a cluster barrier: this CTA's counters of slot `sl` go to every
+// CTA of the cluster (thread c stores to CTA c), so that after the barrier
+// they are read locally.  The CTA's appends are complete (__syncthreads).
+__device__ __forceinline__ void loc_publish(cg::cluster_group& cl, LocalShared& ls, int sl, unsigned r) {
+  __syncthreads();
+  if (threadIdx.x < kCluster) {
+    LocCounters c;
+    c.medges = ls.medges[sl];
+    c.cnt = ls.cnt[sl];
+    c.flags = (ls.ovf[sl] ? 1u : 0u) | (r == 0 && ls.stop ? 2u : 0u);
+    cl.map_shared_rank(&ls, threadIdx.x)->all[sl][r] = c;
+  }
+}
+
+// After a cluster barrier: every warp reads counter slot `sl` of all CTAs
+// (lane c, CTA c's copy in this CTA's shared memory).  Returns the lane's
+// count and exclusive prefix (for lanes below kCluster) and the cluster's
+// totals.
+__device__ __forceinline__ void loc_counts(LocalShared& ls, int sl, unsigned& c, unsigned& p, unsigned& n,
+                                           unsigned long long& m, unsigned& o, unsigned& x) {
+  const int lane = lane_id();
+  c = 0;
+  unsigned long long me = 0;
+  o = 0;
+  x = 0;
+  if (lane < kCluster) {
+    const LocCounters& r = ls.all[sl][lane];
+    c = r.cnt;
+    me = r.medges;
+    o = r.flags & 1u;
+    x = r.flags & 2u;
+  }
+  unsigned incl = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  n = __shfl_sync(kFull, incl, 31);
+  p = lane < kCluster ? incl - c : ~0u;
+  m = warp_sum_u64(me);
+  o = __any_sync(kFull, o != 0) ? 1u : 0u;
+  x = __any_sync(kFull, x != 0) ? 1u : 0u;
+}
 
 // One episode of small-frontier levels (every CTA calls it; cluster 0 works,
 // the rest wait).  The current frontier is the class lists (at most
-// kLocEnterN entries, so a CTA's share fits its buffer).  Returns false if
-// the run aborted.
+// kLocEnterN entries).  Returns false if the run aborted.
 template <class OffT>
 __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh, const unsigned* cnt, int lbuf,
                           int& L, unsigned long long& n_f, unsigned long long& prev_n_f, unsigned long long& m_f,
@@ -371,108 +478,149 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
   if (blockIdx.x < kCluster) {
     cg::cluster_group cl = cg::this_cluster();
     const unsigned r = cl.block_rank();
-    LocalShared* L0 = cl.map_shared_rank(&ls, 0u);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     if (threadIdx.x < 3) {
       ls.cnt[threadIdx.x] = 0;
-      ls.ntot[threadIdx.x] = 0;
       ls.ovf[threadIdx.x] = 0;
-      ls.stop[threadIdx.x] = 0;
       ls.medges[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) ls.stop = 0;
     __syncthreads();
-    // this CTA's share of the current frontier: the entries j of the class
-    // lists (in class order) with j % kCluster == r
+    // the current frontier: the entries j of the class lists (in class
+    // order) with j % kCluster == r, as if this CTA had claimed them
     unsigned base = 0;
     for (int c = 0; c < kClasses; ++c) {
       const int32_t* list = a.w.list[lbuf][c];
       for (unsigned i = threadIdx.x; i < cnt[c]; i += kThreads)
-        if ((base + i) % kCluster == r) ls.f[0][atomicAdd(&ls.cnt[0], 1u)] = list[i];
+        if ((base + i) % kCluster == r) {
+          const int v = list[i];
+          const long long b0 = (long long)gload(a.off + v);
+          ls.f[0][atomicAdd(&ls.cnt[0], 1u)] = loc_pack(b0, (long long)gload(a.off + v + 1) - b0);
+        }
       base += cnt[c];
     }
+    loc_publish(cl, ls, 0, r);
     cl.sync();
-    int cur = 0;
+    unsigned cc, cp, N;  // this lane's CTA count and prefix; frontier size
+    {
+      unsigned long long M0;
+      unsigned O0, X0;
+      loc_counts(ls, 0, cc, cp, N, M0, O0, X0);
+    }
+    // counter slots rotate over three (the one after next is cleared during
+    // a level), entry buffers over two
+    int cur = 0, fc = 0;
     while (true) {
       const int nx = cur == 2 ? 0 : cur + 1, nn = nx == 2 ? 0 : nx + 1;
       const unsigned long long t_it = globaltimer();
+      unsigned ab = 0;
       if (threadIdx.x == 0) {
-        ls.cnt[nn] = 0;  // the frontier after next: nobody touches it in this level
+        ls.cnt[nn] = 0;  // slot nn was last read before the previous barrier
+        ls.ovf[nn] = 0;
+        ls.medges[nn] = 0;
         if (r == 0) {
-          ls.ntot[nn] = 0;
-          ls.ovf[nn] = 0;
-          ls.stop[nn] = 0;
-          ls.medges[nn] = 0;
-          ls.stop[nx] = (unsigned)ld_volatile_i32(&s->abort);
+          ab = (unsigned)ld_volatile_i32(&s->abort);  // stored at the end of the level
+          if (blockIdx.x == 0) *(volatile long long*)&s->loc[kLcBeat] = L;  // progress for the waiting CTAs
         }
       }
-      const unsigned myc = ls.cnt[cur] < (unsigned)kLocCap ? ls.cnt[cur] : (unsigned)kLocCap;
+      // this CTA's slice of the frontier
+      const unsigned lo = (unsigned)(((unsigned long long)N * r) / kCluster);
+      const unsigned myc = (unsigned)(((unsigned long long)N * (r + 1)) / kCluster) - lo;
       const int next = L + 1;
-      unsigned long long nrec = 0, mrec = 0;
-      // groups of up to 32 consecutive tasks per warp; the warp walks their
-      // concatenated edges, kPushBatch rounds of 32 edge slots at a time
+      unsigned long long mrec = 0;
+      // groups of up to 64 tasks per warp (two per lane); the warp walks
+      // their concatenated edges, kLocBatch rounds of 32 at a time
       unsigned gs = (myc + kWarps - 1) / kWarps;
-      gs = gs < 1 ? 1 : (gs > 32 ? 32 : gs);
+      gs = gs < 1 ? 1 : (gs > 64 ? 64 : gs);
       for (unsigned b = (unsigned)warp * gs; b < myc; b += (unsigned)kWarps * gs) {
         const unsigned lim = b + gs < myc ? b + gs : myc;
-        const unsigned i = b + lane;
-        long long beg = 0;
-        int deg = 0;
-        if (i < lim) {
-          const int v = ls.f[cur][i];
-          beg = gload(a.off + v);
-          deg = (int)(gload(a.off + v + 1) - beg);
-        }
-        int incl = deg;
+        const unsigned i0 = b + lane, i1 = b + 32 + lane;
+        const unsigned g0 = lo + (i0 < lim ? i0 : 0), g1 = lo + (i1 < lim ? i1 : 0);
+        const int t0 = loc_owner(cp, g0), t1 = loc_owner(cp, g1);
+        const unsigned p0 = __shfl_sync(kFull, cp, t0), p1 = __shfl_sync(kFull, cp, t1);
+        unsigned long long e0 = 0, e1 = 0;
+        if (i0 < lim) e0 = cl.map_shared_rank(&ls, (unsigned)t0)->f[fc][g0 - p0];
+        if (i1 < lim) e1 = cl.map_shared_rank(&ls, (unsigned)t1)->f[fc][g1 - p1];
+        const long long b0 = (long long)(e0 >> 24), b1 = (long long)(e1 >> 24);
+        const int d0 = (int)(e0 & kLocDegMask), d1 = (int)(e1 & kLocDegMask);
+        int ia = d0, ib = d1;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - deg;
-        for (int e0 = 0; e0 < total; e0 += 32 * kPushBatch) {
-          int u[kPushBatch], lv[kPushBatch];
-#pragma unroll
-          for (int q = 0; q < kPushBatch; ++q) {
-            const int e = e0 + 32 * q + lane;
-            int j = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-              const int t = __shfl_sync(kFull, incl, j + step - 1);
-              if (t <= e) j += step;
-            }
-            const long long bj = __shfl_sync(kFull, beg, j);
-            const int xj = __shfl_sync(kFull, excl, j);
-            u[q] = e < total ? gload(a.idx + bj + (e - xj)) : -1;
-          }
-#pragma unroll
-          for (int q = 0; q < kPushBatch; ++q) lv[q] = u[q] >= 0 ? a.level[u[q]] : 0;
-#pragma unroll
-          for (int q = 0; q < kPushBatch; ++q) {
-            if (u[q] >= 0 && lv[q] == -1 && atomicCAS(&a.level[u[q]], -1, next) == -1) {
-              const long long d = (long long)gload(a.off + u[q] + 1) - (long long)gload(a.off + u[q]);
-              ++nrec;
-              mrec += (unsigned long long)d;
-              LocalShared* Ld = cl.map_shared_rank(&ls, (unsigned)u[q] % kCluster);
-              const unsigned pos = atomicAdd(&Ld->cnt[nx], 1u);
-              if (pos < (unsigned)kLocCap) Ld->f[nx][pos] = u[q];
-              else atomicOr(&L0->ovf[nx], 1u);
-            }
+          const int ya = __shfl_up_sync(kFull, ia, o), yb = __shfl_up_sync(kFull, ib, o);
+          if (lane >= o) {
+            ia += ya;
+            ib += yb;
           }
         }
-        evisit += deg;
+        const int ta = __shfl_sync(kFull, ia, 31);
+        ib += ta;
+        const int total = __shfl_sync(kFull, ib, 31);
+        for (int q0 = 0; q0 < total; q0 += 32 * kLocBatch) {
+          int u[kLocBatch];
+#pragma unroll
+          for (int q = 0; q < kLocBatch; ++q) {
+            const int j = q0 + 32 * q + lane;
+            bool hi;
+            const int t = loc_find(ia, ib, ta, j < total ? j : total - 1, hi);
+            const long long s0 = __shfl_sync(kFull, b0, t), s1 = __shfl_sync(kFull, b1, t);
+            const int x0 = __shfl_sync(kFull, ia - d0, t), x1 = __shfl_sync(kFull, ib - d1, t);
+            const long long bj = hi ? s1 : s0;
+            const int ej = hi ? x1 : x0;
+            u[q] = j < total ? gload(a.idx + bj + (j - ej)) : -1;
+          }
+          // claim: compare-and-swap on the level with the target's offsets
+          // loaded alongside
+          unsigned long long ent[kLocBatch];
+#pragma unroll
+          for (int q = 0; q < kLocBatch; ++q) {
+            ent[q] = 0;
+            if (u[q] >= 0) {
+              const int old = atomicCAS(&a.level[u[q]], -1, next);
+              const long long ob = (long long)gload(a.off + u[q]);
+              const long long oe = (long long)gload(a.off + u[q] + 1);
+              if (old == -1) {
+                mrec += (unsigned long long)(oe - ob);
+                ent[q] = loc_pack(ob, oe - ob) | (1ull << 63);
+              }
+            }
+          }
+          // append the claims to this CTA's buffer: one shared atomic per
+          // warp and batch slot
+#pragma unroll
+          for (int q = 0; q < kLocBatch; ++q) {
+            const bool mine = (ent[q] >> 63) != 0;
+            const unsigned mk = __ballot_sync(kFull, mine);
+            if (mk == 0) continue;
+            const int leader = __ffs(mk) - 1;
+            unsigned base_q = 0;
+            if (lane == leader) base_q = atomicAdd(&ls.cnt[nx], (unsigned)__popc(mk));
+            base_q = __shfl_sync(kFull, base_q, leader);
+            if (mine) {
+              const unsigned pos = base_q + (unsigned)__popc(mk & lanemask_lt());
+              if (pos < (unsigned)kLocCap) ls.f[fc ^ 1][pos] = ent[q] & ~(1ull << 63);
+              else ls.ovf[nx] = 1;
+            }
+          }
+        }
+        evisit += d0 + d1;
       }
-      nrec = cta_sum_u64(nrec, sh);
-      mrec = cta_sum_u64(mrec, sh);
-      if (threadIdx.x == 0 && nrec) {
-        atomicAdd(&L0->ntot[nx], (unsigned)nrec);
-        atomicAdd(&L0->medges[nx], mrec);
-      }
+      mrec = warp_sum_u64(mrec);
+      if (lane == 0 && mrec) atomicAdd(&ls.medges[nx], mrec);
+      if (threadIdx.x == 0 && r == 0) ls.stop = ab;
+      const unsigned long long t_walk = globaltimer();
+      loc_publish(cl, ls, nx, r);
       cl.sync();
+      const unsigned long long t_bar = globaltimer();
       // the same values, so the same decisions, in every CTA of the cluster
-      const unsigned N = L0->ntot[nx], O = L0->ovf[nx], X = L0->stop[nx];
-      const unsigned long long M = L0->medges[nx];
+      unsigned long long M;
+      unsigned O, X, N1;
+      loc_counts(ls, nx, cc, cp, N1, M, O, X);
       trace_put(a.w, it, kPush | (kOnline << 8) | (1 << 19), (long long)n_f, (long long)m_f, L, t_it);
+      if (blockIdx.x == 0 && threadIdx.x == 0 && it < a.w.trace_cap) {
+        a.w.trace[(long long)kTraceWords * it + 6] = (long long)t_walk;  // CTA 0's walk done
+        a.w.trace[(long long)kTraceWords * it + 7] = (long long)t_bar;   // ... and the cluster barrier passed
+      }
+      N = N1;
       fsum += (long long)n_f;
       ++it;
       ++push_it;
@@ -489,7 +637,9 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       const bool to_pull = k.direction != 1 && (double)M > (double)m_u / k.alpha;
       if (O || X || N > kLocExitN || M > kLocEnterM || to_pull) break;
       cur = nx;
+      fc ^= 1;
     }
+    cl.sync();  // no CTA leaves while another still reads its shared memory
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       long long* w = s->loc;
       w[kLcL] = L; w[kLcNf] = (long long)n_f; w[kLcMf] = (long long)m_f; w[kLcPrevNf] = (long long)prev_n_f;
@@ -498,18 +648,23 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       red_release_add_u64(&s->loc_epoch, 1ull);
     }
   }
-  // every CTA: wait for the episode's hand-back (bounded), then take its state
+  // every CTA: wait for the episode's hand-back, then take its state; the
+  // wait is bounded by the barrier timeout without progress (a level done)
   if (threadIdx.x == 0) {
     int ok = 1;
     unsigned long long t0 = 0;
+    long long beat = -1;
     unsigned spins = 0;
     while (ld_acquire_u64(&s->loc_epoch) < episodes + 1) {
       __nanosleep(64);
       if ((++spins & 63u) == 0) {
         if (ld_volatile_i32(&s->abort)) { ok = 0; break; }
         const unsigned long long t = globaltimer();
-        if (t0 == 0) t0 = t;
-        else if (t - t0 > k.timeout_ns) {
+        const long long b = *(const volatile long long*)&s->loc[kLcBeat];
+        if (t0 == 0 || b != beat) {
+          t0 = t;
+          beat = b;
+        } else if (t - t0 > k.timeout_ns) {
           atomicExch(&s->abort, 1);
           atomicCAS(&s->err, 0, 4 /* SIMDX_EBARRIER_TIMEOUT */);
           ok = 0;
@@ -549,8 +704,8 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
   constexpr bool kHasPull = (DIRS & kPull) != 0;
   constexpr bool kSplit = DIRS != (kPush | kPull);  // runs may span several launches
   __shared__ CtaShared sh;
-  __shared__ PullShared ps;
-  __shared__ typename std::conditional<CLU, LocalShared, char>::type loc_sm;
+  __shared__ typename std::conditional<CLU, PullLocalShared, PullShared>::type pl_sm;
+  PullShared& ps = pull_part(pl_sm);
   const unsigned grid = gridDim.x;
   Sync* s = a.w.sync;
   const Knobs& k = a.k;
@@ -718,7 +873,7 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
       if (k.small && dir == kPush && k.direction != 2 && cnt[0] + cnt[1] + cnt[2] + cnt[3] <= kLocEnterN &&
           m_f <= kLocEnterM) {
         bool done = false;
-        if (!bfs_local(a, loc_sm, sh, cnt, lbuf, L, n_f, prev_n_f, m_f, m_u, it, push_it, online_it, fsum, evisit,
+        if (!bfs_local(a, pl_sm.loc, sh, cnt, lbuf, L, n_f, prev_n_f, m_f, m_u, it, push_it, online_it, fsum, evisit,
                        episodes, done))
           return;
         lists_ok = false;  // levels are in the level array: the ballot filter lists the frontier

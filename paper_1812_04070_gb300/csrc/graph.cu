@@ -235,7 +235,10 @@ int grid_for_cluster(const simdx_graph* g, const void* kernel, int cluster) {
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      if (cudaOccupancyMaxActiveClusters(&mc, kernel, &cfg) != cudaSuccess) mc = 0;
+      if (cluster > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        mc = 0;
+      else if (cudaOccupancyMaxActiveClusters(&mc, kernel, &cfg) != cudaSuccess)
+        mc = 0;
       max_clusters[kernel] = mc;
     }
   }

@@ -451,21 +451,30 @@ def test_bfs_small_frontier_cluster(gi, mode):
 
 
 def test_bfs_small_frontier_levels_and_multi_root():
-    """On a grid every level is small: the trace marks the cluster levels
-    (bit 19), and the statistics count every level; a multi-root BFS over a
-    block-diagonal pack gives each graph's levels."""
+    """On a grid every frontier is small: the trace marks the cluster levels
+    (bit 19) and the statistics count every level.  Every push level runs on
+    the cluster (the last levels turn to pull when the frontier's edges
+    outweigh the unvisited ones); push-only runs every level there.  A
+    multi-root BFS over a block-diagonal pack gives each graph's levels."""
     import torch
     from paper_1812_04070_gb300 import simdx_stats
     g = gg.grid(120, 90)
-    G = make(g, bits=64, small_frontier=1)
-    st = simdx_stats()
-    lev = G.bfs(0, stats=st).cpu().numpy()
-    torch.cuda.synchronize()
-    assert np.array_equal(lev, oracle.bfs(g.offsets, g.indices, 0))
-    assert st.iterations == 120 + 90 - 1 and st.status == 0
-    tr = G.trace()
-    assert sum((int(r[0]) >> 19) & 1 for r in tr) >= st.iterations - 2
-    G.close()
+    want = oracle.bfs(g.offsets, g.indices, 0)
+    for direction in (0, 1):
+        G = make(g, bits=64, small_frontier=1, direction=direction)
+        st = simdx_stats()
+        lev = G.bfs(0, stats=st).cpu().numpy()
+        torch.cuda.synchronize()
+        assert np.array_equal(lev, want)
+        assert st.iterations == 120 + 90 - 1 and st.status == 0
+        tr = G.trace()
+        kind = [int(r[0]) for r in tr]
+        assert all((x >> 19) & 1 for x in kind if x & 0xff == 1), direction  # every push level
+        if direction == 1:
+            assert len(kind) == st.iterations
+            # cluster levels: walk end, then barrier, within the level's span
+            assert all(r[4] <= r[6] <= r[7] <= r[5] for r in tr)
+        G.close()
     graphs, srcs = gg.multigraph_batch(count=12, n_lo=50, n_hi=2000, seed=9)
     packed, bases = gg.pack(graphs)
     roots = [int(x) for x in (srcs.astype(np.int64) + bases[:-1])]
@@ -474,3 +483,46 @@ def test_bfs_small_frontier_levels_and_multi_root():
     for i, x in enumerate(graphs):
         assert np.array_equal(lv[bases[i]:bases[i + 1]], oracle.bfs(x.offsets, x.indices, int(srcs[i]))), i
     P.close()
+
+
+def _layered(sizes, seed):
+    """A layered graph: each vertex of a layer joins one or two random
+    vertices of the layer before (so the BFS from vertex 0 has the layers as
+    its frontiers), plus a few edges inside layers."""
+    rng = np.random.default_rng(seed)
+    first = np.concatenate([[0], np.cumsum(sizes)])
+    src, dst = [], []
+    for i in range(1, len(sizes)):
+        v = np.arange(first[i], first[i + 1])
+        for _ in range(2):
+            src.append(v)
+            dst.append(rng.integers(first[i - 1], first[i], v.size))
+        if sizes[i] > 1:
+            src.append(rng.integers(first[i], first[i + 1], sizes[i] // 4))
+            dst.append(rng.integers(first[i], first[i + 1], sizes[i] // 4))
+    return gg.from_edges(int(first[-1]), np.concatenate(src), np.concatenate(dst), "layered")
+
+
+def test_bfs_small_frontier_wide_and_overflow():
+    """Frontiers of several thousand vertices (more than 32 tasks per warp of
+    the cluster: both halves of a lane's tasks), and a level in which one CTA
+    of the cluster claims more vertices than its buffer holds (a hub whose
+    1500 neighbours all fall to the CTA that walks it), which ends the
+    episode and resumes it on the grid."""
+    g = _layered([1, 40, 3500, 3900, 200, 3000, 64, 1], seed=5)
+    for direction in (0, 1):  # push-only walks every layer on the cluster
+        G = make(g, bits=64, small_frontier=1, direction=direction)
+        assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0)), direction
+        if direction == 1:
+            assert all((int(r[0]) >> 19) & 1 for r in G.trace())
+        G.close()
+    k = 1500
+    kids = 8 * np.arange(1, k + 1)
+    src = np.concatenate([np.zeros(k, np.int64), kids, kids + 1])
+    dst = np.concatenate([kids, kids + 1, kids + 2])
+    g = gg.from_edges(8 * k + 8, src, dst, "skewed")
+    for direction in (0, 1):
+        G = make(g, bits=32, small_frontier=1, direction=direction)
+        assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0)), direction
+        assert G.last_status() == 0
+        G.close()
