@@ -902,7 +902,7 @@ def run_ablation(args, rank, world, local):
             rows.append(row)
         res[a] = rows
         G.set_config(fusion=0, filter=0, pr_alpha=8.0, sssp_combine=0, delta=default_delta, direction=0,
-                     pr_row_cost=0, stage_edges=0, pr_recut=0, small_frontier=0)
+                     pr_row_cost=0, stage_edges=0, pr_recut=0, small_frontier=2)
     G.close()
     base = res[wl["algs"][0]][0]
     return {"metric": f"us per iteration ({wl['algs'][0]}, all fusion)", "value": base["us_per_iteration"],

@@ -186,9 +186,12 @@ typedef struct {
                                 thread-block cluster (16 CTAs, the frontier in distributed shared
                                 memory, a cluster barrier per level) while the other CTAs wait;
                                 the launch is then in clusters of 16 (a few CTAs fewer fit).
-                                0 = every level on the whole grid.  Trace records of such levels
-                                carry bit 19, with words 6 and 7 the times (ns) at which CTA 0
-                                finished its walk and passed the cluster barrier. */
+                                0 = every level on the whole grid.  2 [default] = 1 for graphs
+                                whose largest out-degree is at most 64 (meshes, grids, road
+                                networks: many small levels), else 0.  Trace records of such
+                                levels carry bit 19, with words 6 and 7 the SM clock cycles
+                                CTA 0 spent in its walk and in publishing its counters plus the
+                                cluster barrier. */
     int32_t reserved[5];
 } simdx_config;
 

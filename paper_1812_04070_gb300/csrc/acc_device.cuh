@@ -135,6 +135,21 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// Direction rules (Sec. 4.2): m > rest / alpha, decided by every thread of
+// every CTA once per iteration, in single precision and multiplied out
+// (double-precision division is slow on this part).  The decision only picks
+// a direction; the result of the run does not depend on it.
+__device__ __forceinline__ bool exceeds_share(unsigned long long m, long long rest, float alpha) {
+  return (float)m * alpha > (float)rest;
+}
+
+// The global timer as the trace needs it: read by the one thread that writes
+// the trace (thread 0 of CTA 0), 0 elsewhere.  A read of the global timer is
+// not free, and an iteration's critical path should not pay it in every
+// thread.
+__device__ __forceinline__ unsigned long long trace_clock() {
+  return (blockIdx.x == 0 && threadIdx.x == 0) ? globaltimer() : 0ull;
+}
 // Graph arrays are read-only for the whole kernel: non-coherent loads are safe
 // there (and only there; state written during the kernel uses plain loads).
 template <class T>
@@ -476,7 +491,7 @@ __device__ void bitmap_filter(int n, const uint32_t* bm, Deg deg, Visit visit, C
 struct ClassTimer {
   PhaseSlot* slot;
   unsigned long long t;
-  __device__ explicit ClassTimer(PhaseSlot* s) : slot(s), t(threadIdx.x == 0 ? globaltimer() : 0) {}
+  __device__ explicit ClassTimer(PhaseSlot* s) : slot(s), t(s && threadIdx.x == 0 ? globaltimer() : 0) {}
   __device__ __forceinline__ void lap(int c) {
     if (slot && threadIdx.x == 0) {
       const unsigned long long now = globaltimer();
@@ -1169,12 +1184,12 @@ __device__ void det_filter_write(int n, Pred pred, Cls cls_of, CtaShared& sh, co
 // active edges, level / bucket, and %globaltimer at the iteration's start and
 // end as seen by CTA 0.
 __device__ __forceinline__ void trace_put(const Work& w, int it, long long a, long long b, long long c,
-                                          long long d, unsigned long long t0 = 0) {
+                                          long long d, unsigned long long t0 = 0, unsigned long long t1 = 0) {
   if (blockIdx.x == 0 && threadIdx.x == 0 && it < w.trace_cap) {
     long long* r = w.trace + (long long)kTraceWords * it;
     r[0] = a; r[1] = b; r[2] = c; r[3] = d;
     r[4] = (long long)t0;
-    r[5] = (long long)globaltimer();
+    r[5] = (long long)(t1 ? t1 : globaltimer());
     r[6] = 0; r[7] = 0;
   }
 }

@@ -40,6 +40,7 @@ std::vector<Knob> knobs_for(int algo) {
   k.push_back({"huge_min", {1024, 2048, 4096, 8192, 16384}, SIMDX_KNOB_I(huge_min)});
   k.push_back({"bin_per_thread", {16, 32, 64, 128}, SIMDX_KNOB_I(bin_per_thread)});
   if (algo == SIMDX_ALGO_BFS) {
+    k.push_back({"small_frontier", {0, 1}, SIMDX_KNOB_I(small_frontier)});
     k.push_back({"alpha", {4, 7, 14, 28, 56}, SIMDX_KNOB_I(alpha)});
     k.push_back({"beta", {6, 12, 24, 48, 96}, SIMDX_KNOB_I(beta)});
   } else if (algo == SIMDX_ALGO_SSSP) {

@@ -510,9 +510,10 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
     // counter slots rotate over three (the one after next is cleared during
     // a level), entry buffers over two
     int cur = 0, fc = 0;
+    unsigned long long t_it = trace_clock();  // a level's start: the previous level's end
     while (true) {
       const int nx = cur == 2 ? 0 : cur + 1, nn = nx == 2 ? 0 : nx + 1;
-      const unsigned long long t_it = globaltimer();
+      const long long c_it = clock64();
       unsigned ab = 0;
       if (threadIdx.x == 0) {
         ls.cnt[nn] = 0;  // slot nn was last read before the previous barrier
@@ -607,19 +608,21 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       mrec = warp_sum_u64(mrec);
       if (lane == 0 && mrec) atomicAdd(&ls.medges[nx], mrec);
       if (threadIdx.x == 0 && r == 0) ls.stop = ab;
-      const unsigned long long t_walk = globaltimer();
+      const long long c_walk = clock64();
       loc_publish(cl, ls, nx, r);
       cl.sync();
-      const unsigned long long t_bar = globaltimer();
+      const long long c_bar = clock64();
       // the same values, so the same decisions, in every CTA of the cluster
       unsigned long long M;
       unsigned O, X, N1;
       loc_counts(ls, nx, cc, cp, N1, M, O, X);
-      trace_put(a.w, it, kPush | (kOnline << 8) | (1 << 19), (long long)n_f, (long long)m_f, L, t_it);
+      const unsigned long long t_end = trace_clock();
+      trace_put(a.w, it, kPush | (kOnline << 8) | (1 << 19), (long long)n_f, (long long)m_f, L, t_it, t_end);
       if (blockIdx.x == 0 && threadIdx.x == 0 && it < a.w.trace_cap) {
-        a.w.trace[(long long)kTraceWords * it + 6] = (long long)t_walk;  // CTA 0's walk done
-        a.w.trace[(long long)kTraceWords * it + 7] = (long long)t_bar;   // ... and the cluster barrier passed
+        a.w.trace[(long long)kTraceWords * it + 6] = c_walk - c_it;  // CTA 0's walk (SM clock cycles)
+        a.w.trace[(long long)kTraceWords * it + 7] = c_bar - c_walk;  // ... its counters and the barrier
       }
+      t_it = t_end;
       N = N1;
       fsum += (long long)n_f;
       ++it;
@@ -634,7 +637,7 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
         done = true;
         break;
       }
-      const bool to_pull = k.direction != 1 && (double)M > (double)m_u / k.alpha;
+      const bool to_pull = k.direction != 1 && exceeds_share(M, m_u, k.alpha);
       if (O || X || N > kLocExitN || M > kLocEnterM || to_pull) break;
       cur = nx;
       fc ^= 1;
@@ -803,8 +806,8 @@ __global__ void __launch_bounds__(kThreads, 4) bfs_kernel(BfsArgs<OffT> a) {
     int dir;
     if (k.direction == 1) dir = kPush;
     else if (k.direction == 2) dir = kPull;
-    else if (prev_dir == kPush) dir = ((double)m_f > (double)m_u / k.alpha) ? kPull : kPush;
-    else dir = ((double)n_f < (double)n / k.beta && n_f <= prev_n_f) ? kPush : kPull;
+    else if (prev_dir == kPush) dir = exceeds_share(m_f, m_u, k.alpha) ? kPull : kPush;
+    else dir = ((float)n_f * k.beta < (float)n && n_f <= prev_n_f) ? kPush : kPull;  // n_f < n / beta
     int filt = kOnline;
 
     // -------- selective / no fusion: leave the loop state to the next launch

@@ -87,6 +87,10 @@ int cuda_status(cudaError_t e, const char* what) {
   return SIMDX_ECUDA;
 }
 
+// small_frontier = 2 turns the cluster levels on for graphs whose largest
+// out-degree is at most this.
+constexpr long long kSmallAutoMaxDeg = 64;
+
 Knobs make_knobs(const simdx_graph* g) {
   const simdx_config& c = g->cfg;
   Knobs k{};
@@ -105,7 +109,11 @@ Knobs make_knobs(const simdx_graph* g) {
   k.skip_phase = c.debug_skip_phase;
   k.fusion = c.fusion;
   k.stage = c.stage_edges;
-  k.small = c.small_frontier;
+  // small frontiers on one cluster: on, or (2) on for graphs without hubs,
+  // whose BFS levels are many and small (meshes, grids, road networks); a
+  // graph with hubs has few levels, and the launch in clusters costs its
+  // large levels a few CTAs
+  k.small = c.small_frontier == 1 || (c.small_frontier == 2 && g->max_deg <= kSmallAutoMaxDeg);
   return k;
 }
 
@@ -396,6 +404,7 @@ void simdx_config_default(simdx_config* c) {
   c->pr_alpha = 8.f;
   c->pr_theta = 2.f;
   c->pr_rho = 0.6f;
+  c->small_frontier = 2;
 }
 
 int64_t simdx_eq1_ctas(int64_t regs_per_sm, int64_t regs_per_thread, int64_t threads_per_cta,
@@ -543,6 +552,7 @@ int simdx_graph_create(const simdx_csr* csr, const simdx_csr* csc, const uint32_
     unsigned long long key = 0;
     std::memcpy(&key, h_bad + 2, sizeof(key));
     g->hub = key ? (int32_t)(0xffffffffull - (key & 0xffffffffull)) : 0;
+    g->max_deg = (long long)(key >> 32);
   }
   const unsigned wmax = static_cast<unsigned>(h_bad[1]);
   if (wmax) g->cfg.delta = wmax >= (1u << 26) ? (1u << 30) : 16u * wmax;
@@ -637,7 +647,7 @@ int simdx_graph_set_config(simdx_graph* g, const simdx_config* cfg) {
       (cfg->sssp_batch_width != 0 && cfg->sssp_batch_width != 8 && cfg->sssp_batch_width != 16 &&
        cfg->sssp_batch_width != 32 && cfg->sssp_batch_width != 64) || cfg->pr_row_cost < 0 ||
       cfg->pr_row_cost > 4096 || cfg->stage_edges < 0 || cfg->stage_edges > 1 || cfg->pr_recut < 0 ||
-      cfg->small_frontier < 0 || cfg->small_frontier > 1)
+      cfg->small_frontier < 0 || cfg->small_frontier > 2)
     return SIMDX_EINVAL;
   bool realloc_ws = cfg->bin_per_thread != g->cfg.bin_per_thread || cfg->ctas_per_sm != g->cfg.ctas_per_sm ||
                     cfg->huge_min != g->cfg.huge_min;

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
     int dir;
     if (k.direction == 1) dir = 1;
     else if (k.direction == 2) dir = 2;
-    else dir = ((double)m_f > (double)m_alive / k.kalpha) ? 2 : 1;
+    else dir = exceeds_share(m_f, (long long)m_alive, k.kalpha) ? 2 : 1;
     int filt = 1;
     if (dir == 1 && (!lists_ok || k.filter == 2)) {
       // rebuild the frontier lists from the metadata

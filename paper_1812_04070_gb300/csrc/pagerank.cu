@@ -454,13 +454,14 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_push_kernel(const __grid
   double l1p = l1_last;     // L1 of the previous scan
   bool none = false;        // the previous scan selected no vertex
   const OffT* off = a.off;
+  const double inv_n = 1.0 / (double)n;  // per-iteration scalars multiply (FP64 division is slow here)
   while (true) {
     const unsigned long long t_it = globaltimer();
     // ---- scan: add G, sum |r|, select |r| > eps and claim
     clear_next_slot(s, sh);
     PhaseSlot& slot = s->slot[slot_of(sh.phase)];
     const unsigned long long eps_fix =
-        none ? 0ull : (unsigned long long)((double)a.theta * l1p / (double)n * kFix);
+        none ? 0ull : (unsigned long long)((double)a.theta * l1p * inv_n * kFix);
     unsigned long long l1acc = 0, dang = 0;
     const long long GG = G;
     auto pred = [&](int v) {
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_push_kernel(const __grid
     }
     if (!grid_sync(s, grid, sh, k)) return;
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
-    const double l1 = (double)p.aux1 / kFix;
+    const double l1 = (double)p.aux1 * kUnfix;  // exact: kUnfix = 1 / kFix, a power of two
     unsigned cnt[kClasses];
     for (int c = 0; c < kClasses; ++c) cnt[c] = p.list_cnt[c];
     const unsigned sel = cnt[0] + cnt[1] + cnt[2] + cnt[3];
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_push_kernel(const __grid
       trace_put(a.w, t, 1 | (2 << 8), sel, 0, (long long)p.aux1, t_it);
       break;
     }
-    const long long Gn = llrint((double)a.d * (double)(long long)p.aux0 / (double)n);
+    const long long Gn = llrint((double)a.d * (double)(long long)p.aux0 * inv_n);
     // ---- push the selected vertices' changes along their out-edges
     clear_next_slot(s, sh);
     {
@@ -836,7 +837,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_kernel(const __grid_cons
     const PhaseSlot& p = s->slot[slot_of(sh.phase - 1)];
     Dfix = p.aux0;
     const double l1_prev = l1_last;
-    l1_last = (double)p.aux1 / kFix;
+    l1_last = (double)p.aux1 * kUnfix;  // exact: a power of two
     trace_put(a.w, t, 2 | (2 << 8), n, a.e, (long long)p.aux1, t_it);
     trace_classes(a.w, t, p);
     ++t;

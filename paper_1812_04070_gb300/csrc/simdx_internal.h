@@ -36,6 +36,7 @@ struct simdx_graph {
   int32_t* in_idx = nullptr;
   uint32_t* w = nullptr;
   int32_t hub = 0;           // a vertex of largest degree (smallest id among them)
+  long long max_deg = 0;     // its out-degree
   // knobs
   simdx_config cfg{};
   // workspace

@@ -74,7 +74,7 @@ def test_config_layout_matches_header(lib):
     assert ctypes.sizeof(simdx.simdx_config) == 4 * words
     c = simdx.simdx_config_default()
     assert c.batch_group == 0 and c.fusion == 0 and c.sssp_combine == 0 and c.sssp_batch_width == 0
-    assert c.pr_row_cost == 0 and c.stage_edges == 0 and c.pr_recut == 0 and c.small_frontier == 0
+    assert c.pr_row_cost == 0 and c.stage_edges == 0 and c.pr_recut == 0 and c.small_frontier == 2
     assert list(c.reserved) == [0] * 5
     assert (c.pr_alpha, c.pr_theta, c.pr_rho) == (8.0, 2.0, pytest.approx(0.6))
 

@@ -472,8 +472,8 @@ def test_bfs_small_frontier_levels_and_multi_root():
         assert all((x >> 19) & 1 for x in kind if x & 0xff == 1), direction  # every push level
         if direction == 1:
             assert len(kind) == st.iterations
-            # cluster levels: walk end, then barrier, within the level's span
-            assert all(r[4] <= r[6] <= r[7] <= r[5] for r in tr)
+            # cluster levels: start <= end; walk and barrier cycles recorded
+            assert all(r[4] <= r[5] and r[6] > 0 and r[7] > 0 for r in tr)
         G.close()
     graphs, srcs = gg.multigraph_batch(count=12, n_lo=50, n_hi=2000, seed=9)
     packed, bases = gg.pack(graphs)
