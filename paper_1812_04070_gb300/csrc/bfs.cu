@@ -21,14 +21,13 @@
 //               on overflow (or when forced) the ballot filter rebuilds
 //               sorted, unique lists from the level array or the frontier
 //               bitmap (Sec. 4, JIT control).
-#include <cooperative_groups.h>
 
 #include <cstring>
 #include <type_traits>
 
+#include "acc_cluster.cuh"
 #include "simdx_internal.h"
 
-namespace cg = cooperative_groups;
 
 namespace simdx {
 
@@ -330,50 +329,13 @@ __device__ void bfs_pull_big(const BfsArgs<OffT>& a, int cur, const uint32_t* fb
 }
 
 // ------------------------------------------------ small frontiers
-// A push level with a small frontier costs a grid barrier and a chain of
-// dependent global round trips whatever its size (about 10 us on GB300).
-// While the frontier stays small, the levels run on the first thread-block
-// cluster alone, with a cluster barrier per level; the other CTAs wait on a
-// flag (bounded like the grid barrier).  Each CTA of the cluster appends the
-// vertices it claims to its own shared memory (one shared atomic per warp
-// and batch slot); before the barrier it stores its counters into every
-// CTA's shared memory, so after it all CTAs read the same totals locally and
-// take the same decisions.  CTA r walks the r-th sixteenth of the
-// concatenated buffers, reading the entries from distributed shared memory.
-// No remote atomics, no contended counters.  The episode hands the loop
-// state back through the barrier block; levels are in the level array, so
-// the grid rebuilds its lists by the ballot filter.
-//
-// A frontier entry is the vertex's edge range, packed as (beg << 24) | deg:
-// the claim of a vertex loads its offsets together with the compare-and-swap
-// on its level, so a level is two dependent global round trips (edge
-// targets; claim + offsets) plus the cluster barrier.  Degrees of a walked
-// frontier are at most kLocEnterM (a larger one ends the episode before its
-// level), and beg < 2^39 for any graph that fits in device memory (bit 63
-// marks a claim while the entry is in registers).
-constexpr int kCluster = 16;                        // CTAs of the cluster (a non-portable size)
-constexpr int kLocCap = 512;                        // entries a CTA can claim in one level
-constexpr unsigned kLocEnterN = 4096;               // enter at most this many frontier vertices
-constexpr unsigned long long kLocEnterM = 65536;    // ... and frontier edges
-constexpr unsigned kLocExitN = 6144;                // leave when the next frontier holds more
-constexpr int kLocBatch = 4;                        // edges per lane in flight
-constexpr unsigned long long kLocDegMask = (1ull << 24) - 1;
-static_assert(kCluster <= 32 && (kCluster & (kCluster - 1)) == 0, "one lane per CTA of the cluster");
-
-struct LocCounters {
-  unsigned long long medges;  // out-edges of the CTA's claims
-  unsigned cnt;               // the CTA's claims
-  unsigned flags;             // bit 0: it claimed more than kLocCap; bit 1 (rank 0): the run aborted
-};
-
-struct LocalShared {
-  unsigned long long f[2][kLocCap];  // entries this CTA claimed: the current and the next frontier
-  unsigned cnt[3];                   // claims of this CTA in a level (counter slots rotate over three)
-  unsigned ovf[3];                   // this CTA claimed more than kLocCap
-  unsigned stop;                     // rank 0: the run aborted (read before the barrier)
-  unsigned long long medges[3];      // out-edges of this CTA's claims
-  LocCounters all[3][kCluster];      // every CTA's counters of a level, stored here by that CTA
-};
+// While a push frontier is small (at most kLocEnterN vertices and kLocEnterM
+// edges), the levels run on the first thread-block cluster (acc_cluster.cuh):
+// a level is two dependent global round trips (edge targets; the claim's
+// compare-and-swap with the target's offsets loaded alongside) plus the
+// cluster barrier, where the grid pays a grid barrier and its filter.  The
+// episode hands the loop state back through the barrier block; levels are
+// in the level array, so the grid rebuilds its lists by the ballot filter.
 
 // The pull levels' and the cluster levels' shared memory never live at once
 // (a grid barrier or the episode's closing cluster barrier lies between).
@@ -385,85 +347,6 @@ __device__ __forceinline__ PullShared& pull_part(PullShared& x) { return x; }
 __device__ __forceinline__ PullShared& pull_part(PullLocalShared& x) { return x.ps; }
 
 enum { kLcL, kLcNf, kLcMf, kLcPrevNf, kLcMu, kLcIt, kLcPushIt, kLcOnlineIt, kLcFsum, kLcDone, kLcBeat = 15 };
-
-__device__ __forceinline__ unsigned long long loc_pack(long long beg, long long deg) {
-  return ((unsigned long long)beg << 24) | (unsigned long long)(deg < (long long)kLocDegMask ? deg : kLocDegMask);
-}
-
-// The edge j (0 <= j < total) of a warp's group of up to 64 tasks: lane t
-// holds tasks t and t + 32 with inclusive edge prefixes ia, ib (ib counts on
-// from the first half's total ta).  Returns the task's lane and half.  Every
-// lane reads both prefixes of the lane it probes and keeps the one of its
-// own half (a lane's half depends on its own j).
-__device__ __forceinline__ int loc_find(int ia, int ib, int ta, int j, bool& hi) {
-  hi = j >= ta;
-  int t = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const int xa = __shfl_sync(kFull, ia, t + step - 1);
-    const int xb = __shfl_sync(kFull, ib, t + step - 1);
-    if ((hi ? xb : xa) <= j) t += step;
-  }
-  return t;
-}
-
-// The CTA (lane of the warp) that holds entry g of the concatenated buffers:
-// lanes 0..kCluster-1 hold the exclusive prefix p of the CTAs' counts (lanes
-// beyond hold ~0u).
-__device__ __forceinline__ int loc_owner(unsigned p, unsigned g) {
-  int t = 0;
-#pragma unroll
-  for (int step = kCluster / 2; step >= 1; step >>= 1) {
-    const unsigned x = __shfl_sync(kFull, p, t + step);
-    if (x <= g) t += step;
-  }
-  return t;
-}
-
-// Before a cluster barrier: this CTA's counters of slot `sl` go to every
-// CTA of the cluster (thread c stores to CTA c), so that after the barrier
-// they are read locally.  The CTA's appends are complete (__syncthreads).
-__device__ __forceinline__ void loc_publish(cg::cluster_group& cl, LocalShared& ls, int sl, unsigned r) {
-  __syncthreads();
-  if (threadIdx.x < kCluster) {
-    LocCounters c;
-    c.medges = ls.medges[sl];
-    c.cnt = ls.cnt[sl];
-    c.flags = (ls.ovf[sl] ? 1u : 0u) | (r == 0 && ls.stop ? 2u : 0u);
-    cl.map_shared_rank(&ls, threadIdx.x)->all[sl][r] = c;
-  }
-}
-
-// After a cluster barrier: every warp reads counter slot `sl` of all CTAs
-// (lane c, CTA c's copy in this CTA's shared memory).  Returns the lane's
-// count and exclusive prefix (for lanes below kCluster) and the cluster's
-// totals.
-__device__ __forceinline__ void loc_counts(LocalShared& ls, int sl, unsigned& c, unsigned& p, unsigned& n,
-                                           unsigned long long& m, unsigned& o, unsigned& x) {
-  const int lane = lane_id();
-  c = 0;
-  unsigned long long me = 0;
-  o = 0;
-  x = 0;
-  if (lane < kCluster) {
-    const LocCounters& r = ls.all[sl][lane];
-    c = r.cnt;
-    me = r.medges;
-    o = r.flags & 1u;
-    x = r.flags & 2u;
-  }
-  unsigned incl = c;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const unsigned y = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += y;
-  }
-  n = __shfl_sync(kFull, incl, 31);
-  p = lane < kCluster ? incl - c : ~0u;
-  m = warp_sum_u64(me);
-  o = __any_sync(kFull, o != 0) ? 1u : 0u;
-  x = __any_sync(kFull, x != 0) ? 1u : 0u;
-}
 
 // One episode of small-frontier levels (every CTA calls it; cluster 0 works,
 // the rest wait).  The current frontier is the class lists (at most
@@ -479,11 +362,7 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
     cg::cluster_group cl = cg::this_cluster();
     const unsigned r = cl.block_rank();
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    if (threadIdx.x < 3) {
-      ls.cnt[threadIdx.x] = 0;
-      ls.ovf[threadIdx.x] = 0;
-      ls.medges[threadIdx.x] = 0;
-    }
+    if (threadIdx.x < 3) loc_clear(ls, threadIdx.x);
     if (threadIdx.x == 0) ls.stop = 0;
     __syncthreads();
     // the current frontier: the entries j of the class lists (in class
@@ -501,12 +380,8 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
     }
     loc_publish(cl, ls, 0, r);
     cl.sync();
-    unsigned cc, cp, N;  // this lane's CTA count and prefix; frontier size
-    {
-      unsigned long long M0;
-      unsigned O0, X0;
-      loc_counts(ls, 0, cc, cp, N, M0, O0, X0);
-    }
+    unsigned cc, cp, zc, zp;  // this lane's CTA count and prefix
+    unsigned N = loc_counts(ls, 0, cc, cp, zc, zp).n;
     // counter slots rotate over three (the one after next is cleared during
     // a level), entry buffers over two
     int cur = 0, fc = 0;
@@ -516,9 +391,7 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       const long long c_it = clock64();
       unsigned ab = 0;
       if (threadIdx.x == 0) {
-        ls.cnt[nn] = 0;  // slot nn was last read before the previous barrier
-        ls.ovf[nn] = 0;
-        ls.medges[nn] = 0;
+        loc_clear(ls, nn);  // slot nn was last read before the previous barrier
         if (r == 0) {
           ab = (unsigned)ld_volatile_i32(&s->abort);  // stored at the end of the level
           if (blockIdx.x == 0) *(volatile long long*)&s->loc[kLcBeat] = L;  // progress for the waiting CTAs
@@ -529,8 +402,6 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       const unsigned myc = (unsigned)(((unsigned long long)N * (r + 1)) / kCluster) - lo;
       const int next = L + 1;
       unsigned long long mrec = 0;
-      // groups of up to 64 tasks per warp (two per lane); the warp walks
-      // their concatenated edges, kLocBatch rounds of 32 at a time
       unsigned gs = (myc + kWarps - 1) / kWarps;
       gs = gs < 1 ? 1 : (gs > 64 ? 64 : gs);
       for (unsigned b = (unsigned)warp * gs; b < myc; b += (unsigned)kWarps * gs) {
@@ -581,27 +452,12 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
               const long long oe = (long long)gload(a.off + u[q] + 1);
               if (old == -1) {
                 mrec += (unsigned long long)(oe - ob);
-                ent[q] = loc_pack(ob, oe - ob) | (1ull << 63);
+                ent[q] = loc_pack(ob, oe - ob) | kLocClaim;
               }
             }
           }
-          // append the claims to this CTA's buffer: one shared atomic per
-          // warp and batch slot
 #pragma unroll
-          for (int q = 0; q < kLocBatch; ++q) {
-            const bool mine = (ent[q] >> 63) != 0;
-            const unsigned mk = __ballot_sync(kFull, mine);
-            if (mk == 0) continue;
-            const int leader = __ffs(mk) - 1;
-            unsigned base_q = 0;
-            if (lane == leader) base_q = atomicAdd(&ls.cnt[nx], (unsigned)__popc(mk));
-            base_q = __shfl_sync(kFull, base_q, leader);
-            if (mine) {
-              const unsigned pos = base_q + (unsigned)__popc(mk & lanemask_lt());
-              if (pos < (unsigned)kLocCap) ls.f[fc ^ 1][pos] = ent[q] & ~(1ull << 63);
-              else ls.ovf[nx] = 1;
-            }
-          }
+          for (int q = 0; q < kLocBatch; ++q) loc_append1(ls, fc ^ 1, nx, ent[q]);
         }
         evisit += d0 + d1;
       }
@@ -613,9 +469,7 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       cl.sync();
       const long long c_bar = clock64();
       // the same values, so the same decisions, in every CTA of the cluster
-      unsigned long long M;
-      unsigned O, X, N1;
-      loc_counts(ls, nx, cc, cp, N1, M, O, X);
+      const LocTotals T = loc_counts(ls, nx, cc, cp, zc, zp);
       const unsigned long long t_end = trace_clock();
       trace_put(a.w, it, kPush | (kOnline << 8) | (1 << 19), (long long)n_f, (long long)m_f, L, t_it, t_end);
       if (blockIdx.x == 0 && threadIdx.x == 0 && it < a.w.trace_cap) {
@@ -623,22 +477,22 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
         a.w.trace[(long long)kTraceWords * it + 7] = c_bar - c_walk;  // ... its counters and the barrier
       }
       t_it = t_end;
-      N = N1;
+      N = T.n;
       fsum += (long long)n_f;
       ++it;
       ++push_it;
       ++online_it;
       prev_n_f = n_f;
-      n_f = N;
-      m_f = M;
-      m_u -= (long long)M;
+      n_f = N;  // one entry per vertex
+      m_f = T.m;
+      m_u -= (long long)T.m;
       ++L;
       if (N == 0) {
         done = true;
         break;
       }
-      const bool to_pull = k.direction != 1 && exceeds_share(M, m_u, k.alpha);
-      if (O || X || N > kLocExitN || M > kLocEnterM || to_pull) break;
+      const bool to_pull = k.direction != 1 && exceeds_share(T.m, m_u, k.alpha);
+      if (T.ovf || T.stop || N > kLocExitN || T.m > kLocEnterM || to_pull) break;
       cur = nx;
       fc ^= 1;
     }
@@ -651,34 +505,8 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       red_release_add_u64(&s->loc_epoch, 1ull);
     }
   }
-  // every CTA: wait for the episode's hand-back, then take its state; the
-  // wait is bounded by the barrier timeout without progress (a level done)
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned long long t0 = 0;
-    long long beat = -1;
-    unsigned spins = 0;
-    while (ld_acquire_u64(&s->loc_epoch) < episodes + 1) {
-      __nanosleep(64);
-      if ((++spins & 63u) == 0) {
-        if (ld_volatile_i32(&s->abort)) { ok = 0; break; }
-        const unsigned long long t = globaltimer();
-        const long long b = *(const volatile long long*)&s->loc[kLcBeat];
-        if (t0 == 0 || b != beat) {
-          t0 = t;
-          beat = b;
-        } else if (t - t0 > k.timeout_ns) {
-          atomicExch(&s->abort, 1);
-          atomicCAS(&s->err, 0, 4 /* SIMDX_EBARRIER_TIMEOUT */);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    sh.ok = ok;
-  }
-  __syncthreads();
-  if (!sh.ok) return false;
+  // every CTA: wait for the episode's hand-back, then take its state
+  if (!loc_wait_handback(s, k, sh, &s->loc_epoch, &s->loc[kLcBeat], episodes)) return false;
   ++episodes;
   const volatile long long* w = s->loc;
   L = (int)w[kLcL]; n_f = (unsigned long long)w[kLcNf]; m_f = (unsigned long long)w[kLcMf];

@@ -17,7 +17,9 @@
 // once they become few, the order Sec. 5 gives for k-core; the switch
 // compares the frontier's edges with the alive vertices' edges.
 #include <climits>
+#include <type_traits>
 
+#include "acc_cluster.cuh"
 #include "simdx_internal.h"
 
 namespace simdx {
@@ -363,7 +365,7 @@ __device__ void core_scan(long long count, const int32_t* dom, int32_t* keep, un
                           int32_t* removed_at, const uint32_t* cnt, uint32_t* core, const OffT* off,
                           const Work& w, const Knobs& k, unsigned grid, int nbuf, PhaseSlot& slot,
                           int (&cw)[kCoreCats][kWarps], int (&cb)[kCoreCats], unsigned long long& nalive,
-                          unsigned long long& ndel, unsigned long long& mymin) {
+                          unsigned long long& ndel, unsigned long long& mymin, unsigned long long& mdel) {
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const int J = ballot_steps(count, grid);
   const long long csz = (long long)kThreads * J;
@@ -386,6 +388,7 @@ __device__ void core_scan(long long count, const int32_t* dom, int32_t* keep, un
             core[v] = kt;
             ++ndel;
             const long long d = (long long)gload(off + v + 1) - (long long)gload(off + v);
+            mdel += (unsigned long long)d;
             if (d > 0) cat = degree_class(d, k);
           }
         }
@@ -440,9 +443,346 @@ __device__ void core_scan(long long count, const int32_t* dom, int32_t* keep, un
   }
 }
 
+// ------------------------------------------------ small frontiers
+// Most peeling steps of a power-law graph delete a handful of vertices, and
+// most levels scan a small remaining domain; each would cost a grid barrier
+// and a chain of global round trips.  While a push frontier is small, or the
+// domain holds at most kCoreLocDom vertices, the steps run on the first
+// thread-block cluster (acc_cluster.cuh).  A push step decrements each
+// neighbour's residual degree (atomicSub, the target's offsets loaded
+// alongside; the decrement that takes it from K + 1 to K deletes it, the
+// same unique transition as the grid's push).  A scan step splits the domain
+// into one segment per CTA; each CTA compacts its kept vertices into its own
+// segment of the other domain buffer, so no CTA waits on another's order.
+// The episode hands back when the frontier grows (lists rebuilt by the
+// ballot filter from removed_at), compacting the segments into one domain,
+// or when a level ends with a domain too large to scan here.
+constexpr long long kCoreLocDom = 65536;  // scan the domain here when it holds at most this many
+constexpr int kScanPer = 4;              // domain vertices per thread in flight
+
+enum { kCcK, kCcPending, kCcMpend, kCcDomSel, kCcDcount, kCcDsel, kCcIt, kCcBallotIt, kCcOnlineIt, kCcFsum,
+       kCcDone, kCcBeat = 15 };
+
 template <class OffT>
-__global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a) {
+__device__ bool core_local(const CoreArgs<OffT>& a, LocalShared& ls, CtaShared& sh, int32_t* removed_at,
+                           uint32_t* cnt, int32_t* const (&doms)[2], const unsigned* cnt_l, int lbuf, long long& K,
+                           unsigned long long& pending, unsigned long long& m_pend, const int32_t*& dom,
+                           long long& dcount, int& dsel, int& it, int& ballot_it, int& online_it, long long& fsum,
+                           long long& evisit, unsigned long long& episodes, bool& done) {
+  Sync* s = a.w.sync;
+  const Knobs& k = a.k;
+  const OffT* off = a.off;
+  if (blockIdx.x < kCluster) {
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned r = cl.block_rank();
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    if (threadIdx.x < 3) loc_clear(ls, threadIdx.x);
+    if (threadIdx.x == 0) ls.stop = 0;
+    __syncthreads();
+    // the entry frontier: the class lists' entries j with j % kCluster == r
+    if (pending > 0) {
+      unsigned base = 0;
+      for (int c = 0; c < kClasses; ++c) {
+        const int32_t* list = a.w.list[lbuf][c];
+        for (unsigned i = threadIdx.x; i < cnt_l[c]; i += kThreads)
+          if ((base + i) % kCluster == r) {
+            const int v = list[i];
+            const long long b0 = (long long)gload(off + v);
+            loc_put(ls, 0, 0, b0, (long long)gload(off + v + 1) - b0);
+          }
+        base += cnt_l[c];
+      }
+    }
+    loc_publish(cl, ls, 0, r);
+    cl.sync();
+    unsigned cc, cp, zc, zp;
+    unsigned N = loc_counts(ls, 0, cc, cp, zc, zp).n;
+    // the domain: this CTA's segment [seg_lo, seg_lo + seg_n) of src (the
+    // identity when src is null), compacted into the other buffer
+    const long long seg_lo = dcount * (long long)r / kCluster;
+    long long seg_n = dcount * (long long)(r + 1) / kCluster - seg_lo;
+    const int32_t* src = dom;
+    int wsel = dsel;         // the buffer the next scan writes
+    bool segmented = false;  // the domain lives in per-CTA segments
+    long long seg_pre = 0;   // this CTA's segment's place in a compacted domain
+    long long dtotal = dcount;
+    unsigned long long m_cur = m_pend;
+    bool first_push = false;  // the push right after a scan lists by ballot in the grid's count
+    int cur = 0, fc = 0;
+    unsigned long long Kt = (unsigned long long)(K + 1);
+    int attempt = 0;  // scans of this level that deleted nothing (jumps)
+    long long steps = 0;
+    long long c_scans = 0;  // SM clock cycles of scans since the last push
+    bool handback = false;
+    unsigned long long t_it = trace_clock();
+    while (true) {
+      const int nx = cur == 2 ? 0 : cur + 1, nn = nx == 2 ? 0 : nx + 1;
+      unsigned ab = 0;
+      if (threadIdx.x == 0) {
+        loc_clear(ls, nn);
+        if (r == 0) {
+          ab = (unsigned)ld_volatile_i32(&s->abort);
+          if (blockIdx.x == 0) *(volatile long long*)&s->loc[kCcBeat] = ++steps;  // progress for the waiting CTAs
+        }
+      }
+      const bool scan = N == 0;
+      const long long c0 = clock64();
+      unsigned long long mrec = 0;
+      if (scan) {
+        // ---- scan the segment at level Kt: gone, deleted now (core = Kt,
+        // removed_at = it - 1, listed if it has edges), or kept
+        int32_t* dst = doms[wsel];
+        unsigned long long nalive = 0, ndel = 0, mymin = ~0ull;
+        for (long long i0 = 0; i0 < seg_n; i0 += (long long)kThreads * kScanPer) {
+          int v[kScanPer], ra[kScanPer];
+          unsigned c[kScanPer];
+          long long b0[kScanPer], e0[kScanPer];
+#pragma unroll
+          for (int q = 0; q < kScanPer; ++q) {
+            const long long i = i0 + (long long)q * kThreads + threadIdx.x;
+            v[q] = -1;
+            if (i < seg_n) v[q] = src ? src[seg_lo + i] : (int)(seg_lo + i);
+          }
+#pragma unroll
+          for (int q = 0; q < kScanPer; ++q) {
+            ra[q] = 0;
+            c[q] = 0u;
+            b0[q] = e0[q] = 0;
+            if (v[q] >= 0) {
+              // read at L2: other CTAs' pushes wrote these since this SM may
+              // have cached them (a cluster barrier does not refresh L1)
+              ra[q] = __ldcg(removed_at + v[q]);
+              c[q] = __ldcg(cnt + v[q]);
+              b0[q] = (long long)gload(off + v[q]);
+              e0[q] = (long long)gload(off + v[q] + 1);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kScanPer; ++q) {
+            const bool alive = v[q] >= 0 && ra[q] == INT_MAX;
+            const bool del = alive && c[q] <= (unsigned)Kt;
+            if (alive) {
+              ++nalive;
+              if (c[q] < mymin) mymin = c[q];
+            }
+            if (del) {
+              removed_at[v[q]] = it - 1;
+              a.core[v[q]] = (uint32_t)Kt;
+              ++ndel;
+              mrec += (unsigned long long)(e0[q] - b0[q]);
+            }
+            loc_append(ls, fc ^ 1, nx, del, b0[q], e0[q] - b0[q]);
+            const bool kept = alive && !del;
+            const unsigned mk = __ballot_sync(kFull, kept);
+            if (mk) {
+              const int leader = __ffs(mk) - 1;
+              unsigned bq = 0;
+              if (lane == leader) bq = atomicAdd(&ls.z[nx], (unsigned)__popc(mk));
+              bq = __shfl_sync(kFull, bq, leader);
+              if (kept) dst[seg_lo + bq + (unsigned)__popc(mk & lanemask_lt())] = v[q];
+            }
+          }
+        }
+        nalive = warp_sum_u64(nalive | (ndel << 32));
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          const unsigned long long y = __shfl_xor_sync(kFull, mymin, d);
+          mymin = y < mymin ? y : mymin;
+        }
+        if (lane == 0) {
+          if (nalive) atomicAdd(&ls.x[nx], nalive);
+          if (mymin != ~0ull) atomicMin(&ls.y[nx], mymin);
+        }
+      } else {
+        // ---- push: this CTA's slice of the frontier
+        const unsigned lo = (unsigned)(((unsigned long long)N * r) / kCluster);
+        const unsigned myc = (unsigned)(((unsigned long long)N * (r + 1)) / kCluster) - lo;
+        const unsigned Kv = (unsigned)K;
+        unsigned gs = (myc + kWarps - 1) / kWarps;
+        gs = gs < 1 ? 1 : (gs > 64 ? 64 : gs);
+        for (unsigned b = (unsigned)warp * gs; b < myc; b += (unsigned)kWarps * gs) {
+          const unsigned lim = b + gs < myc ? b + gs : myc;
+          const unsigned i0 = b + lane, i1 = b + 32 + lane;
+          const unsigned g0 = lo + (i0 < lim ? i0 : 0), g1 = lo + (i1 < lim ? i1 : 0);
+          const int t0 = loc_owner(cp, g0), t1 = loc_owner(cp, g1);
+          const unsigned p0 = __shfl_sync(kFull, cp, t0), p1 = __shfl_sync(kFull, cp, t1);
+          unsigned long long e0 = 0, e1 = 0;
+          if (i0 < lim) e0 = cl.map_shared_rank(&ls, (unsigned)t0)->f[fc][g0 - p0];
+          if (i1 < lim) e1 = cl.map_shared_rank(&ls, (unsigned)t1)->f[fc][g1 - p1];
+          const long long b0 = (long long)(e0 >> 24), b1 = (long long)(e1 >> 24);
+          const int d0 = (int)(e0 & kLocDegMask), d1 = (int)(e1 & kLocDegMask);
+          int ia = d0, ib = d1;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(kFull, ia, o), yb = __shfl_up_sync(kFull, ib, o);
+            if (lane >= o) {
+              ia += ya;
+              ib += yb;
+            }
+          }
+          const int ta = __shfl_sync(kFull, ia, 31);
+          ib += ta;
+          const int total = __shfl_sync(kFull, ib, 31);
+          for (int q0 = 0; q0 < total; q0 += 32 * kLocBatch) {
+            int u[kLocBatch];
+#pragma unroll
+            for (int q = 0; q < kLocBatch; ++q) {
+              const int j = q0 + 32 * q + lane;
+              bool hi;
+              const int t = loc_find(ia, ib, ta, j < total ? j : total - 1, hi);
+              const long long s0 = __shfl_sync(kFull, b0, t), s1 = __shfl_sync(kFull, b1, t);
+              const int x0 = __shfl_sync(kFull, ia - d0, t), x1 = __shfl_sync(kFull, ib - d1, t);
+              const long long bj = hi ? s1 : s0;
+              const int ej = hi ? x1 : x0;
+              u[q] = j < total ? gload(a.idx + bj + (j - ej)) : -1;
+            }
+            // decrement the neighbours still above the level: a residual
+            // degree <= K means deleted (earlier, by this level's scan, or by
+            // the decrement that crossed K + 1 -> K), and degrees only fall,
+            // so the L2 value of the last barrier can skip them; the atomic
+            // decides the one crossing
+            unsigned c[kLocBatch];
+            long long ob[kLocBatch], oe[kLocBatch];
+#pragma unroll
+            for (int q = 0; q < kLocBatch; ++q) {
+              c[q] = 0;
+              ob[q] = oe[q] = 0;
+              if (u[q] >= 0) {
+                c[q] = __ldcg(cnt + u[q]);
+                ob[q] = (long long)gload(off + u[q]);
+                oe[q] = (long long)gload(off + u[q] + 1);
+              }
+            }
+            bool got[kLocBatch];
+#pragma unroll
+            for (int q = 0; q < kLocBatch; ++q) {
+              got[q] = false;
+              if (c[q] > Kv) {
+                const unsigned old = atomicSub(&cnt[u[q]], 1u);
+                if (old == Kv + 1) {
+                  removed_at[u[q]] = it;
+                  a.core[u[q]] = Kv;
+                  mrec += (unsigned long long)(oe[q] - ob[q]);
+                  got[q] = true;
+                }
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < kLocBatch; ++q) loc_append(ls, fc ^ 1, nx, got[q], ob[q], oe[q] - ob[q]);
+          }
+          evisit += d0 + d1;
+        }
+      }
+      mrec = warp_sum_u64(mrec);
+      if (lane == 0 && mrec) atomicAdd(&ls.medges[nx], mrec);
+      if (threadIdx.x == 0 && r == 0) ls.stop = ab;
+      const long long c1 = clock64();
+      loc_publish(cl, ls, nx, r);
+      cl.sync();
+      const LocTotals T = loc_counts(ls, nx, cc, cp, zc, zp);
+      const long long c2 = clock64();
+      if (scan) c_scans += c2 - c0;
+      if (T.stop) {
+        handback = true;  // aborted: the waiting CTAs see the flag
+        break;
+      }
+      if (scan) {
+        const unsigned long long nalive = T.x & 0xffffffffull, ndel = T.x >> 32;
+        src = doms[wsel];
+        wsel ^= 1;
+        segmented = true;
+        seg_n = (long long)ls.z[nx];
+        seg_pre = (long long)__shfl_sync(kFull, zp, (int)r);
+        dtotal = (long long)T.z;
+        if (nalive == 0) {
+          done = true;
+          break;
+        }
+        if (ndel == 0) {
+          Kt = T.y;  // no alive vertex has degree Kt: jump to the smallest
+          ++attempt;
+        } else {
+          K = (long long)Kt;
+          Kt = (unsigned long long)(K + 1);
+          attempt = 0;
+          ++ballot_it;
+          first_push = true;
+        }
+        N = T.n;
+        m_cur = T.m;
+        if (T.ovf || N > kLocExitN || T.m > kLocEnterM) {
+          handback = true;  // a large frontier: the grid lists and pushes it
+          cur = nx;
+          break;
+        }
+      } else {
+        const unsigned long long t_end = trace_clock();
+        trace_put(a.w, it, 1 | ((first_push ? 2 : 1) << 8) | (1 << 19), (long long)N, (long long)T.m, K, t_it,
+                  t_end);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && it < a.w.trace_cap) {
+          a.w.trace[(long long)kTraceWords * it + 6] = c_scans;  // CTA 0's cycles in scans since the last push
+          a.w.trace[(long long)kTraceWords * it + 7] = c1 - c0;  // ... and in this push's walk
+        }
+        c_scans = 0;
+        t_it = t_end;
+        fsum += (long long)N;
+        if (!first_push) ++online_it;
+        first_push = false;
+        ++it;
+        N = T.n;
+        m_cur = T.m;
+        if (T.ovf || N > kLocExitN || T.m > kLocEnterM) {
+          handback = true;
+          cur = nx;
+          break;
+        }
+        if (N == 0 && !segmented && dcount > kCoreLocDom) break;  // the level ends; the grid scans
+      }
+      cur = nx;
+      fc ^= 1;
+    }
+    // a frontier handed back is pending (its vertices have removed_at ==
+    // it - 1); a segmented domain is compacted into the buffer not holding it
+    if (handback && segmented && !done) {
+      int32_t* dst = doms[wsel];
+      for (long long i = threadIdx.x; i < seg_n; i += kThreads) dst[seg_pre + i] = src[seg_lo + i];
+    }
+    __threadfence();
+    cl.sync();  // no CTA leaves while another still reads its shared memory
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      long long* w = s->loc;
+      w[kCcK] = K;
+      w[kCcPending] = done ? 0 : (long long)N;
+      w[kCcMpend] = (long long)m_cur;
+      w[kCcDomSel] = segmented ? (handback ? wsel : -2) : -1;
+      w[kCcDcount] = dtotal;
+      w[kCcDsel] = segmented ? (wsel ^ 1) : dsel;
+      w[kCcIt] = it; w[kCcBallotIt] = ballot_it; w[kCcOnlineIt] = online_it; w[kCcFsum] = fsum;
+      w[kCcDone] = done;
+      red_release_add_u64(&s->loc_epoch, 1ull);
+    }
+  }
+  if (!loc_wait_handback(s, k, sh, &s->loc_epoch, &s->loc[kCcBeat], episodes)) return false;
+  ++episodes;
+  const volatile long long* w = s->loc;
+  K = w[kCcK];
+  pending = (unsigned long long)w[kCcPending];
+  m_pend = (unsigned long long)w[kCcMpend];
+  const long long ds = w[kCcDomSel];
+  if (ds >= 0) dom = doms[ds];
+  dcount = w[kCcDcount];
+  dsel = (int)w[kCcDsel];
+  it = (int)w[kCcIt]; ballot_it = (int)w[kCcBallotIt]; online_it = (int)w[kCcOnlineIt]; fsum = w[kCcFsum];
+  done = w[kCcDone] != 0;
+  return true;
+}
+
+// CLU: small frontiers and small domains run on the first thread-block
+// cluster (the small_frontier knob; launched in clusters of kCluster).
+template <class OffT, bool CLU = false>
+__global__ void __launch_bounds__(kThreads, CLU ? 3 : 4) coreness_kernel(CoreArgs<OffT> a) {
   __shared__ CtaShared sh;
+  __shared__ typename std::conditional<CLU, LocalShared, char>::type loc_sm;
   __shared__ int cw[kCoreCats][kWarps];
   __shared__ int cb[kCoreCats];
   const unsigned grid = gridDim.x;
@@ -475,7 +815,22 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
   int dsel = 0;
   int it = 0, ballot_it = 0, online_it = 0;
   long long evisit = 0, fsum = 0;
+  unsigned long long m_pend = 0;    // out-edges of the pending vertices
+  unsigned long long episodes = 0;  // small-frontier episodes so far
   while (true) {
+    if constexpr (CLU) {
+      const bool scan_here = pending == 0 && dcount <= kCoreLocDom;
+      const bool push_here = pending > 0 && lists_ok && pending <= kLocEnterN && m_pend <= kLocEnterM;
+      if (k.small && (scan_here || push_here)) {
+        bool done = false;
+        if (!core_local(a, loc_sm, sh, removed_at, cnt, doms, cnt_l, lbuf, K, pending, m_pend, dom, dcount, dsel,
+                        it, ballot_it, online_it, fsum, evisit, episodes, done))
+          return;
+        if (done) break;
+        lists_ok = false;  // a pending frontier is listed again from removed_at
+        continue;
+      }
+    }
     const unsigned long long t_it = globaltimer();
     int filt = 1;
     if (pending == 0) {
@@ -486,13 +841,17 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
       for (int attempt = 0; attempt < 2; ++attempt) {
         clear_next_slot(s, sh);
         PhaseSlot& slot = s->slot[slot_of(sh.phase)];
-        unsigned long long nalive = 0, ndel = 0, mymin = ~0ull;
+        unsigned long long nalive = 0, ndel = 0, mymin = ~0ull, mdel = 0;
         int32_t* keep = doms[dsel];
         // deleted as if by the push before the next one
         core_scan<OffT>(dcount, dom, keep, (unsigned)Kt, it - 1, removed_at, cnt, a.core, off, a.w, k, grid,
-                        lbuf, slot, cw, cb, nalive, ndel, mymin);
+                        lbuf, slot, cw, cb, nalive, ndel, mymin, mdel);
         const unsigned long long td = cta_sum_u64(ndel, sh);
-        if (threadIdx.x == 0 && td) atomicAdd(&slot.nact, td);
+        const unsigned long long tmd = cta_sum_u64(mdel, sh);
+        if (threadIdx.x == 0 && td) {
+          atomicAdd(&slot.nact, td);
+          atomicAdd(&slot.mact, tmd);
+        }
         const unsigned long long ta = cta_sum_u64(nalive, sh);
         {
           unsigned long long m = mymin;
@@ -523,6 +882,7 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
         if (p.nact > 0) {
           K = (long long)Kt;
           pending = cnt_l[0] + cnt_l[1] + cnt_l[2] + cnt_l[3];
+          m_pend = p.mact;
           break;
         }
         Kt = ~p.aux2;  // no alive vertex has degree K + 1: jump to the smallest
@@ -571,6 +931,7 @@ __global__ void __launch_bounds__(kThreads, 4) coreness_kernel(CoreArgs<OffT> a)
     for (int c = 0; c < kClasses; ++c) cnt_l[c] = p.list_cnt[c];
     lists_ok = p.overflow == 0;
     pending = p.nact;
+    m_pend = p.mact;
     lbuf ^= 1;
     ++it;
   }
@@ -602,12 +963,23 @@ static int run_coreness(simdx_graph* g, uint32_t* core, simdx_stats* stats, cuda
   a.core = core;
   a.w = make_work(g);
   a.k = make_knobs(g);
-  const void* kern = (const void*)coreness_kernel<OffT>;
-  int grid = grid_for(g, kern);
+  // the cluster steps pay off on any graph here (the peeling's tail is
+  // small steps whatever the degrees), so the automatic setting turns them on
+  a.k.small = g->cfg.small_frontier != 0;
   int rc = prepare_launch(g, st);
   if (rc) return rc;
   void* args[] = {&a};
-  if ((rc = launch_coop(kern, grid, args, st)) != SIMDX_OK) return rc;
+  if (a.k.small) {
+    const void* kern = (const void*)coreness_kernel<OffT, true>;
+    const int grid = grid_for_cluster(g, kern, kCluster);
+    if (grid >= kCluster) {
+      if ((rc = launch_coop(kern, grid, args, st, kCluster)) != SIMDX_OK) return rc;
+      return finish_launch(g, stats, st);
+    }
+    a.k.small = 0;  // no cluster fits: the grid runs every step
+  }
+  const void* kern = (const void*)coreness_kernel<OffT>;
+  if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
   return finish_launch(g, stats, st);
 }
 

@@ -20,6 +20,9 @@ FORCED = {
     "all_classes_pull": dict(small_max=2, med_max=4, huge_min=8, direction=2),
     "all_classes_ballot": dict(small_max=2, med_max=4, huge_min=8, filter=2),
     "one_cta_per_sm": dict(ctas_per_sm=1),
+    "grid_only": dict(small_frontier=0),
+    "cluster": dict(small_frontier=1),
+    "cluster_all_classes": dict(small_frontier=1, small_max=2, med_max=4, huge_min=8),
 }
 
 

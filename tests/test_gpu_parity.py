@@ -87,7 +87,8 @@ def test_sssp_dense_iterations(delta):
     G.close()
 
 
-@pytest.mark.parametrize("mode", ["default", "ballot", "overflow", "tiny_bins", "all_classes", "one_cta_per_sm"])
+@pytest.mark.parametrize("mode", ["default", "ballot", "overflow", "tiny_bins", "all_classes", "one_cta_per_sm",
+                                  "grid_only", "cluster_all_classes"])
 @pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
 def test_coreness(gi, mode):
     """Coreness equals Batagelj-Zaversnik's; the fixed-k kernel keeps exactly
@@ -525,4 +526,21 @@ def test_bfs_small_frontier_wide_and_overflow():
         G = make(g, bits=32, small_frontier=1, direction=direction)
         assert np.array_equal(G.bfs(0).cpu().numpy(), oracle.bfs(g.offsets, g.indices, 0)), direction
         assert G.last_status() == 0
+        G.close()
+
+
+@pytest.mark.parametrize("small", [0, 1])
+def test_coreness_cluster_steps(small):
+    """The k-core decomposition with its small steps on one thread-block
+    cluster (small_frontier 1, the default's choice for coreness) and without
+    (0): the same coreness on a graph whose levels mix large and small
+    domains and frontiers (R-MAT 14, hubs) and on a grid (every level
+    small); the cluster's push steps carry bit 19 in the trace."""
+    for g in (gg.rmat(14), gg.grid(60, 70), _layered([1, 40, 3500, 3900, 200, 3000, 64, 1], seed=6)):
+        G = make(g, bits=64, small_frontier=small)
+        core = G.coreness().cpu().numpy().view(np.uint32)
+        assert np.array_equal(core, oracle.coreness(g.offsets, g.indices)), (g.name, small)
+        assert G.last_status() == 0
+        flags = [(int(r[0]) >> 19) & 1 for r in G.trace()]
+        assert (sum(flags) > 0) == bool(small), (g.name, small)
         G.close()
