@@ -189,9 +189,15 @@ typedef struct {
                                 0 = every level on the whole grid.  2 [default] = 1 for graphs
                                 whose largest out-degree is at most 64 (meshes, grids, road
                                 networks: many small levels), else 0.  Trace records of such
-                                levels carry bit 19, with words 6 and 7 the SM clock cycles
-                                CTA 0 spent in its walk and in publishing its counters plus the
-                                cluster barrier. */
+                                levels carry bit 19; in a BFS record words 6 and 7 are the SM clock
+                                cycles of the slowest CTA's walk and of CTA 0's counter
+                                publication plus cluster barrier, in a coreness record CTA 0's
+                                cycles in level scans since the previous record and the slowest
+                                CTA's push walk.  simdx_kcore_decompose: 0 = every step on the
+                                grid; 1 = the levels whose remaining vertices fit the cluster
+                                (at most 65536) in a second launch in clusters, small steps and
+                                level scans on the cluster, the densest core's push in a third,
+                                plain launch; 2 = 1 for graphs of at most 2^22 vertices. */
     int32_t reserved[5];
 } simdx_config;
 

@@ -43,7 +43,7 @@ constexpr unsigned kLocEnterN = 4096;             // enter with at most this man
 constexpr unsigned long long kLocEnterM = 65536;  // ... and frontier edges
 constexpr unsigned kLocExitN = 6144;              // leave when the next frontier holds more
 constexpr int kLocBatch = 4;                      // edges per lane in flight
-constexpr long long kLocChunk = 256;              // edges per frontier entry at most
+constexpr long long kLocChunk = 64;               // edges per frontier entry at most
 constexpr unsigned long long kLocDegMask = (1ull << 24) - 1;
 constexpr unsigned long long kLocClaim = 1ull << 63;  // a claimed entry, while in registers
 static_assert(kCluster <= 32 && (kCluster & (kCluster - 1)) == 0, "one lane per CTA of the cluster");
@@ -56,7 +56,7 @@ struct LocCounters {
   unsigned cnt;               // the CTA's entries
   unsigned flags;             // bit 0: it claimed more than kLocCap; bit 1 (rank 0): the run aborted
   unsigned z;                 // per CTA, with a prefix (algorithm's use)
-  unsigned pad;
+  unsigned walk;              // SM clock cycles the CTA spent in the step before publishing
 };
 
 struct LocalShared {
@@ -78,6 +78,7 @@ struct LocTotals {
   unsigned long long x;  // sum of x
   unsigned long long y;  // minimum of y
   unsigned z;            // sum of z
+  unsigned walk;         // the slowest CTA's cycles in the step
   unsigned ovf;          // some CTA overflowed
   unsigned stop;         // rank 0 saw the abort flag
 };
@@ -129,7 +130,8 @@ __device__ __forceinline__ int loc_owner(unsigned p, unsigned g) {
 // Before a cluster barrier: this CTA's counters of slot `sl` go to every
 // CTA of the cluster (thread c stores to CTA c), so that after the barrier
 // they are read locally.  The CTA's appends are complete (__syncthreads).
-__device__ __forceinline__ void loc_publish(cg::cluster_group& cl, LocalShared& ls, int sl, unsigned r) {
+__device__ __forceinline__ void loc_publish(cg::cluster_group& cl, LocalShared& ls, int sl, unsigned r,
+                                            unsigned walk = 0) {
   __syncthreads();
   if (threadIdx.x < kCluster) {
     LocCounters c;
@@ -139,7 +141,7 @@ __device__ __forceinline__ void loc_publish(cg::cluster_group& cl, LocalShared& 
     c.cnt = ls.cnt[sl];
     c.flags = (ls.ovf[sl] ? 1u : 0u) | (r == 0 && ls.stop ? 2u : 0u);
     c.z = ls.z[sl];
-    c.pad = 0;
+    c.walk = walk;
     cl.map_shared_rank(&ls, threadIdx.x)->all[sl][r] = c;
   }
 }
@@ -154,7 +156,7 @@ __device__ __forceinline__ LocTotals loc_counts(const LocalShared& ls, int sl, u
   c = 0;
   zc = 0;
   unsigned long long me = 0, mx = 0, my = ~0ull;
-  unsigned o = 0, x = 0;
+  unsigned o = 0, x = 0, wk = 0;
   if (lane < kCluster) {
     const LocCounters& r = ls.all[sl][lane];
     c = r.cnt;
@@ -164,6 +166,7 @@ __device__ __forceinline__ LocTotals loc_counts(const LocalShared& ls, int sl, u
     my = r.y;
     o = r.flags & 1u;
     x = r.flags & 2u;
+    wk = r.walk;
   }
   unsigned incl = c, zincl = zc;
 #pragma unroll
@@ -187,6 +190,12 @@ __device__ __forceinline__ LocTotals loc_counts(const LocalShared& ls, int sl, u
     my = v < my ? v : my;
   }
   t.y = my;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned v = __shfl_xor_sync(kFull, wk, d);
+    wk = v > wk ? v : wk;
+  }
+  t.walk = wk;
   t.ovf = __any_sync(kFull, o != 0) ? 1u : 0u;
   t.stop = __any_sync(kFull, x != 0) ? 1u : 0u;
   return t;

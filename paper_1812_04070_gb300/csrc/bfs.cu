@@ -465,7 +465,7 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       if (lane == 0 && mrec) atomicAdd(&ls.medges[nx], mrec);
       if (threadIdx.x == 0 && r == 0) ls.stop = ab;
       const long long c_walk = clock64();
-      loc_publish(cl, ls, nx, r);
+      loc_publish(cl, ls, nx, r, (unsigned)(c_walk - c_it));
       cl.sync();
       const long long c_bar = clock64();
       // the same values, so the same decisions, in every CTA of the cluster
@@ -473,7 +473,7 @@ __device__ bool bfs_local(const BfsArgs<OffT>& a, LocalShared& ls, CtaShared& sh
       const unsigned long long t_end = trace_clock();
       trace_put(a.w, it, kPush | (kOnline << 8) | (1 << 19), (long long)n_f, (long long)m_f, L, t_it, t_end);
       if (blockIdx.x == 0 && threadIdx.x == 0 && it < a.w.trace_cap) {
-        a.w.trace[(long long)kTraceWords * it + 6] = c_walk - c_it;  // CTA 0's walk (SM clock cycles)
+        a.w.trace[(long long)kTraceWords * it + 6] = (long long)T.walk;  // the slowest CTA's walk (SM cycles)
         a.w.trace[(long long)kTraceWords * it + 7] = c_bar - c_walk;  // ... its counters and the barrier
       }
       t_it = t_end;

@@ -296,6 +296,11 @@ struct CoreArgs {
   uint32_t* core;
   Work w;
   Knobs k;
+  int split;     // 1: stop at the first level whose domain fits the cluster; 2: stop before a large
+                 // push (at least kCoreBigM edges) that deletes most of what remains (the densest
+                 // core's level); the loop state goes to the resume record
+  int resume;    // continue the run a launch stopped with this split value (nothing to do if it
+                 // finished or stopped otherwise)
 };
 
 template <class OffT>
@@ -677,7 +682,7 @@ __device__ bool core_local(const CoreArgs<OffT>& a, LocalShared& ls, CtaShared& 
       if (lane == 0 && mrec) atomicAdd(&ls.medges[nx], mrec);
       if (threadIdx.x == 0 && r == 0) ls.stop = ab;
       const long long c1 = clock64();
-      loc_publish(cl, ls, nx, r);
+      loc_publish(cl, ls, nx, r, (unsigned)(c1 - c0));
       cl.sync();
       const LocTotals T = loc_counts(ls, nx, cc, cp, zc, zp);
       const long long c2 = clock64();
@@ -721,7 +726,7 @@ __device__ bool core_local(const CoreArgs<OffT>& a, LocalShared& ls, CtaShared& 
                   t_end);
         if (blockIdx.x == 0 && threadIdx.x == 0 && it < a.w.trace_cap) {
           a.w.trace[(long long)kTraceWords * it + 6] = c_scans;  // CTA 0's cycles in scans since the last push
-          a.w.trace[(long long)kTraceWords * it + 7] = c1 - c0;  // ... and in this push's walk
+          a.w.trace[(long long)kTraceWords * it + 7] = (long long)T.walk;  // ... the slowest CTA's push walk
         }
         c_scans = 0;
         t_it = t_end;
@@ -777,6 +782,12 @@ __device__ bool core_local(const CoreArgs<OffT>& a, LocalShared& ls, CtaShared& 
   return true;
 }
 
+// Loop state words of the resume record when a run is split between a grid
+// launch (the large levels) and a cluster launch (the rest).
+enum { kCrK, kCrDom, kCrDcount, kCrDsel, kCrIt, kCrBallotIt, kCrOnlineIt, kCrFsum, kCrPhases, kCrPending, kCrMpend };
+constexpr unsigned long long kCoreBigM = 1ull << 20;  // a push this large goes back to the plain grid
+constexpr long long kCoreAutoMaxN = 1ll << 22;        // small_frontier = 2: clusters up to this many vertices
+
 // CLU: small frontiers and small domains run on the first thread-block
 // cluster (the small_frontier knob; launched in clusters of kCluster).
 template <class OffT, bool CLU = false>
@@ -798,12 +809,17 @@ __global__ void __launch_bounds__(kThreads, CLU ? 3 : 4) coreness_kernel(CoreArg
   auto deg = [off](int v) { return (long long)gload(off + v + 1) - (long long)gload(off + v); };
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
-  for (long long v = gtid; v < n; v += gthreads) {
-    cnt[v] = (uint32_t)deg((int)v);
-    removed_at[v] = INT_MAX;
+  // a resumed run skips the set-up; a run the first launch finished ends here
+  const bool resumed = a.resume && ld_volatile_i32(&s->rs.active) == a.resume;
+  if (a.resume && !resumed) return;
+  if (!resumed) {
+    for (long long v = gtid; v < n; v += gthreads) {
+      cnt[v] = (uint32_t)deg((int)v);
+      removed_at[v] = INT_MAX;
+    }
+    clear_next_slot(s, sh);
+    if (!grid_sync(s, grid, sh, k)) return;
   }
-  clear_next_slot(s, sh);
-  if (!grid_sync(s, grid, sh, k)) return;
 
   int lbuf = 0;
   unsigned cnt_l[kClasses] = {0u, 0u, 0u, 0u};
@@ -817,7 +833,46 @@ __global__ void __launch_bounds__(kThreads, CLU ? 3 : 4) coreness_kernel(CoreArg
   long long evisit = 0, fsum = 0;
   unsigned long long m_pend = 0;    // out-edges of the pending vertices
   unsigned long long episodes = 0;  // small-frontier episodes so far
+  long long phases0 = 0;            // barrier phases of the first launch
+  if (resumed) {
+    const volatile long long* r = s->rs.v;
+    K = r[kCrK];
+    const long long ds = r[kCrDom];
+    dom = ds < 0 ? nullptr : doms[ds];
+    dcount = r[kCrDcount];
+    dsel = (int)r[kCrDsel];
+    it = (int)r[kCrIt];
+    ballot_it = (int)r[kCrBallotIt];
+    online_it = (int)r[kCrOnlineIt];
+    fsum = r[kCrFsum];
+    phases0 = r[kCrPhases];
+    pending = (unsigned long long)r[kCrPending];
+    m_pend = (unsigned long long)r[kCrMpend];
+    lists_ok = pending == 0;  // a pending frontier is listed again from removed_at
+  }
   while (true) {
+    if ((a.split == 1 && pending == 0 && dcount <= kCoreLocDom) ||
+        (a.split == 2 && pending > 0 && m_pend >= kCoreBigM && 2 * pending >= (unsigned long long)dcount)) {
+      // the rest of the run is the cluster launch's: hand the loop state over
+      const unsigned long long ev = cta_sum_u64((unsigned long long)evisit, sh);
+      if (threadIdx.x == 0) atomicAdd(&s->evisit, ev);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long* r = s->rs.v;
+        r[kCrK] = K;
+        r[kCrDom] = dom == nullptr ? -1 : (dom == doms[0] ? 0 : 1);
+        r[kCrDcount] = dcount;
+        r[kCrDsel] = dsel;
+        r[kCrIt] = it;
+        r[kCrBallotIt] = ballot_it;
+        r[kCrOnlineIt] = online_it;
+        r[kCrFsum] = fsum;
+        r[kCrPhases] = phases0 + (long long)sh.phase;
+        r[kCrPending] = (long long)pending;
+        r[kCrMpend] = (long long)m_pend;
+        s->rs.active = a.split;
+      }
+      return;
+    }
     if constexpr (CLU) {
       const bool scan_here = pending == 0 && dcount <= kCoreLocDom;
       const bool push_here = pending > 0 && lists_ok && pending <= kLocEnterN && m_pend <= kLocEnterM;
@@ -946,7 +1001,7 @@ __global__ void __launch_bounds__(kThreads, CLU ? 3 : 4) coreness_kernel(CoreArg
     st.pull_iters = 0;
     st.ballot_iters = ballot_it;
     st.online_iters = online_it;
-    st.phases = (int)sh.phase;
+    st.phases = (int)(phases0 + (long long)sh.phase);
     st.grid = (int)grid;
     st.edges_visited = (long long)s->evisit;
     st.frontier_sum = fsum;
@@ -963,22 +1018,36 @@ static int run_coreness(simdx_graph* g, uint32_t* core, simdx_stats* stats, cuda
   a.core = core;
   a.w = make_work(g);
   a.k = make_knobs(g);
-  // the cluster steps pay off on any graph here (the peeling's tail is
-  // small steps whatever the degrees), so the automatic setting turns them on
-  a.k.small = g->cfg.small_frontier != 0;
+  // the peeling's tail is small steps whatever the degrees; the automatic
+  // setting turns the cluster on up to kCoreAutoMaxN vertices (measured on
+  // R-MAT: 34 % faster at 2^18, 24 % at 2^20, 6 % at 2^22, 5 % slower at
+  // 2^24, where the tail's larger pushes dominate and run on fewer CTAs)
+  a.k.small = g->cfg.small_frontier == 1 || (g->cfg.small_frontier == 2 && g->n <= kCoreAutoMaxN);
   int rc = prepare_launch(g, st);
   if (rc) return rc;
   void* args[] = {&a};
-  if (a.k.small) {
-    const void* kern = (const void*)coreness_kernel<OffT, true>;
-    const int grid = grid_for_cluster(g, kern, kCluster);
-    if (grid >= kCluster) {
-      if ((rc = launch_coop(kern, grid, args, st, kCluster)) != SIMDX_OK) return rc;
-      return finish_launch(g, stats, st);
-    }
-    a.k.small = 0;  // no cluster fits: the grid runs every step
-  }
   const void* kern = (const void*)coreness_kernel<OffT>;
+  const void* kclu = (const void*)coreness_kernel<OffT, true>;
+  const int gclu = a.k.small ? grid_for_cluster(g, kclu, kCluster) : 0;
+  if (gclu >= kCluster) {
+    // the large levels on the plain grid (every CTA it fits), the tail --
+    // levels whose remaining vertices fit the cluster's scans -- in
+    // clusters; the second launch finds the first one's state in the
+    // resume record (or nothing to do)
+    a.split = 1;
+    if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
+    if ((rc = prepare_resume(g, st)) != SIMDX_OK) return rc;
+    a.split = 2;
+    a.resume = 1;
+    if ((rc = launch_coop(kclu, gclu, args, st, kCluster)) != SIMDX_OK) return rc;
+    // a large push of the tail (the densest core's level) back on the plain grid
+    if ((rc = prepare_resume(g, st)) != SIMDX_OK) return rc;
+    a.split = 0;
+    a.resume = 2;
+    if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
+    return finish_launch(g, stats, st, 3);
+  }
+  a.k.small = 0;  // off, or no cluster fits: the grid runs every step
   if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
   return finish_launch(g, stats, st);
 }
