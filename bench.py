@@ -34,6 +34,7 @@ definitions.
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -250,11 +251,13 @@ def _code_only(text: str) -> str:
 def kernel_source_hash(kernel: str) -> str:
     """Hash of the code a kernel is built from (comments and layout
     ignored): its own file (<algorithm>.cu for <algorithm>_kernel) and the
-    shared device header (the host-side header declares no device code)."""
+    shared device headers (*.cuh; the host-side header declares no device
+    code)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1812_04070_gb300", "csrc")
     own = KERNEL_FILES.get(kernel, kernel.replace("_kernel", "") + ".cu")
-    for fn in [own, "acc_device.cuh"]:
+    headers = sorted(os.path.basename(p) for p in glob.glob(os.path.join(csrc, "*.cuh")))
+    for fn in [own] + headers:
         with open(os.path.join(csrc, fn), encoding="utf-8") as f:
             h.update(fn.encode())
             h.update(_code_only(f.read()).encode())
