@@ -551,8 +551,14 @@ def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
     for a in algs:
         d2h += g.n * (4 if a in ("bfs", "sssp", "pagerank", "coreness", "wcc") else 5)
 
+    split = {"create": 0.0, "run": 0.0}
+
     def one():
+        t0 = time.perf_counter()
         G = Graph(p_off.numpy(), p_idx.numpy(), weights=p_w.numpy().view(np.uint32) if "sssp" in algs else None)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        split["create"] += t1 - t0
         for a in algs:
             if tuned_full:
                 G.set_config(**tuned_full[a])
@@ -571,9 +577,11 @@ def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
             else:
                 host_out[a].copy_(G.pagerank(0.85, 1e-6, 1000), non_blocking=True)
         torch.cuda.synchronize()
+        split["run"] += time.perf_counter() - t1
         G.close()
 
     one()
+    split["create"] = split["run"] = 0.0
     ts = []
     for _ in range(args.e2e_steps):
         t0 = time.perf_counter()
@@ -583,6 +591,8 @@ def run_e2e(args, g, w, bits, algs, edges_step, world, tuned_full=None):
     return {"value": round(job_rate(edges_step * len(ts), tot, world) / 1e9, 3), "unit": "GTEPS",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": round(tot / len(ts) * 1e3, 3),
+            "ms_create_per_step": round(split["create"] / len(ts) * 1e3, 3),
+            "ms_algorithms_and_d2h_per_step": round(split["run"] / len(ts) * 1e3, 3),
             "note": "host pinned CSR -> simdx_graph_create -> algorithms -> results to host, per step"}
 
 
