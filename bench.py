@@ -857,7 +857,10 @@ def run_ablation(args, rank, world, local):
                       ("edges staged by bulk copy", dict(sssp_combine=0, stage_edges=1)),
                       ("delta=64", dict(stage_edges=0, delta=64)), ("delta=256", dict(delta=256)),
                       ("delta=unbounded", dict(delta=0)), ("pull every iteration", dict(delta=default_delta,
-                                                                                         direction=2))],
+                                                                                         direction=2)),
+                      ("small frontiers on one cluster", dict(direction=0, small_frontier=1)),
+                      ("delta=64, small frontiers on one cluster", dict(delta=64)),
+                      ("delta=64, grid only", dict(small_frontier=0))],
              "kcore": [fl(0, 0), fl(0, 2)],
              "pagerank": [("pull, then push (default switch rule)", dict(pr_alpha=8.0)),
                           ("pull only", dict(pr_alpha=0.0))] +

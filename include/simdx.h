@@ -197,7 +197,10 @@ typedef struct {
                                 grid; 1 = the levels whose remaining vertices fit the cluster
                                 (at most 65536) in a second launch in clusters, small steps and
                                 level scans on the cluster, the densest core's push in a third,
-                                plain launch; 2 = 1 for graphs of at most 2^22 vertices. */
+                                plain launch; 2 = 1 for graphs of at most 2^22 vertices.
+                                simdx_sssp (single source, all fusion, push): 1 = push
+                                iterations whose frontier below the bucket bound fits run on
+                                the cluster; 0 and 2 = the grid. */
     int32_t reserved[5];
 } simdx_config;
 

@@ -544,3 +544,48 @@ def test_coreness_cluster_steps(small):
         flags = [(int(r[0]) >> 19) & 1 for r in G.trace()]
         assert (sum(flags) > 0) == bool(small), (g.name, small)
         G.close()
+
+
+SSSP_SMALL = {"cluster": dict(small_frontier=1), "cluster_all_classes": dict(small_frontier=1, small_max=2, med_max=4,
+                                                                            huge_min=8),
+              "cluster_ballot": dict(small_frontier=1, filter=2), "cluster_delta64": dict(small_frontier=1, delta=64),
+              "cluster_delta0": dict(small_frontier=1, delta=0)}
+
+
+@pytest.mark.parametrize("mode", list(SSSP_SMALL))
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_sssp_small_frontier_cluster(gi, mode):
+    """Single-source SSSP with its small push frontiers on one thread-block
+    cluster: distances equal Dijkstra's on every graph, for narrow, wide
+    and unbounded buckets."""
+    g = GRAPHS[gi]
+    w = gg.weights(g, 77 + gi, 1, 64)
+    G = make(g, w, bits=64 if gi % 2 else 32, **SSSP_SMALL[mode])
+    for s in sources(g):
+        d = G.sssp(s).cpu().numpy().view(np.uint32)
+        assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, s)), (g.name, mode, s)
+    assert G.last_status() == 0
+    G.close()
+
+
+def test_sssp_small_frontier_grid_and_layers():
+    """On a grid every push frontier is small: the cluster runs them (trace
+    bit 19) and the grid advances the buckets; a layered graph with wide
+    layers and a skewed one (a hub whose improvements overflow the claiming
+    CTA) hand back and forth."""
+    for g, w in ((gg.grid(90, 70), None), (_layered([1, 40, 3500, 3900, 200, 3000, 64, 1], seed=8), None)):
+        w = gg.weights(g, 31, 1, 1000)
+        G = make(g, w, bits=64, small_frontier=1)
+        d = G.sssp(0).cpu().numpy().view(np.uint32)
+        assert np.array_equal(d, oracle.sssp(g.offsets, g.indices, w, 0)), g.name
+        flags = [(int(r[0]) >> 19) & 1 for r in G.trace()]
+        assert sum(flags) > 0, g.name
+        G.close()
+    k = 1500
+    kids = 8 * np.arange(1, k + 1)
+    g = gg.from_edges(8 * k + 8, np.concatenate([np.zeros(k, np.int64), kids, kids + 1]),
+                      np.concatenate([kids, kids + 1, kids + 2]), "skewed")
+    w = gg.weights(g, 32, 1, 64)
+    G = make(g, w, bits=32, small_frontier=1)
+    assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
+    G.close()
