@@ -314,6 +314,21 @@ SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
 SIMDX_API int simdx_kcore_decompose(simdx_graph *g, uint32_t *coreness, simdx_stats *stats,
                                     void *stream);
 
+/* Batched k-core (the k-core of Sec. 6 for several k in one call): for
+ * every ks[i], row i of in_core / residual_deg is what simdx_kcore(ks[i])
+ * returns -- in_core[i*n + v] = 1 iff v belongs to the ks[i]-core, and
+ * residual_deg[i*n + v] = the number of v's neighbours (edges) inside that
+ * core for a member, 0 otherwise.  One decomposition (simdx_kcore_decompose,
+ * its coreness kept in the graph's workspace) answers every k: v is in the
+ * k-core exactly when coreness(v) >= k; one more launch counts, per vertex,
+ * the neighbours whose coreness reaches each k and writes the rows.
+ * ks: host uint32[nk], any order, repeats allowed, 1 <= nk <= 64; in_core:
+ * device uint8[nk * n]; residual_deg: device uint32[nk * n] or NULL (not
+ * written).  Needs a symmetric graph.  Errors: EINVAL (NULL ks or in_core,
+ * nk outside [1, 64], directed graph). */
+SIMDX_API int simdx_kcore_batch(simdx_graph *g, const uint32_t *ks, int32_t nk, uint8_t *in_core,
+                                uint32_t *residual_deg, simdx_stats *stats, void *stream);
+
 /* Weakly connected components (Sec. 3.2 lists WCC with the voting
  * algorithms): label[v] = the smallest vertex id of v's component, so two
  * vertices share a label exactly when a path joins them.  Two launches on

@@ -169,6 +169,18 @@ class Graph:
                           _stream_handle(stream))
         return out, resid
 
+    def kcore_batch(self, ks, want_resid: bool = True, stats: simdx_stats | None = None, stream=None):
+        """The k-core of every k in `ks` (simdx_kcore_batch): uint8 rows
+        [len(ks), n] of membership and, if asked, int32 rows of residual
+        degrees (uint32 values)."""
+        torch = _torch()
+        ks = [int(k) for k in ks]
+        inc = torch.empty((len(ks), self.n), dtype=torch.uint8, device=self.device)
+        res = torch.empty((len(ks), self.n), dtype=torch.int32, device=self.device) if want_resid else None
+        simdx.simdx_kcore_batch(self.handle, ks, inc.data_ptr(), res.data_ptr() if want_resid else None, stats,
+                                _stream_handle(stream))
+        return inc, res
+
     def coreness(self, out=None, stats: simdx_stats | None = None, stream=None):
         """uint32 coreness of every vertex in an int32 tensor
         (simdx_kcore_decompose)."""

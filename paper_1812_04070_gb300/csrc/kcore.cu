@@ -17,6 +17,7 @@
 // once they become few, the order Sec. 5 gives for k-core; the switch
 // compares the frontier's edges with the alive vertices' edges.
 #include <climits>
+#include <utility>
 #include <type_traits>
 
 #include "acc_cluster.cuh"
@@ -1009,8 +1010,10 @@ __global__ void __launch_bounds__(kThreads, CLU ? 3 : 4) coreness_kernel(CoreArg
   }
 }
 
+// The decomposition's launches on `st` (no statistics read-back); returns
+// their count in *launches.
 template <class OffT>
-static int run_coreness(simdx_graph* g, uint32_t* core, simdx_stats* stats, cudaStream_t st) {
+static int launch_coreness(simdx_graph* g, uint32_t* core, cudaStream_t st, int* launches) {
   CoreArgs<OffT> a{};
   a.n = (int)g->n;
   a.off = (const OffT*)g->off;
@@ -1045,11 +1048,131 @@ static int run_coreness(simdx_graph* g, uint32_t* core, simdx_stats* stats, cuda
     a.split = 0;
     a.resume = 2;
     if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
-    return finish_launch(g, stats, st, 3);
+    *launches = 3;
+    return SIMDX_OK;
   }
   a.k.small = 0;  // off, or no cluster fits: the grid runs every step
   if ((rc = launch_coop(kern, grid_for(g, kern), args, st)) != SIMDX_OK) return rc;
-  return finish_launch(g, stats, st);
+  *launches = 1;
+  return SIMDX_OK;
+}
+
+template <class OffT>
+static int run_coreness(simdx_graph* g, uint32_t* core, simdx_stats* stats, cudaStream_t st) {
+  int launches = 0;
+  const int rc = launch_coreness<OffT>(g, core, st, &launches);
+  return rc ? rc : finish_launch(g, stats, st, launches);
+}
+
+// ---------------------------------------------------------------- k-core batch
+// The k-core of every k in one list from one decomposition: v is in the
+// k-core exactly when coreness(v) >= k, and its degree inside the k-core
+// counts the neighbours u with min(coreness(u), coreness(v)) >= k.  A warp
+// takes 32 consecutive vertices one after another, streams each one's
+// edges, and for every edge finds how many of the (sorted) k values
+// min(coreness(u), coreness(v)) reaches; one ballot per k value counts them
+// for all 32 edges of a round.  The counts go to shared memory and leave as
+// coalesced rows, one per k.
+constexpr int kKcoreBatchMax = 64;
+
+struct KcoreRows {
+  uint32_t ks[kKcoreBatchMax];   // ascending
+  int32_t row[kKcoreBatchMax];   // the caller's row of ks[i]
+  int nk;
+};
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) kcore_rows_kernel(int n, const OffT* off, const int32_t* idx,
+                                                             const uint32_t* core, const KcoreRows q,
+                                                             uint8_t* in_core, uint32_t* resid) {
+  extern __shared__ uint32_t s_cnt[];  // [warp][k][32 vertices]
+  __shared__ uint32_t ks[kKcoreBatchMax];
+  const int nk = q.nk;
+  for (int i = threadIdx.x; i < nk; i += kThreads) ks[i] = q.ks[i];
+  __syncthreads();
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t* cntw = s_cnt + (size_t)warp * nk * 32;
+  const long long tiles = ((long long)n + 31) / 32;
+  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < tiles; tile += (long long)gridDim.x * kWarps) {
+    const long long base = tile * 32;
+    const int nv = (int)((long long)n - base < 32 ? (long long)n - base : 32);
+    for (int vi = 0; vi < nv; ++vi) {
+      const long long v = base + vi;
+      const uint32_t cv = __ldg(core + v);
+      uint32_t c0 = 0, c1 = 0;  // counts of k values lane and lane + 32
+      if (cv >= ks[0] && resid) {  // in some core: count its neighbours in each
+        const long long b = (long long)__ldg(off + v), e = (long long)__ldg(off + v + 1);
+        for (long long p0 = b; p0 < e; p0 += 32) {
+          const long long p = p0 + lane;
+          int j = 0;  // k values reached by this edge
+          if (p < e) {
+            const uint32_t cu = __ldg(core + __ldg(idx + p));
+            const uint32_t m = cu < cv ? cu : cv;
+            int lo = 0, hi = nk;  // first i with ks[i] > m
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (ks[mid] <= m) lo = mid + 1;
+              else hi = mid;
+            }
+            j = lo;
+          }
+          for (int i = 0; i < nk; ++i) {
+            const unsigned c = (unsigned)__popc(__ballot_sync(kFull, j > i));
+            if (lane == (i & 31)) {
+              if (i < 32) c0 += c;
+              else c1 += c;
+            }
+          }
+        }
+      }
+      if (lane < nk) cntw[lane * 32 + vi] = c0;
+      if (lane + 32 < nk) cntw[(lane + 32) * 32 + vi] = c1;
+    }
+    __syncwarp();
+    if (lane < nv) {
+      const long long v = base + lane;
+      const uint32_t cv = __ldg(core + v);
+      for (int i = 0; i < nk; ++i) {
+        const bool inc = cv >= ks[i];
+        const size_t at = (size_t)q.row[i] * (size_t)n + (size_t)v;
+        in_core[at] = inc ? 1 : 0;
+        if (resid) resid[at] = inc ? cntw[i * 32 + lane] : 0u;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <class OffT>
+static int run_kcore_batch(simdx_graph* g, const uint32_t* ks, int nk, uint8_t* in_core, uint32_t* resid,
+                           simdx_stats* stats, cudaStream_t st) {
+  // the decomposition's output lives in the spare fifth of the algorithm
+  // state (the peeling uses four n-word arrays)
+  uint32_t* core = reinterpret_cast<uint32_t*>(g->state) + 4 * (size_t)g->n;
+  int launches = 0;
+  int rc = launch_coreness<OffT>(g, core, st, &launches);
+  if (rc) return rc;
+  KcoreRows q{};
+  q.nk = nk;
+  for (int i = 0; i < nk; ++i) {
+    q.ks[i] = ks[i];
+    q.row[i] = i;
+  }
+  for (int i = 1; i < nk; ++i)  // insertion sort of (k, row) by k
+    for (int j = i; j > 0 && q.ks[j - 1] > q.ks[j]; --j) {
+      std::swap(q.ks[j - 1], q.ks[j]);
+      std::swap(q.row[j - 1], q.row[j]);
+    }
+  const void* kern = (const void*)kcore_rows_kernel<OffT>;
+  const size_t smem = sizeof(uint32_t) * (size_t)kWarps * (size_t)nk * 32;
+  SIMDX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long tiles = ((long long)g->n + 31) / 32;
+  const long long blocks = (tiles + kWarps - 1) / kWarps;
+  const unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
+  kcore_rows_kernel<OffT><<<grid, kThreads, smem, st>>>((int)g->n, (const OffT*)g->off, g->idx, core, q, in_core,
+                                                       resid);
+  SIMDX_CUDA(cudaGetLastError());
+  return finish_launch(g, stats, st, launches + 1);
 }
 
 const void* kcore_kernel_ptr(int off_bits) {
@@ -1092,6 +1215,19 @@ extern "C" int simdx_kcore(simdx_graph* g, uint32_t k, uint8_t* in_core, uint32_
   }
   return g->off_bits == 32 ? run_kcore<int32_t>(g, k, in_core, residual_deg, stats, st)
                            : run_kcore<long long>(g, k, in_core, residual_deg, stats, st);
+}
+
+extern "C" int simdx_kcore_batch(simdx_graph* g, const uint32_t* ks, int32_t nk, uint8_t* in_core,
+                                 uint32_t* residual_deg, simdx_stats* stats, void* stream) {
+  if (!g || !ks || !in_core || !g->symmetric || nk < 1 || nk > kKcoreBatchMax) return SIMDX_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g->n == 0) {
+    int rc = prepare_launch(g, st);
+    return rc ? rc : finish_launch(g, stats, st);
+  }
+  return g->off_bits == 32 ? run_kcore_batch<int32_t>(g, ks, nk, in_core, residual_deg, stats, st)
+                           : run_kcore_batch<long long>(g, ks, nk, in_core, residual_deg, stats, st);
 }
 
 extern "C" int simdx_kcore_decompose(simdx_graph* g, uint32_t* coreness, simdx_stats* stats, void* stream) {

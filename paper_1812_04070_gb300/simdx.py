@@ -87,6 +87,8 @@ SIGNATURES = {
     "simdx_sssp": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_kcore": (ctypes.c_int, [_vp, _u32, _vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_kcore_decompose": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
+    "simdx_kcore_batch": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), _i32, _vp, _vp,
+                                         ctypes.POINTER(simdx_stats), _vp]),
     "simdx_wcc": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_pagerank": (ctypes.c_int, [_vp, _f32, _f32, _i32, _vp, ctypes.POINTER(simdx_stats), _vp]),
     "simdx_bfs_noalloc": (ctypes.c_int, [ctypes.POINTER(simdx_csr), _i32, _vp, _vp]),
@@ -208,6 +210,13 @@ def simdx_kcore(g: int, k: int, in_core_ptr: int, resid_ptr: int | None, stats: 
                 stream: int | None) -> None:
     _check(_lib().simdx_kcore(g, k, in_core_ptr, resid_ptr, ctypes.byref(stats) if stats is not None else None,
                               stream), "simdx_kcore")
+
+
+def simdx_kcore_batch(g: int, ks, in_core_ptr: int, resid_ptr: int | None, stats: simdx_stats | None,
+                      stream: int | None) -> None:
+    arr = (ctypes.c_uint32 * len(ks))(*[int(k) for k in ks])
+    _check(_lib().simdx_kcore_batch(g, arr, len(ks), in_core_ptr, resid_ptr,
+                                    ctypes.byref(stats) if stats is not None else None, stream), "simdx_kcore_batch")
 
 
 def simdx_kcore_decompose(g: int, core_ptr: int, stats: simdx_stats | None, stream: int | None) -> None:

@@ -50,11 +50,17 @@ def test_rmat20_sssp_kcore_pagerank():
     g, w = _rmat(20)
     G = make(g, w, bits=32)
     assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
-    for k in (16, 32):
+    ks = (16, 32)
+    binc, bres = G.kcore_batch([32, 16, 100])
+    for k in ks:
         inc, resid = G.kcore(k)
         ei, er = oracle.kcore(g.offsets, g.indices, k)
         assert np.array_equal(inc.cpu().numpy(), ei)
         assert np.array_equal(resid.cpu().numpy(), er)
+        row = 1 if k == 16 else 0
+        assert np.array_equal(binc[row].cpu().numpy(), ei) and np.array_equal(bres[row].cpu().numpy(), er)
+    ei, er = oracle.kcore(g.offsets, g.indices, 100)
+    assert np.array_equal(binc[2].cpu().numpy(), ei) and np.array_equal(bres[2].cpu().numpy().view(np.uint32), er)
     assert np.array_equal(G.coreness().cpu().numpy().view(np.uint32), oracle.coreness(g.offsets, g.indices))
     assert np.array_equal(G.wcc().cpu().numpy().view(np.uint32), oracle.wcc(g.offsets, g.indices))
     st, rel = assert_pagerank(G, g)

@@ -589,3 +589,53 @@ def test_sssp_small_frontier_grid_and_layers():
     G = make(g, w, bits=32, small_frontier=1)
     assert np.array_equal(G.sssp(0).cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 0))
     G.close()
+
+
+KCORE_BATCH_KS = [16, 0, 1, 2, 3, 5, 32, 1000, 3, 7]
+
+
+@pytest.mark.parametrize("mode", ["default", "grid_only", "no_resid"])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=GRAPH_IDS)
+def test_kcore_batch(gi, mode):
+    """simdx_kcore_batch: row i equals simdx_kcore(ks[i]) and the oracle's
+    peeling for that k (membership and residual degrees), for k values in
+    any order with repeats, k = 0 and a k above every coreness."""
+    g = GRAPHS[gi]
+    knobs = dict(small_frontier=0) if mode == "grid_only" else {}
+    G = make(g, bits=32 if gi % 2 else 64, **knobs)
+    inc, res = G.kcore_batch(KCORE_BATCH_KS, want_resid=mode != "no_resid")
+    inc = inc.cpu().numpy()
+    for i, k in enumerate(KCORE_BATCH_KS):
+        ei, er = oracle.kcore(g.offsets, g.indices, k)
+        assert np.array_equal(inc[i], ei), (g.name, mode, k)
+        if res is not None:
+            assert np.array_equal(res[i].cpu().numpy().view(np.uint32), er), (g.name, mode, k)
+    assert G.last_status() == 0
+    G.close()
+
+
+def test_kcore_batch_limits():
+    """64 k values in one call; 0 or 65 values and a directed graph are
+    rejected."""
+    from paper_1812_04070_gb300 import SimdxError, simdx
+    from gpu_util import directed_graph
+    from paper_1812_04070_gb300 import Graph
+    g = gg.rmat(13)
+    G = make(g, bits=32)
+    ks = list(range(0, 128, 2))
+    inc, res = G.kcore_batch(ks)
+    core = oracle.coreness(g.offsets, g.indices)
+    for i, k in enumerate(ks):
+        assert np.array_equal(inc[i].cpu().numpy(), (core >= k).astype(np.uint8)), k
+        assert np.array_equal(res[i].cpu().numpy().view(np.uint32), oracle.kcore(g.offsets, g.indices, k)[1]), k
+    for bad in ([], list(range(65))):
+        with pytest.raises(SimdxError) as e:
+            G.kcore_batch(bad)
+        assert e.value.status == simdx.EINVAL
+    G.close()
+    off, idx, ioff, iidx, _ = directed_graph(300, 1500, 3)
+    D = Graph(off, idx, csc=(ioff, iidx))
+    with pytest.raises(SimdxError) as e:
+        D.kcore_batch([2])
+    assert e.value.status == simdx.EINVAL
+    D.close()
