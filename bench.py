@@ -674,6 +674,24 @@ def run_batch(args, rank, world, local):
     res["sssp_virtual_copies"] = {"batched_qps": round(64 / tg * 1e3, 1), "batched_ms": round(tg, 3),
                                   "launches": st.launches, "identical": bool(torch.equal(ob, o1))}
     G.set_config(batch_group=0)
+    # k-core for 64 values of k (1..64): one decomposition and one row launch
+    # against 64 fixed-k runs
+    ks = list(range(1, 65))
+    kin = torch.empty((64, g.n), dtype=torch.uint8, device="cuda")
+    krs = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+
+    def kone():
+        for i, k in enumerate(ks):
+            G.kcore(k, out=kin[i], resid=krs[i])
+
+    tk1 = _ev_time(kone, reps)
+    kb_in, kb_rs = G.kcore_batch(ks)
+    torch.cuda.synchronize()
+    tkb = _ev_time(lambda: G.kcore_batch(ks), reps)
+    res["kcore_k1_64"] = {"batched_qps": round(64 / tkb * 1e3, 1), "per_query_qps": round(64 / tk1 * 1e3, 1),
+                          "batched_ms": round(tkb, 3), "per_query_ms": round(tk1, 3),
+                          "identical": bool(torch.equal(kb_in, kin) and torch.equal(kb_rs, krs)),
+                          "note": "simdx_kcore_batch (one decomposition, then the rows) against simdx_kcore per k"}
     G.close()
     graphs, gsrc = gg.multigraph_batch(count=256)
     packed, bases = gg.pack(graphs)
@@ -706,24 +724,6 @@ def run_batch(args, rank, world, local):
     for Gi in Gs:
         Gi.close()
     P.close()
-    # k-core for 64 values of k (1..64): one decomposition and one row launch
-    # against 64 fixed-k runs
-    ks = list(range(1, 65))
-    kin = torch.empty((64, g.n), dtype=torch.uint8, device="cuda")
-    krs = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
-
-    def kone():
-        for i, k in enumerate(ks):
-            G.kcore(k, out=kin[i], resid=krs[i])
-
-    tk1 = _ev_time(kone, reps)
-    kb_in, kb_rs = G.kcore_batch(ks)
-    torch.cuda.synchronize()
-    tkb = _ev_time(lambda: G.kcore_batch(ks), reps)
-    res["kcore_k1_64"] = {"batched_qps": round(64 / tkb * 1e3, 1), "per_query_qps": round(64 / tk1 * 1e3, 1),
-                          "batched_ms": round(tkb, 3), "per_query_ms": round(tk1, 3),
-                          "identical": bool(torch.equal(kb_in, kin) and torch.equal(kb_rs, krs)),
-                          "note": "simdx_kcore_batch (one decomposition, then the rows) against simdx_kcore per k"}
     tot_b = 64 / res["bfs"]["batched_qps"] + 64 / res["sssp"]["batched_qps"] + 256 / res["multigraph_bfs"]["batched_qps"]
     value = job_rate(64 + 64 + 256, tot_b, world)
     return {"metric": "queries/s (batched)", "value": round(value, 1), "unit": "queries/s", "n_gpus": world,

@@ -1074,6 +1074,7 @@ static int run_coreness(simdx_graph* g, uint32_t* core, simdx_stats* stats, cuda
 // for all 32 edges of a round.  The counts go to shared memory and leave as
 // coalesced rows, one per k.
 constexpr int kKcoreBatchMax = 64;
+constexpr long long kKcoreRowsHeavy = 128;  // vertices of more edges are counted by a whole CTA
 
 struct KcoreRows {
   uint32_t ks[kKcoreBatchMax];   // ascending
@@ -1100,8 +1101,10 @@ __global__ void __launch_bounds__(kThreads) kcore_rows_kernel(int n, const OffT*
       const long long v = base + vi;
       const uint32_t cv = __ldg(core + v);
       uint32_t c0 = 0, c1 = 0;  // counts of k values lane and lane + 32
-      if (cv >= ks[0] && resid) {  // in some core: count its neighbours in each
-        const long long b = (long long)__ldg(off + v), e = (long long)__ldg(off + v + 1);
+      const long long b = (long long)__ldg(off + v), e = (long long)__ldg(off + v + 1);
+      if (cv >= ks[0] && resid && e - b <= kKcoreRowsHeavy) {  // in some core: count its neighbours in each
+        int nkv = 0;  // the k values this vertex's core reaches (the others count nothing)
+        while (nkv < nk && ks[nkv] <= cv) ++nkv;
         for (long long p0 = b; p0 < e; p0 += 32) {
           const long long p = p0 + lane;
           int j = 0;  // k values reached by this edge
@@ -1116,7 +1119,7 @@ __global__ void __launch_bounds__(kThreads) kcore_rows_kernel(int n, const OffT*
             }
             j = lo;
           }
-          for (int i = 0; i < nk; ++i) {
+          for (int i = 0; i < nkv; ++i) {
             const unsigned c = (unsigned)__popc(__ballot_sync(kFull, j > i));
             if (lane == (i & 31)) {
               if (i < 32) c0 += c;
@@ -1129,8 +1132,11 @@ __global__ void __launch_bounds__(kThreads) kcore_rows_kernel(int n, const OffT*
       if (lane + 32 < nk) cntw[(lane + 32) * 32 + vi] = c1;
     }
     __syncwarp();
-    if (lane < nv) {
-      const long long v = base + lane;
+    const long long vl = base + lane;
+    const bool heavy = lane < nv && resid &&
+                       (long long)__ldg(off + vl + 1) - (long long)__ldg(off + vl) > kKcoreRowsHeavy;
+    if (lane < nv && !heavy) {  // a heavy vertex's rows come from kcore_rows_heavy_kernel
+      const long long v = vl;
       const uint32_t cv = __ldg(core + v);
       for (int i = 0; i < nk; ++i) {
         const bool inc = cv >= ks[i];
@@ -1140,6 +1146,81 @@ __global__ void __launch_bounds__(kThreads) kcore_rows_kernel(int n, const OffT*
       }
     }
     __syncwarp();
+  }
+}
+
+// The vertices of more than kKcoreRowsHeavy edges, one CTA each: every
+// thread takes edges, finds how many k values min(coreness(u),
+// coreness(v)) reaches, and adds one to that bin of a shared histogram
+// (one atomic per distinct bin of a warp); the counts of k value i are the
+// bins above i.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) kcore_rows_heavy_kernel(int n, const OffT* off, const int32_t* idx,
+                                                                   const uint32_t* core, const KcoreRows q,
+                                                                   uint8_t* in_core, uint32_t* resid) {
+  __shared__ uint32_t ks[kKcoreBatchMax];
+  __shared__ unsigned hist[kKcoreBatchMax + 1];
+  __shared__ int heavy[kThreads];
+  __shared__ int nheavy;
+  const int nk = q.nk;
+  for (int i = threadIdx.x; i < nk; i += kThreads) ks[i] = q.ks[i];
+  const int lane = lane_id();
+  // vertex v goes to CTA v % grid: the hubs, low ids in a power-law graph
+  // without relabelling, spread over the CTAs
+  const long long per = ((long long)n + gridDim.x - 1) / gridDim.x;
+  for (long long c0 = 0; c0 < per; c0 += kThreads) {
+    if (threadIdx.x == 0) nheavy = 0;
+    __syncthreads();
+    const long long v = (c0 + threadIdx.x) * (long long)gridDim.x + blockIdx.x;
+    if (c0 + threadIdx.x < per && v < n && (long long)__ldg(off + v + 1) - (long long)__ldg(off + v) > kKcoreRowsHeavy)
+      heavy[atomicAdd(&nheavy, 1)] = (int)v;
+    __syncthreads();
+    const int nh = nheavy;
+    for (int h = 0; h < nh; ++h) {
+      const int hv = heavy[h];
+      const uint32_t cv = __ldg(core + hv);
+      for (int i = threadIdx.x; i <= nk; i += kThreads) hist[i] = 0;
+      __syncthreads();
+      if (cv >= ks[0]) {
+        const long long b = (long long)__ldg(off + hv), e = (long long)__ldg(off + hv + 1);
+        constexpr int kPer = 4;  // edges per thread in flight
+        for (long long p0 = b; p0 < e; p0 += (long long)kThreads * kPer) {
+          uint32_t cu[kPer];
+#pragma unroll
+          for (int q = 0; q < kPer; ++q) {
+            const long long p = p0 + (long long)q * kThreads + threadIdx.x;
+            cu[q] = p < e ? __ldg(core + __ldg(idx + p)) : 0u;
+          }
+#pragma unroll
+          for (int q = 0; q < kPer; ++q) {
+            const long long p = p0 + (long long)q * kThreads + threadIdx.x;
+            int j = -1;
+            if (p < e) {
+              const uint32_t m = cu[q] < cv ? cu[q] : cv;
+              int lo = 0, hi = nk;
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ks[mid] <= m) lo = mid + 1;
+                else hi = mid;
+              }
+              j = lo;
+            }
+            const unsigned peers = __match_any_sync(kFull, j);
+            if (j >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[j], (unsigned)__popc(peers));
+          }
+        }
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < nk; i += kThreads) {
+        const bool inc = cv >= ks[i];
+        unsigned c = 0;
+        for (int t = i + 1; t <= nk; ++t) c += hist[t];
+        const size_t at = (size_t)q.row[i] * (size_t)n + (size_t)hv;
+        in_core[at] = inc ? 1 : 0;
+        resid[at] = inc ? c : 0u;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -1172,7 +1253,12 @@ static int run_kcore_batch(simdx_graph* g, const uint32_t* ks, int nk, uint8_t* 
   kcore_rows_kernel<OffT><<<grid, kThreads, smem, st>>>((int)g->n, (const OffT*)g->off, g->idx, core, q, in_core,
                                                        resid);
   SIMDX_CUDA(cudaGetLastError());
-  return finish_launch(g, stats, st, launches + 1);
+  if (!resid) return finish_launch(g, stats, st, launches + 1);
+  const long long hb = ((long long)g->n + kThreads - 1) / kThreads;
+  kcore_rows_heavy_kernel<OffT><<<(unsigned)(hb < 1216 ? hb : 1216), kThreads, 0, st>>>(
+      (int)g->n, (const OffT*)g->off, g->idx, core, q, in_core, resid);
+  SIMDX_CUDA(cudaGetLastError());
+  return finish_launch(g, stats, st, launches + 2);
 }
 
 const void* kcore_kernel_ptr(int off_bits) {
