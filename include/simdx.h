@@ -320,8 +320,9 @@ SIMDX_API int simdx_kcore_decompose(simdx_graph *g, uint32_t *coreness, simdx_st
  * residual_deg[i*n + v] = the number of v's neighbours (edges) inside that
  * core for a member, 0 otherwise.  One decomposition (simdx_kcore_decompose,
  * its coreness kept in the graph's workspace) answers every k: v is in the
- * k-core exactly when coreness(v) >= k; one more launch counts, per vertex,
- * the neighbours whose coreness reaches each k and writes the rows.
+ * k-core exactly when coreness(v) >= k; two more launches count, per
+ * vertex, the neighbours whose coreness reaches each k and write the rows
+ * (a warp per vertex of up to 128 edges, a CTA per vertex of more).
  * ks: host uint32[nk], any order, repeats allowed, 1 <= nk <= 64; in_core:
  * device uint8[nk * n]; residual_deg: device uint32[nk * n] or NULL (not
  * written).  Needs a symmetric graph.  Errors: EINVAL (NULL ks or in_core,
