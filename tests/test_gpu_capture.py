@@ -95,3 +95,53 @@ def test_capture_rejects_stats():
             G.bfs(0, out=out, stats=simdx_stats())
     torch.cuda.synchronize()
     G.close()
+
+
+def test_capture_cluster_launches():
+    """On a grid (no hubs) BFS runs its small levels in a launch in clusters,
+    the k-core decomposition splits into a plain, a cluster and a plain
+    launch, the batched k-core adds its row launches, and SSSP in cluster
+    mode launches in clusters: a capture records them all and replays give
+    the calls' results."""
+    import torch
+    g = gg.grid(60, 50)
+    w = gg.weights(g, 4, 1, 100)
+    G = make(g, w, bits=64)
+    S = make(g, w, bits=32, small_frontier=1)
+    n = g.n
+    dev = torch.device("cuda")
+    o1 = torch.empty(n, dtype=torch.int32, device=dev)
+    oc = torch.empty(n, dtype=torch.int32, device=dev)
+    os_ = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def calls():
+        G.bfs(7, out=o1)
+        G.coreness(out=oc)
+        kb = G.kcore_batch([1, 2, 3])
+        S.sssp(11, out=os_)
+        return kb
+
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        calls()
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (o1, oc, os_)]
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=s):
+        kin, kres = calls()
+    for rep in range(2):
+        for t in (o1, oc, os_):
+            t.fill_(-5)
+        kin.fill_(7)
+        cg.replay()
+        torch.cuda.synchronize()
+        for t, r in zip((o1, oc, os_), ref):
+            assert torch.equal(t, r), rep
+        core = oracle.coreness(g.offsets, g.indices)
+        for i, k in enumerate([1, 2, 3]):
+            assert np.array_equal(kin[i].cpu().numpy(), (core >= k).astype(np.uint8)), (rep, k)
+    assert np.array_equal(o1.cpu().numpy(), oracle.bfs(g.offsets, g.indices, 7))
+    assert np.array_equal(os_.cpu().numpy().view(np.uint32), oracle.sssp(g.offsets, g.indices, w, 11))
+    assert np.array_equal(oc.cpu().numpy().view(np.uint32), core)
+    G.close()
+    S.close()
