@@ -32,10 +32,12 @@
  *     simdx_graph_set_config (when a larger workspace is needed) and the
  *     batch / server entry points that say so; the algorithm calls allocate
  *     nothing.
- *   - CUDA graphs: simdx_bfs, simdx_sssp, simdx_kcore, simdx_pagerank,
- *     simdx_bfs_batch, simdx_sssp_batch (groups of up to 64 sources) and
- *     simdx_bfs_multi can be captured into a CUDA graph (stream capture on
- *     `stream`) and replayed, each launch a cooperative kernel node, when
+ *   - CUDA graphs: simdx_bfs, simdx_sssp, simdx_kcore, simdx_kcore_decompose,
+ *     simdx_kcore_batch, simdx_pagerank, simdx_bfs_batch, simdx_sssp_batch
+ *     (groups of up to 64 sources) and simdx_bfs_multi can be captured into
+ *     a CUDA graph (stream capture on `stream`) and replayed, each launch a
+ *     cooperative kernel node (in clusters where small_frontier puts it
+ *     there), when
  *     (a) stats is NULL (a captured call with stats returns EUNSUPPORTED),
  *     (b) a call of the same kind ran on the graph outside the capture
  *     before (it allocates the batch state; for simdx_bfs_multi with at
