@@ -261,9 +261,10 @@ SIMDX_API int simdx_graph_last_status(simdx_graph *g, void *stream);
  * distances, and the next filter scans every vertex), active vertices, active edges, level / bucket bound,
  * %globaltimer ns at the iteration's start and at its end (as seen by CTA 0),
  * and two algorithm-specific words: for BFS the end of the main compute phase
- * and the number of high in-degree pull candidates; for the others the
- * slowest CTA's time in degree classes (ns, 32 bits each) as (3 << 32 | 2)
- * and (1 << 32 | 0)}.  A batched SSSP run as several launches (see
+ * and the number of high in-degree pull candidates; for PageRank's pull the
+ * slowest CTA's time in its phases (ns, 32 bits each); 0 for the others,
+ * whose per-class timing was dropped (it cost 3.5 % of the grid SSSP), and
+ * the cluster records described under small_frontier}.  A batched SSSP run as several launches (see
  * batch_group) numbers its records across them.  Writes up to `cap` records
  * to host memory `rec` and returns the number of iterations of the run in
  * *count. */

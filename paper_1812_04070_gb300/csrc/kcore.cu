@@ -221,13 +221,13 @@ __global__ void __launch_bounds__(kThreads, 4) kcore_kernel(KcoreArgs<OffT> a) {
     unsigned long long nrec = 0, mrec = 0;
     if (dir == 1) {
       KcorePush<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit, &slot);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit);
       nrec = f.nrec;
       mrec = f.mrec;
       ++push_it;
     } else {
       KcorePull<OffT> f(removed_at, cnt, a.off, kk, it, sh, a.w, k, grid);
-      pull_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, red_u32, k.huge_min, sh, a.w, evisit, &slot);
+      pull_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, red_u32, k.huge_min, sh, a.w, evisit);
       nrec = f.nrec;
       mrec = f.mrec;
       ++pull_it;
@@ -972,7 +972,7 @@ __global__ void __launch_bounds__(kThreads, CLU ? 3 : 4) coreness_kernel(CoreArg
     const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                       a.w.list[lbuf][3]};
     CorePush<OffT> f(removed_at, cnt, a.core, a.off, (unsigned)K, it, sh, a.w, k, grid);
-    push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit, &slot);
+    push_classes<OffT>(f, a.off, a.idx, lists, cnt_l, grid, k.huge_min, sh, evisit);
     online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
     const unsigned long long tn = cta_sum_u64(f.nrec, sh), tm = cta_sum_u64(f.mrec, sh);
     if (threadIdx.x == 0 && tn) {

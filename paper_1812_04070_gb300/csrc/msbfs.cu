@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 4) msbfs_kernel(const __grid_constan
     PhaseSlot& slot = s->slot[slot_of(sh.phase)];
     MsPush<OffT> f(fr[0], fr[1], a.visit, off, sh, a.w, k, grid);
     const int32_t* lists[kClasses] = {a.w.list[0][0], a.w.list[0][1], a.w.list[0][2], a.w.list[0][3]};
-    push_classes<OffT>(f, off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
+    push_classes<OffT>(f, off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit);
     online_flush(sh, a.w, k, grid, 1, slot);
     unsigned long long tn = cta_sum_u64(f.nrec, sh);
     if (threadIdx.x == 0 && tn) atomicAdd(&slot.nact, tn);
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 4) msbfs_kernel(const __grid_constan
     f.ld = a.ld;
     f.next = L + 1;
     const int32_t* lists[kClasses] = {a.w.list[0][0], a.w.list[0][1], a.w.list[0][2], a.w.list[0][3]};
-    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_m, k.huge_min, sh, a.w, evisit, &slot);
+    pull_classes<OffT>(f, ioff, a.iidx, lists, cnt, grid, red_m, k.huge_min, sh, a.w, evisit);
     unsigned long long tn = cta_sum_u64(f.nrec, sh);
     if (threadIdx.x == 0 && tn) atomicAdd(&slot.nact, tn);
     if (!grid_sync(s, grid, sh, k)) return;

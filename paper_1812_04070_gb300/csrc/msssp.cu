@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 4) msssp_kernel(const __grid_constan
       {
         const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                           a.w.list[lbuf][3]};
-        push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot);
+        push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit);
       }
       online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
       const unsigned long long tn = cta_sum_u64(f.nrec, sh);

@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 4) pagerank_push_kernel(const __grid
       PhaseSlot& slot2 = s->slot[slot_of(sh.phase)];
       PrPush f{res, push_c};
       const int32_t* lists[kClasses] = {a.w.list[1][0], a.w.list[1][1], a.w.list[1][2], a.w.list[1][3]};
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot2);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit);
     }
     if (!grid_sync(s, grid, sh, k)) return;
     trace_put(a.w, t, 1 | (2 << 8), sel, 0, (long long)p.aux1, t_it);

@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
         SsspVerify<OffT> fv{a.wt, a.dist, pend};
         const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                           a.w.list[lbuf][3]};
-        pull_classes<OffT>(fv, a.off, a.idx, lists, cc, grid, red_u, k.huge_min, sh, a.w, evisit, &slot_v);
+        pull_classes<OffT>(fv, a.off, a.idx, lists, cc, grid, red_u, k.huge_min, sh, a.w, evisit);
         const unsigned long long ch = cta_sum_u64(fv.changed, sh);
         if (threadIdx.x == 0 && ch) atomicAdd(&slot_v.aux0, ch);
         if (!grid_sync(s, grid, sh, k)) return;
@@ -838,7 +838,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       SsspPull<OffT> f(fbm, pdist, a.wt, a.dist, pend, a.off, T, sh, a.w, k, grid);
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
-      pull_classes<OffT>(f, a.off, a.idx, lists, cc, grid, red_u, k.huge_min, sh, a.w, evisit, &slot);
+      pull_classes<OffT>(f, a.off, a.idx, lists, cc, grid, red_u, k.huge_min, sh, a.w, evisit);
       online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
       tn = cta_sum_u64(f.nrec, sh);
       tm = cta_sum_u64(f.mrec, sh);
@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(kThreads, 4) sssp_kernel(const __grid_constant
       scan_all = f.dense;
       const int32_t* lists[kClasses] = {a.w.list[lbuf][0], a.w.list[lbuf][1], a.w.list[lbuf][2],
                                         a.w.list[lbuf][3]};
-      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, &slot, &stg);
+      push_classes<OffT>(f, a.off, a.idx, lists, cnt, grid, k.huge_min, sh, evisit, nullptr, &stg);
       online_flush(sh, a.w, k, grid, lbuf ^ 1, slot);
       tn = cta_sum_u64(f.nrec, sh);
       tm = cta_sum_u64(f.mrec, sh);
