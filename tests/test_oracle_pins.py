@@ -369,6 +369,25 @@ def test_coreness_invariants_rmat():
     assert np.all(strong >= core)
 
 
+def test_kcore_residual_from_coreness():
+    """The identity the batched k-core computes from one decomposition: the
+    k-core's residual degree of a member v is the number of its neighbours
+    u with min(coreness(u), coreness(v)) >= k, and 0 outside the core --
+    checked against the peeling oracle for every k on R-MAT 12, a grid and
+    a star (the peeling and the decomposition are separate programs)."""
+    for g in (gg.rmat(12), gg.grid(20, 30), gg.star(40)):
+        core = oracle.coreness(g.offsets, g.indices).astype(np.int64)
+        deg = g.degrees()
+        u = np.repeat(np.arange(g.n), deg)
+        m = np.minimum(core[u], core[g.indices])
+        for k in range(0, int(core.max()) + 2):
+            inc, res = oracle.kcore(g.offsets, g.indices, k)
+            want = np.bincount(u, weights=(m >= k), minlength=g.n).astype(np.int64)
+            want[core < k] = 0
+            assert np.array_equal(inc.astype(bool), core >= k), (g.name, k)
+            assert np.array_equal(res.astype(np.int64), want), (g.name, k)
+
+
 # ----------------------------------------------------------------- PageRank
 def pagerank_dense(g, d):
     """Fixed point of the PageRank map by a dense FP64 linear solve."""
