@@ -503,7 +503,8 @@ __device__ bool core_local(const CoreArgs<OffT>& a, LocalShared& ls, CtaShared& 
     loc_publish(cl, ls, 0, r);
     cl.sync();
     unsigned cc, cp, zc, zp;
-    unsigned N = loc_counts(ls, 0, cc, cp, zc, zp).n;
+    const LocTotals T0 = loc_counts(ls, 0, cc, cp, zc, zp);
+    unsigned N = T0.n;
     // the domain: this CTA's segment [seg_lo, seg_lo + seg_n) of src (the
     // identity when src is null), compacted into the other buffer
     const long long seg_lo = dcount * (long long)r / kCluster;
@@ -520,9 +521,12 @@ __device__ bool core_local(const CoreArgs<OffT>& a, LocalShared& ls, CtaShared& 
     int attempt = 0;  // scans of this level that deleted nothing (jumps)
     long long steps = 0;
     long long c_scans = 0;  // SM clock cycles of scans since the last push
-    bool handback = false;
+    // the entry lists' pieces may overflow a CTA's buffer (a few vertices of
+    // many edges in one CTA's share): then nothing is walked here, and the
+    // grid lists and pushes the pending vertices itself
+    bool handback = T0.ovf != 0;
     unsigned long long t_it = trace_clock();
-    while (true) {
+    while (!handback) {
       const int nx = cur == 2 ? 0 : cur + 1, nn = nx == 2 ? 0 : nx + 1;
       unsigned ab = 0;
       if (threadIdx.x == 0) {

@@ -639,3 +639,17 @@ def test_kcore_batch_limits():
         D.kcore_batch([2])
     assert e.value.status == simdx.EINVAL
     D.close()
+
+
+def test_coreness_cluster_entry_overflow():
+    """A hub of 33,000 edges alone in a pending frontier (its leaves went
+    first): its pieces of at most 64 edges overflow the one CTA whose share
+    it is, so the cluster walks nothing and the grid pushes it; the result
+    stays exact."""
+    k = 33000
+    g = gg.from_edges(k + 1, np.zeros(k, np.int64), np.arange(1, k + 1), "hub")
+    for small in (1, 2):
+        G = make(g, bits=32, small_frontier=small)
+        assert np.array_equal(G.coreness().cpu().numpy().view(np.uint32), oracle.coreness(g.offsets, g.indices))
+        assert G.last_status() == 0
+        G.close()
