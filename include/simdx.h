@@ -306,7 +306,8 @@ SIMDX_API int simdx_kcore(simdx_graph *g, uint32_t k, uint8_t *in_core,
 /* k-core decomposition (Sec. 6 "k-Core", run for every k): coreness[v] =
  * the largest k such that v belongs to the k-core (0 for isolated
  * vertices), so simdx_kcore(k) keeps exactly the vertices with coreness >=
- * k.  One persistent launch peels level after level: at level K every
+ * k.  Persistent launches peel level after level (one on the grid, or,
+ * with small_frontier, up to three: see there): at level K every
  * remaining vertex of residual degree <= K is deleted with coreness K, its
  * push decrements its remaining neighbours, and the decrement that takes a
  * neighbour to K deletes it at the same level; a scan of the remaining
