@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <unordered_map>
@@ -224,12 +225,17 @@ int launch_coop(const void* kernel, int grid, void** args, cudaStream_t st, int 
 // most the clusters that fit at once, a multiple of the cluster size (0 if
 // none fits).
 int grid_for_cluster(const simdx_graph* g, const void* kernel, int cluster) {
+  // per device: the non-portable cluster size is allowed on each device the
+  // kernel runs on
   static std::mutex mu;
-  static std::unordered_map<const void*, int> max_clusters;
+  static std::map<std::pair<int, const void*>, int> max_clusters;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const auto key = std::make_pair(dev, kernel);
   int mc = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto it = max_clusters.find(kernel);
+    auto it = max_clusters.find(key);
     if (it != max_clusters.end()) {
       mc = it->second;
     } else {
@@ -247,7 +253,7 @@ int grid_for_cluster(const simdx_graph* g, const void* kernel, int cluster) {
         mc = 0;
       else if (cudaOccupancyMaxActiveClusters(&mc, kernel, &cfg) != cudaSuccess)
         mc = 0;
-      max_clusters[kernel] = mc;
+      max_clusters[key] = mc;
     }
   }
   int grid = std::min(grid_for(g, kernel), mc * cluster);

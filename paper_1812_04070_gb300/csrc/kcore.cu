@@ -18,6 +18,7 @@
 // compares the frontier's edges with the alive vertices' edges.
 #include <climits>
 #include <mutex>
+#include <set>
 #include <utility>
 #include <type_traits>
 
@@ -1251,15 +1252,20 @@ static int run_kcore_batch(simdx_graph* g, const uint32_t* ks, int nk, uint8_t* 
     }
   const void* kern = (const void*)kcore_rows_kernel<OffT>;
   const size_t smem = sizeof(uint32_t) * (size_t)kWarps * (size_t)nk * 32;
-  // the largest row buffer, allowed once (not a stream operation, so a
-  // call inside a stream capture does not repeat it)
-  static std::once_flag allow;
-  cudaError_t ae = cudaSuccess;
-  std::call_once(allow, [&] {
-    ae = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(uint32_t) * kWarps * kKcoreBatchMax * 32));
-  });
-  SIMDX_CUDA(ae);
+  // the largest row buffer, allowed once per device (not a stream
+  // operation, so a call inside a stream capture does not repeat it)
+  {
+    static std::mutex mu;
+    static std::set<int> allowed;
+    int dev = 0;
+    SIMDX_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!allowed.count(dev)) {
+      SIMDX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(uint32_t) * kWarps * kKcoreBatchMax * 32)));
+      allowed.insert(dev);
+    }
+  }
   const long long tiles = ((long long)g->n + 31) / 32;
   const long long blocks = (tiles + kWarps - 1) / kWarps;
   const unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
